@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the IC(k) hot path: numeric factorization (value scatter + the
+persistent Chol/Trsm/Herk/Gemm task-DAG kernel) followed by a PCG solve with the
+factor as preconditioner.
+
+Workload (default): 27-point constant-coefficient Laplacian on a 96^3 grid
+(884,736 rows, 23,393,656 nonzeros), geometric nested dissection, 2D blocks of at
+most 4096 rows, IC(2), FP64, b ~ N(0,1), PCG to relative residual 1e-10.
+
+A step is one numeric factorization plus one PCG solve.  value = algorithmic factor
+flops / factor time (GFLOP/s, the time of the two numeric kernels measured with CUDA
+events on the launching stream).  e2e repeats the step through the C ABI from pinned
+host buffers, with the host-to-device copies of A's values and b and the
+device-to-host copy of x inside the timed region.
+
+--impl reference times the CPU oracle (the single-threaded FP64 reference the
+parity tests use) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IC(k) factor GFLOP/s & HBM GB/s; PCG time-to-1e-8 vs plain FP64 on GB300"
+FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (see the alu roofline in the design notes)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=96)
+    ap.add_argument("--k", type=int, default=2)
+    ap.add_argument("--block-rows", type=int, default=4096)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--warps", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"27-point Laplacian {a.side}^3 (n={a.side ** 3}), geometric ND, 2D blocks <= "
+            f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+
+        util = [num(r[4]) for r in rows]
+        loaded = [r for r, u in zip(rows, util) if u >= 50] or rows
+        sm = [num(r[1]) for r in loaded]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in loaded:
+            for nm, v in zip(names, r[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": num(loaded[0][2]),
+                "samples": len(loaded), "reasons": sorted(reasons)}
+
+
+def run_oracle_sample(side, k, reps=1):
+    """Oracle numeric IC(k) on a side^3 27-point problem: (flops, seconds per run)."""
+    import oracle
+    import synth
+    prob = synth.laplace3d_27pt(side)
+    perm, _ = oracle.nd_grid(side, side, side, 1, 4096)
+    h = oracle.OracleIC.from_problem(prob, perm, k)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        st = h.numeric(prob.vals)
+        times.append(time.perf_counter() - t0)
+        assert st == 0
+    return h.flops, statistics.median(times)
+
+
+def reference_arm(a, rank, world):
+    if rank != 0:
+        return
+    # bounded sample: a 48^3 sub-problem of the same family (about 1 s per step)
+    side = max(8, a.side // 2)
+    for _ in range(a.warmup):
+        run_oracle_sample(side, a.k)
+    ts, fl = [], 0.0
+    for _ in range(a.steps):
+        fl, t = run_oracle_sample(side, a.k)
+        ts.append(t)
+    t = sum(ts) / len(ts)
+    v = fl / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "sample": f"{side}^3 sub-problem, IC({a.k})"},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle numeric IC({a.k}) of the {side}^3 27-point problem "
+                                       f"per step ({fl:.3g} flops)"},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if a.impl == "reference":
+        reference_arm(a, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import synth
+    import paper_1601_05871_gb300 as ick
+    from paper_1601_05871_gb300.build import build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    ick.load()
+
+    prob = synth.laplace3d_27pt(a.side)
+    perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.block_rows)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
+                        warps_per_cta=a.warps)
+    st = ick.ic_stats(h)
+    ick.ic_set_timing(h, True)
+    stream = torch.cuda.current_stream()
+    av = torch.from_numpy(prob.vals).cuda()
+    b_host = synth.rhs(prob.n, 2000 + rank)
+    b = torch.from_numpy(b_host).cuda()
+    x = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+
+    def step():
+        ick.ic_numeric(h, av, stream)
+        t = ick.ic_get_timing(h)
+        it, rel = ick.pcg_solve(h, av, b, x, a.tol, 5000, stream)
+        return t["prepare_ms"] + t["numeric_ms"], t["numeric_ms"], it, rel
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    ick.ic_reset_timing(h)
+    fact_ms, kern_ms, iters, rels = [], [], [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(a.steps):
+            f, kms, it, rel = step()
+            fact_ms.append(f)
+            kern_ms.append(kms)
+            iters.append(it)
+            rels.append(rel)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    tim = ick.ic_get_timing(h)
+    clocks = clk.summary()
+    mean_fact = sum(fact_ms) / len(fact_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms, mean_fact], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms, mean_fact = tt.tolist()
+    ms_per_step = total_ms / a.steps
+    value = world * st["flops"] / (mean_fact * 1e-3) / 1e9
+    hbm = world * st["bytes"] / (mean_fact * 1e-3) / 1e9
+    apply_ms_step = tim["apply_ms"] / a.steps
+    mean_kern = sum(kern_ms) / len(kern_ms)
+
+    # true residual of the last solve, in FP64 on the host
+    xh = x.cpu().numpy()
+    true_rel = float(np.linalg.norm(prob.scipy() @ xh - b_host) / np.linalg.norm(b_host))
+
+    # dominant kernel by measured share of the step: numeric task kernel vs triangular solves
+    peak_hbm = 6783.5
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak_hbm = float(peaks.get("hbm_gbs", peak_hbm))
+        peak_src = "measured"
+    except Exception:
+        peak_src = "fallback"
+    n, nnz_l = st["n"], st["nnz_l"]
+    solve_bytes = nnz_l * 12 + n * 8 * 4  # both solves: L values + indices, r, y, z, perm
+    roof_numeric = {"kernel": "ic_numeric (value scatter + persistent task-DAG kernel)",
+                    "bound": "alu", "achieved": st["flops"] / (mean_fact * 1e-3) / 1e9,
+                    "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "peak_source": "nominal FP64",
+                    "hbm_achieved_gbs": st["bytes"] / (mean_fact * 1e-3) / 1e9,
+                    "hbm_peak_gbs": peak_hbm, "traffic": None}
+    roof_numeric["frac"] = roof_numeric["achieved"] / roof_numeric["peak"]
+    per_apply = tim["apply_ms"] / max(1, tim["apply_calls"])
+    roof_solve = {"kernel": "forward_solve + backward_solve (one ic_apply)", "bound": "hbm",
+                  "achieved": solve_bytes / (per_apply * 1e-3) / 1e9 if per_apply > 0 else 0.0,
+                  "peak": peak_hbm, "unit": "GB/s", "peak_source": peak_src, "traffic": None}
+    roof_solve["frac"] = roof_solve["achieved"] / roof_solve["peak"]
+    dominant = roof_solve if apply_ms_step > mean_kern else roof_numeric
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "n": n, "nnz_a": st["nnz_a"], "nnz_l": nnz_l,
+                       "k": a.k, "block_rows": a.block_rows, "ranges": st["nranges"],
+                       "blocks": st["nblocks"], "tasks": st["ntasks"], "items": st["nitems"],
+                       "critical_path_tasks": st["critical_path"], "warps_per_cta": a.warps,
+                       "grid_ctas": st["grid_ctas"], "flops": st["flops"], "bytes": st["bytes"],
+                       "l2": "inputs larger than L2 (factor values alone 8*nnz(L) bytes)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "hbm_gbs": hbm, "factor_ms": mean_fact, "numeric_kernel_ms": mean_kern,
+            "pcg": {"iters": iters[-1], "relres": rels[-1], "true_relres": true_rel,
+                    "tol": a.tol, "apply_ms_per_step": apply_ms_step,
+                    "time_to_solution_ms": ms_per_step},
+            "roofline": dominant, "roofline_numeric": roof_numeric, "roofline_solve": roof_solve,
+            "gpu_launches": int(tim["launches"]), "clocks": clocks}
+
+    if not a.no_e2e:
+        ab = torch.from_numpy(prob.vals).pin_memory()
+        bb = torch.from_numpy(b_host).pin_memory()
+        xb = torch.empty(prob.n, dtype=torch.float64).pin_memory()
+        av2 = torch.empty_like(av)
+        b2 = torch.empty_like(b)
+
+        def e2e_step():
+            av2.copy_(ab, non_blocking=True)
+            b2.copy_(bb, non_blocking=True)
+            ick.ic_numeric(h, av2, stream)
+            ick.pcg_solve(h, av2, b2, x, a.tol, 5000, stream)
+            xb.copy_(x, non_blocking=True)
+            stream.synchronize()
+
+        for _ in range(a.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        t_e2e = (time.perf_counter() - t0) / a.steps
+        if world > 1:
+            tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = tt.item()
+        line["e2e"] = {"value": world * st["flops"] / t_e2e / 1e9, "unit": "GFLOP/s",
+                       "h2d_bytes_per_step": int(prob.vals.nbytes + b_host.nbytes),
+                       "d2h_bytes_per_step": int(xh.nbytes), "ms_per_step": t_e2e * 1e3,
+                       "note": "factor flops / end-to-end step time (copies + factor + PCG)"}
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        fl, t = run_oracle_sample(a.side, a.k)
+        line["cpu_baseline"] = {"value": fl / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one oracle numeric IC({a.k}) of the full {a.side}^3 "
+                                          f"workload ({t:.1f} s)"}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

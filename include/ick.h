@@ -1,0 +1,235 @@
+/*
+ * ick.h -- C ABI of the GB300 level-of-fill incomplete Cholesky library (libick.so).
+ *
+ * The library computes IC(k) on the 2D sparse partitioned-block layout of
+ * Kim, Rajamanickam, Stelle, Edwards and Olivier, "Task Parallel Incomplete
+ * Cholesky Factorization using 2D Partitioned-Block Layout" (arXiv:1601.05871):
+ * symbolic factorization (Algorithm 1, Section 3.1), the 2D block matrix
+ * (Section 3.2) and the numeric Cholesky-by-blocks task DAG (Section 3.3, the
+ * Chol / Trsm / Herk / Gemm task generator figure) executed by one persistent
+ * CUDA kernel.  The factor is used as a PCG preconditioner (Section 1).
+ *
+ * Conventions shared by every call:
+ *   - A is symmetric positive definite, given as a FULL symmetric CSR pattern
+ *     (both triangles) with sorted, duplicate-free columns and a structural
+ *     diagonal in every row; rowptr is int64, colind int32, values float64.
+ *   - perm[new] = old.  B = P^T A P is the reordered matrix, B_ij = A_perm[i],perm[j].
+ *     Only the upper triangle of B is read (B_ij with i <= j, wherever it lies in A),
+ *     so A's values must be symmetric bit for bit.
+ *   - The factor is kept as U = L^T (upper CSR, diagonal first in each row) so that
+ *     B ~= U^T U = L L^T; ic_get_factor returns L in lower CSR (diagonal last).
+ *   - "host" pointers are CPU memory; "device" pointers are CUDA global memory on the
+ *     current device; "stream" is a cudaStream_t (NULL: the legacy default stream).
+ *   - Every call returns an ic_status; no call aborts the process or traps on the GPU.
+ *     Device waits are bounded by ic_opts.timeout_s and end in IC_ERR_TIMEOUT.
+ *   - Inputs are borrowed for the duration of the call and copied where kept.
+ *     The handle owns every device allocation it makes; ic_destroy frees them.
+ */
+#ifndef ICK_H
+#define ICK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IC_OK = 0,
+    IC_ERR_ARG = 1,       /* bad argument (NULL, size, range, option)                  */
+    IC_ERR_PATTERN = 2,   /* malformed CSR: unsorted, duplicate, out of range,
+                             asymmetric, or missing diagonal                           */
+    IC_ERR_BREAKDOWN = 3, /* a pivot <= 0 or not finite; *breakdown_row = first row    */
+    IC_ERR_TIMEOUT = 4,   /* a bounded device wait expired; the factor is invalid      */
+    IC_ERR_CUDA = 5,      /* a CUDA runtime call failed                                */
+    IC_ERR_NOMEM = 6,     /* host or device allocation failed                          */
+    IC_ERR_NOCONV = 7,    /* PCG reached maxit before the tolerance                    */
+    IC_ERR_STATE = 8      /* call out of order (e.g. ic_apply before ic_numeric)       */
+} ic_status;
+
+enum { IC_F64 = 0, IC_F32 = 1 };
+
+typedef struct {
+    int64_t n;
+    const int64_t* rowptr; /* host, n+1 */
+    const int32_t* colind; /* host, rowptr[n]; full symmetric, sorted */
+} ic_csr_pattern;
+
+/* Options.  A zero-initialised struct selects the defaults given in brackets. */
+typedef struct {
+    int block_rows;    /* [4096] largest block; longer ranges are split evenly; <= 8192 */
+    int dtype;         /* [IC_F64] factor precision                                      */
+    int warps_per_cta; /* [16] warps in each CTA of the persistent numeric kernel: 8|16  */
+    int rows_per_item; /* [32] target rows per work item of a Herk/Gemm task             */
+    double timeout_s;  /* [10] bound on every device wait of one call                    */
+    double shift_alpha;/* [0] factor B + alpha * diag(B) instead of B                    */
+    int exact;         /* [0] 1: each update is a separately rounded multiply then
+                          subtract (no FMA), the same operation sequence per entry as
+                          the up-looking row order, so the FP64 factor is reproducible
+                          bit for bit; 0: fused multiply-add                            */
+    int threads;       /* [0 = all] host threads for the symbolic phase                  */
+    int host_only;     /* [0] 1: ic_symbolic builds the plan in host memory only (no GPU
+                          needed); such a handle serves the ic_get_* and ic_stats calls   */
+    int reserved[5];
+} ic_opts;
+
+typedef struct {
+    int64_t n;            /* rows                                                    */
+    int64_t nnz_a;        /* nonzeros of A (both triangles)                          */
+    int64_t nnz_l;        /* nonzeros of L (= of U), diagonal included               */
+    int64_t nranges;      /* block rows/columns of the 2D block matrix               */
+    int64_t nblocks;      /* existing blocks (i <= j) of the 2D block matrix         */
+    int64_t ntasks;       /* Chol + Trsm + Herk + Gemm tasks                         */
+    int64_t ntasks_type[4];/* per type: Chol, Trsm, Herk, Gemm                       */
+    int64_t nitems;       /* work items the persistent kernel drains                 */
+    int64_t critical_path;/* tasks on the longest DAG path                           */
+    int64_t max_level;    /* largest level of fill kept (<= k)                       */
+    double flops;         /* algorithmic flops of one numeric factorization          */
+    double bytes;         /* compulsory HBM bytes of one numeric factorization       */
+    double symbolic_s;    /* wall time of ic_symbolic                                */
+    int64_t grid_ctas;    /* CTAs of the persistent kernel launch                    */
+} ic_stats_t;
+
+typedef struct ic_handle ic_handle;
+
+/* Geometric nested dissection of a grid (Algorithm 1, steps 1 and 3; Section 3.1,
+ * with Scotch replaced by cuts of the grid coordinates).  The box's longest axis
+ * (ties: x, y, z) is cut by the one-node plane m = lo + (hi-lo)/2; the low half,
+ * the high half and the plane are numbered in that order, recursively.  A part
+ * with <= leaf_rows kept rows, or whose longest extent is < 3, is a leaf (this is
+ * the pruning of the ND tree, Algorithm 1 step 3).  Inside a part rows are
+ * lexicographic with x fastest; dof > 1 keeps a node's dofs together.
+ *   keep      host, nx*ny*nz*dof bytes or NULL: 0 drops that dof (eliminated
+ *             boundary conditions); the returned order covers the kept dofs only,
+ *             indexed in grid order among the kept ones.
+ *   perm_out  host, >= n entries: perm[new] = old.
+ *   ranges_out host, >= n+1 entries or NULL: 0 then the end of each part, in order.
+ *   nranges_out, n_out: number of parts and of kept rows.
+ * Errors: IC_ERR_ARG for non-positive sizes or NULL perm_out. */
+int ic_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep,
+               int32_t* perm_out, int64_t* ranges_out, int64_t* nranges_out, int64_t* n_out);
+
+/* Symbolic factorization (Algorithm 1, steps 2, 4, 5; Sections 3.1-3.3) on the host:
+ * reorders A by perm (NULL: identity), finds the level-k fill pattern S by a
+ * breadth-first search from every row (the Hysom-Pothen scheme of Section 4.1:
+ * entry (i,j) has level = edges - 1 of the shortest path i..j whose interior
+ * vertices are all < min(i,j); kept when <= k), builds the 2D block matrix over
+ * the ranges (NULL: uniform blocks of opts->block_rows rows), generates the
+ * Cholesky-by-blocks task DAG, and uploads everything to the current device.
+ *   A       host pattern (values are not needed here).
+ *   ranges  host, nranges+1 increasing boundaries from 0 to n, or NULL.
+ *   opts    NULL for defaults.
+ *   out     receives the handle; *out is NULL on error.
+ * Errors: IC_ERR_ARG, IC_ERR_PATTERN, IC_ERR_NOMEM, IC_ERR_CUDA. */
+int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
+                int64_t nranges, const ic_opts* opts, ic_handle** out);
+
+/* Numeric factorization (Section 3.3): scatters B's values onto S (zero on fill) and
+ * runs the Chol / Trsm / Herk / Gemm task DAG in one persistent kernel launch that
+ * drains a device ready queue through atomic dependency counters.  Updates that
+ * fall outside S are discarded.  Blocks until the stream has finished the launch.
+ *   values  device, nnz(A) doubles in A's CSR order.
+ *   breakdown_row  host out (may be NULL): -1, or the smallest row (permuted order)
+ *                  whose pivot was <= 0 or not finite (then IC_ERR_BREAKDOWN).
+ * Errors: IC_ERR_ARG, IC_ERR_BREAKDOWN, IC_ERR_TIMEOUT, IC_ERR_CUDA. */
+int ic_numeric(ic_handle* h, const void* values, void* stream, int64_t* breakdown_row);
+
+/* Preconditioner application z = (L L^T)^{-1} r = P (U^T U)^{-1} P^T r: forward then
+ * backward triangular solves on the device (the use of Section 1; the paper does not
+ * describe the solves).  r and z are device vectors of n doubles in the ORIGINAL
+ * ordering; they may not alias.  Asynchronous on stream.  The solves share the
+ * handle's work vector and completion stamps, so calls on one handle must not overlap
+ * on the GPU (issue them on one stream).  Their row dependences are acyclic, so the
+ * bounded waits can only expire if the GPU stops the kernel for longer than
+ * opts.timeout_s; z is then undefined and the next pcg_solve reports IC_ERR_TIMEOUT.
+ * Errors: IC_ERR_ARG, IC_ERR_STATE (no successful ic_numeric yet), IC_ERR_CUDA. */
+int ic_apply(ic_handle* h, const void* r, void* z, void* stream);
+
+/* Preconditioned conjugate gradients on A x = b with M = L L^T (textbook PCG, x0 = 0,
+ * stop when ||r||_2 / ||b||_2 <= tol).  A's pattern is the one given to ic_symbolic.
+ *   A_vals  device, nnz(A) doubles in A's CSR order.
+ *   b, x    device, n doubles, original ordering; x is overwritten.
+ *   iters, relres  host out (may be NULL): iterations done and the final recursive
+ *                  relative residual.
+ * Errors: IC_ERR_ARG, IC_ERR_STATE, IC_ERR_NOCONV (x holds the last iterate), IC_ERR_CUDA. */
+int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, double tol, int maxit,
+              int* iters, double* relres, void* stream);
+
+/* Host copy of L = U^T in lower CSR, permuted order, rows sorted, diagonal last.
+ * rowptr (n+1), colind and vals (nnz_l) are host buffers; any may be NULL to skip.
+ * levels (host, nnz_l int32 or NULL) receives each entry's level of fill.
+ * vals require a successful ic_numeric.
+ * Errors: IC_ERR_ARG, IC_ERR_STATE, IC_ERR_CUDA. */
+int ic_get_factor(ic_handle* h, int64_t* rowptr, int32_t* colind, double* vals, int32_t* levels);
+
+/* Sizes, flop and byte counts and DAG statistics of the handle. */
+int ic_stats(const ic_handle* h, ic_stats_t* out);
+
+/* Task list of the handle in generation order (the loop of Section 3.3's task
+ * generator figure).  type: 0 Chol, 1 Trsm, 2 Herk, 3 Gemm; (tk, ti, tj) block
+ * indices: Chol (k,k,k), Trsm (k,k,j), Herk (k,i,i), Gemm (k,i,j).  pred_ptr
+ * (ntasks+1) and pred list the distinct predecessors.  Call with NULL arrays to get
+ * *ntasks and *npred, then again with buffers of at least those sizes.
+ * Errors: IC_ERR_ARG. */
+int ic_get_tasks(const ic_handle* h, int32_t* type, int32_t* tk, int32_t* ti, int32_t* tj,
+                 int64_t* pred_ptr, int32_t* pred, int64_t* ntasks, int64_t* npred);
+
+/* The same task generator on a bare block pattern: nb block rows, block pattern in
+ * upper CSR (bptr: nb+1, bcol sorted, each row containing its diagonal block).
+ * Same outputs and two-call protocol as ic_get_tasks.
+ * Errors: IC_ERR_ARG, IC_ERR_PATTERN. */
+int ic_block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, int32_t* type, int32_t* tk,
+                 int32_t* ti, int32_t* tj, int64_t* pred_ptr, int32_t* pred, int64_t* ntasks,
+                 int64_t* npred);
+
+/* Work-item targets of one task, for inspection: for each target row r of task t,
+ * (r, first and one-past-last index into the column lists of U, first and
+ * one-past-last position of the target segment in U).  Two-call protocol on *count.
+ * Also returns (when not NULL) U's upper pattern and column lists:
+ * urp (n+1), ucol (nnz_l), cptr (n+1), cp (nnz_l - n: pivot row p of each entry),
+ * cpos (nnz_l - n: position of U_pr).
+ * Errors: IC_ERR_ARG. */
+int ic_get_task_targets(const ic_handle* h, int64_t t, int32_t* tgt5, int64_t* count);
+int ic_get_upper(const ic_handle* h, int64_t* urp, int32_t* ucol, int64_t* cptr, int32_t* cp,
+                 int32_t* cpos);
+
+/* The 2D block matrix of the handle (Section 3.2): ranges (nranges+1 row boundaries
+ * after splitting to at most block_rows rows) and the upper block pattern bptr
+ * (nranges+1), bcol (nblocks; diagonal block first in each block row).  Sizes come
+ * from ic_stats.  Errors: IC_ERR_ARG. */
+int ic_get_blocks(const ic_handle* h, int64_t* ranges, int64_t* bptr, int32_t* bcol);
+
+/* Kernel timing of the handle's calls, from CUDA events recorded on the launching
+ * stream while timing is on (ic_set_timing(h, 1); it adds no synchronisation beyond
+ * what the calls already do).  launches counts the library's own kernel launches
+ * since the last ic_reset_timing. */
+typedef struct {
+    double prepare_ms;     /* value scatter + scheduler reset of the last ic_numeric       */
+    double numeric_ms;     /* persistent task-DAG kernel of the last ic_numeric            */
+    double apply_ms;       /* triangular-solve kernels, summed since the last reset        */
+    int64_t apply_calls;   /* ic_apply calls (direct or inside pcg_solve) since the reset  */
+    int64_t launches;      /* kernels launched by the library since the reset              */
+} ic_timing_t;
+int ic_set_timing(ic_handle* h, int on);
+int ic_reset_timing(ic_handle* h);
+int ic_get_timing(const ic_handle* h, ic_timing_t* out);
+
+/* Fault injection for tests, done on the host: adds `extra` to task t's initial
+ * in-degree, so with extra = 1 the task is never released and the next ic_numeric
+ * ends in IC_ERR_TIMEOUT once opts.timeout_s has passed (every device wait is
+ * bounded; nothing traps).  extra = 0 restores the plan.  Errors: IC_ERR_ARG, IC_ERR_CUDA. */
+int ic_test_hold_task(ic_handle* h, int64_t t, int extra);
+
+void ic_destroy(ic_handle* h);
+
+/* Static English text for a status code. */
+const char* ic_strerror(int status);
+
+/* Detail text of the last failing call made by the calling thread ("" if none).
+ * Valid until that thread's next failing call. */
+const char* ic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICK_H */

@@ -1,0 +1,644 @@
+// C ABI of libick.so (declared in include/ick.h): handle life cycle, device upload of
+// the symbolic plan, and the host orchestration of the numeric, apply and PCG kernels.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ick_internal.h"
+
+using namespace ick;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return IC_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct ic_handle {
+    HostPlan hp;
+    ic_opts opts{};
+    int device = -1;
+    std::vector<void*> allocs;
+    DevPlan dp{};
+    SolvePlan sp{};
+    int grid_numeric = 0;
+    int grid_apply = 0;
+    int epoch = 0;
+    int apply_epoch = 0;
+    bool factored = false;
+    double symbolic_s = 0.0;
+    // pinned host mirrors of small device status words
+    int* h_counters = nullptr;      // counters[0..3], diag[0..1]
+    long long* h_brk = nullptr;
+    PcgScalars* h_sc = nullptr;
+    // PCG scratch
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *partial = nullptr;
+    PcgScalars* sc = nullptr;
+    // timing (ic_set_timing)
+    bool timing = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool apply_pending = false;  // ev[3]..ev[4] bracket an apply not yet added to tm
+    ic_timing_t tm{};
+
+    ~ic_handle() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        for (void* a : allocs) cudaFree(a);
+        if (h_counters) cudaFreeHost(h_counters);
+        if (h_brk) cudaFreeHost(h_brk);
+        if (h_sc) cudaFreeHost(h_sc);
+    }
+
+    template <class T>
+    int alloc(T** out, size_t count) {
+        void* d = nullptr;
+        cudaError_t e = cudaMalloc(&d, count ? count * sizeof(T) : 16);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        allocs.push_back(d);
+        *out = static_cast<T*>(d);
+        return IC_OK;
+    }
+
+    template <class T>
+    int upload(const T** out, const std::vector<T>& v) {
+        T* d = nullptr;
+        int st = alloc(&d, v.size());
+        if (st) return st;
+        if (!v.empty()) {
+            cudaError_t e = cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+        }
+        *out = d;
+        return IC_OK;
+    }
+};
+
+namespace {
+
+ic_opts normalise(const ic_opts* o) {
+    ic_opts r{};
+    if (o) r = *o;
+    if (r.block_rows == 0) r.block_rows = 4096;
+    if (r.warps_per_cta == 0) r.warps_per_cta = 16;
+    if (r.rows_per_item == 0) r.rows_per_item = 32;
+    if (r.timeout_s == 0.0) r.timeout_s = 10.0;
+    return r;
+}
+
+int upload_plan(ic_handle* h) {
+    HostPlan& P = h->hp;
+    DevPlan& D = h->dp;
+    int st = 0;
+    D.n = int(P.n);
+    D.nnz_u = int(P.nnz_u);
+    D.nb = int(P.ranges.size()) - 1;
+    D.ntasks = int(P.task.size());
+    D.total_items = int(P.total_items);
+    D.nseeds = int(P.seeds.size());
+    D.rows_per_item = P.rows_per_item;
+    {
+        const int64_t* dptr = nullptr;
+        if ((st = h->upload(&dptr, P.urp))) return st;
+        D.urp = reinterpret_cast<const long long*>(dptr);
+    }
+    if ((st = h->upload(&D.ucol, P.ucol))) return st;
+    if ((st = h->upload(&D.gsrc, P.gsrc))) return st;
+    if ((st = h->upload(&D.ranges, P.ranges))) return st;
+    if ((st = h->upload(&D.rseg_ptr, P.rseg_ptr))) return st;
+    if ((st = h->upload(&D.rseg_blk, P.rseg_blk))) return st;
+    if ((st = h->upload(&D.rseg_se, P.rseg_se))) return st;
+    if ((st = h->upload(&D.cptr, P.cptr))) return st;
+    if ((st = h->upload(&D.csc, P.csc))) return st;
+    if ((st = h->upload(&D.task, P.task))) return st;
+    if ((st = h->upload(&D.tgt_ptr, P.tgt_ptr))) return st;
+    if ((st = h->upload(&D.tgt, P.tgt))) return st;
+    if ((st = h->upload(&D.tgt_end, P.tgt_end))) return st;
+    if ((st = h->upload(&D.nitems, P.nitems))) return st;
+    if ((st = h->upload(&D.succ_ptr, P.succ_ptr))) return st;
+    if ((st = h->upload(&D.succ, P.succ))) return st;
+    if ((st = h->upload(&D.indeg0, P.indeg0))) return st;
+    if ((st = h->upload(&D.seeds, P.seeds))) return st;
+    double* uval = nullptr;
+    if ((st = h->alloc(&uval, size_t(P.nnz_u)))) return st;
+    D.uval = uval;
+    if ((st = h->alloc(&D.indeg, P.task.size()))) return st;
+    if ((st = h->alloc(&D.items_left, P.task.size()))) return st;
+    if ((st = h->alloc(&D.queue, size_t(P.total_items)))) return st;
+    if ((st = h->alloc(&D.qstamp, size_t(P.total_items)))) return st;
+    CK(cudaMemset(D.qstamp, 0, size_t(P.total_items) * sizeof(int)));
+    if ((st = h->alloc(&D.counters, 8))) return st;
+    if ((st = h->alloc(&D.brk_row, 1))) return st;
+    if ((st = h->alloc(&D.diag, 8))) return st;
+
+    // solve / PCG buffers
+    SolvePlan& S = h->sp;
+    S.n = int(P.n);
+    S.nnz_a = P.nnz_a;
+    S.urp = D.urp;
+    S.ucol = D.ucol;
+    S.cptr = D.cptr;
+    S.csc = D.csc;
+    S.uval = uval;
+    {
+        const int32_t* dperm = nullptr;
+        if ((st = h->upload(&dperm, P.perm))) return st;
+        S.perm = dperm;
+        const int64_t* darp = nullptr;
+        if ((st = h->upload(&darp, P.arp))) return st;
+        S.arp = reinterpret_cast<const long long*>(darp);
+        const int32_t* dacol = nullptr;
+        if ((st = h->upload(&dacol, P.acol))) return st;
+        S.acol = dacol;
+    }
+    if ((st = h->alloc(&S.y, size_t(P.n)))) return st;
+    if ((st = h->alloc(&S.flag, size_t(P.n)))) return st;
+    CK(cudaMemset(S.flag, 0, size_t(P.n) * sizeof(int)));
+    if ((st = h->alloc(&S.counter, 4))) return st;
+    CK(cudaMemset(S.counter, 0, 4 * sizeof(int)));
+    if ((st = h->alloc(&h->r, size_t(P.n)))) return st;
+    if ((st = h->alloc(&h->z, size_t(P.n)))) return st;
+    if ((st = h->alloc(&h->p, size_t(P.n)))) return st;
+    if ((st = h->alloc(&h->q, size_t(P.n)))) return st;
+    if ((st = h->alloc(&h->partial, size_t(kMaxParts)))) return st;
+    if ((st = h->alloc(&h->sc, 1))) return st;
+    CK(cudaMallocHost(&h->h_counters, 16 * sizeof(int)));
+    CK(cudaMallocHost(&h->h_brk, sizeof(long long)));
+    CK(cudaMallocHost(&h->h_sc, sizeof(PcgScalars)));
+
+    int dev = 0, sms = 0, bpsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(numeric_blocks_per_sm(h->opts.warps_per_cta, h->opts.exact != 0, &bpsm));
+    if (bpsm < 1) return fail(IC_ERR_CUDA, "numeric kernel cannot be resident");
+    h->grid_numeric = sms * bpsm;
+    CK(apply_blocks_per_sm(&bpsm));
+    h->grid_apply = sms * (bpsm < 1 ? 1 : bpsm);
+    CK(cudaDeviceSynchronize());
+    return IC_OK;
+}
+
+// Adds the kernel time of the last apply (waiting for its end event) to the totals.
+int fold_apply_time(ic_handle* h) {
+    if (!h->apply_pending) return IC_OK;
+    CK(cudaEventSynchronize(h->ev[4]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[3], h->ev[4]));
+    h->tm.apply_ms += ms;
+    h->apply_pending = false;
+    return IC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ic_strerror(int s) {
+    switch (s) {
+        case IC_OK: return "ok";
+        case IC_ERR_ARG: return "invalid argument";
+        case IC_ERR_PATTERN: return "malformed or asymmetric CSR pattern";
+        case IC_ERR_BREAKDOWN: return "breakdown: non-positive or non-finite pivot";
+        case IC_ERR_TIMEOUT: return "device wait timed out";
+        case IC_ERR_CUDA: return "CUDA runtime error";
+        case IC_ERR_NOMEM: return "out of memory";
+        case IC_ERR_NOCONV: return "PCG did not converge";
+        case IC_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* ic_last_error(void) { return g_last_error.c_str(); }
+
+int ic_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep,
+               int32_t* perm_out, int64_t* ranges_out, int64_t* nranges_out, int64_t* n_out) {
+    try {
+        return nd_grid(nx, ny, nz, dof, leaf_rows, keep, perm_out, ranges_out, nranges_out, n_out);
+    } catch (const std::bad_alloc&) {
+        return fail(IC_ERR_NOMEM, "host allocation failed");
+    }
+}
+
+int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
+                int64_t nranges, const ic_opts* opts, ic_handle** out) {
+    if (!out) return fail(IC_ERR_ARG, "NULL out");
+    *out = nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
+    ic_handle* h = nullptr;
+    try {
+        h = new ic_handle();
+        h->opts = normalise(opts);
+        if (h->opts.warps_per_cta != 8 && h->opts.warps_per_cta != 16) {
+            delete h;
+            return fail(IC_ERR_ARG, "warps_per_cta must be 8 or 16");
+        }
+        if (h->opts.dtype != IC_F64) {
+            delete h;
+            return fail(IC_ERR_ARG, "dtype: only IC_F64 is available");
+        }
+        if (h->opts.rows_per_item < 1 || h->opts.timeout_s < 0) {
+            delete h;
+            return fail(IC_ERR_ARG, "rows_per_item / timeout_s out of range");
+        }
+        std::string err;
+        int st = build_plan(A, k, perm, ranges, nranges, h->opts.block_rows, h->opts.rows_per_item,
+                            h->opts.threads, h->hp, err);
+        if (st) {
+            delete h;
+            return fail(st, err);
+        }
+        if (h->opts.host_only) {
+            h->symbolic_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            *out = h;
+            return IC_OK;
+        }
+        cudaError_t e = cudaGetDevice(&h->device);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "cudaGetDevice");
+        }
+        st = upload_plan(h);
+        if (st) {
+            delete h;
+            return st;
+        }
+    } catch (const std::bad_alloc&) {
+        delete h;
+        return fail(IC_ERR_NOMEM, "host allocation failed");
+    }
+    h->symbolic_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return IC_OK;
+}
+
+int ic_numeric(ic_handle* h, const void* values, void* stream, int64_t* breakdown_row) {
+    if (breakdown_row) *breakdown_row = -1;
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    if (!values && h->hp.nnz_a > 0) return fail(IC_ERR_ARG, "NULL values");
+    if (h->opts.host_only) return fail(IC_ERR_STATE, "handle was created with host_only");
+    DeviceGuard g(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->factored = false;
+    const int epoch = ++h->epoch;
+    const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
+    if (h->timing) CK(cudaEventRecord(h->ev[0], s));
+    CK(launch_numeric_prepare(h->dp, static_cast<const double*>(values), h->opts.shift_alpha, epoch, s));
+    ++h->tm.launches;
+    if (h->timing) CK(cudaEventRecord(h->ev[1], s));
+    if (h->dp.total_items > 0) {
+        CK(launch_numeric(h->dp, epoch, h->opts.warps_per_cta, h->opts.exact != 0, h->grid_numeric,
+                          tmo, s));
+        ++h->tm.launches;
+    }
+    if (h->timing) CK(cudaEventRecord(h->ev[2], s));
+    CK(cudaMemcpyAsync(h->h_counters, h->dp.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->h_counters + 4, h->dp.diag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->h_brk, h->dp.brk_row, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->timing) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+        CK(cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
+        h->tm.prepare_ms = a;
+        h->tm.numeric_ms = b;
+    }
+    const int bits = h->h_counters[2];
+    if (bits & kStTimeout)
+        return fail(IC_ERR_TIMEOUT, "numeric: device wait timed out at site " + std::to_string(h->h_counters[5]));
+    if (h->hp.total_items > 0 && h->h_counters[4] != h->hp.total_items)
+        return fail(IC_ERR_TIMEOUT, "numeric: " + std::to_string(h->h_counters[4]) + " of " +
+                                        std::to_string(h->hp.total_items) + " items completed");
+    if (bits & kStBreakdown) {
+        if (breakdown_row) *breakdown_row = h->h_brk[0];
+        return fail(IC_ERR_BREAKDOWN, "breakdown at row " + std::to_string(h->h_brk[0]));
+    }
+    h->factored = true;
+    return IC_OK;
+}
+
+int ic_apply(ic_handle* h, const void* r, void* z, void* stream) {
+    if (!h || ((!r || !z) && h->hp.n > 0)) return fail(IC_ERR_ARG, "NULL argument");
+    if (r == z && h->hp.n > 0) return fail(IC_ERR_ARG, "r and z may not alias");
+    if (!h->factored) return fail(IC_ERR_STATE, "ic_apply before a successful ic_numeric");
+    if (h->hp.n == 0) return IC_OK;
+    DeviceGuard g(h->device);
+    const int epoch = ++h->apply_epoch;
+    const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (h->timing) {
+        int st = fold_apply_time(h);
+        if (st) return st;
+        CK(cudaEventRecord(h->ev[3], s));
+    }
+    CK(launch_apply(h->sp, static_cast<const double*>(r), static_cast<double*>(z), epoch, tmo,
+                    h->grid_apply, s));
+    h->tm.launches += 2;
+    ++h->tm.apply_calls;
+    if (h->timing) {
+        CK(cudaEventRecord(h->ev[4], s));
+        h->apply_pending = true;
+    }
+    return IC_OK;
+}
+
+int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, double tol, int maxit,
+              int* iters, double* relres, void* stream) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    const int n = int(h->hp.n);
+    if (n > 0 && (!A_vals || !b || !x)) return fail(IC_ERR_ARG, "NULL argument");
+    if (!(tol >= 0.0) || maxit < 0) return fail(IC_ERR_ARG, "tol/maxit out of range");
+    if (!h->factored) return fail(IC_ERR_STATE, "pcg_solve before a successful ic_numeric");
+    if (n == 0) return IC_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double* av = static_cast<const double*>(A_vals);
+    const int parts = pcg_parts(n);
+    int st = 0;
+    int64_t& nl = h->tm.launches;
+    CK(cudaMemsetAsync(h->sp.counter + 2, 0, sizeof(int), s));  // solve abort word
+    ++nl;
+    CK(pcg_init(n, b, x, h->r, s));
+    ++nl;
+    CK(pcg_dot(b, b, n, h->partial, parts, s));
+    ++nl;
+    CK(pcg_finish(h->partial, parts, h->sc, 4, s));
+    if ((st = ic_apply(h, h->r, h->z, s))) return st;
+    CK(cudaMemcpyAsync(h->p, h->z, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    ++nl;
+    CK(pcg_dot(h->r, h->z, n, h->partial, parts, s));
+    ++nl;
+    CK(pcg_finish(h->partial, parts, h->sc, 3, s));
+    ++nl;
+    CK(pcg_dot(h->r, h->r, n, h->partial, parts, s));
+    ++nl;
+    CK(pcg_finish(h->partial, parts, h->sc, 1, s));
+    CK(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double rel = h->h_sc->relres;
+    int it = 0;
+    while (rel > tol && it < maxit) {
+        ++nl;
+        CK(launch_spmv(h->sp, av, h->p, h->q, s));
+        ++nl;
+        CK(pcg_dot(h->p, h->q, n, h->partial, parts, s));
+        ++nl;
+        CK(pcg_finish(h->partial, parts, h->sc, 0, s));
+        ++nl;
+        CK(pcg_step_x_r(n, x, h->r, h->p, h->q, h->sc, h->partial, parts, s));
+        ++nl;
+        CK(pcg_finish(h->partial, parts, h->sc, 1, s));
+        CK(cudaMemcpyAsync(&h->h_sc->relres, &h->sc->relres, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ++it;
+        CK(cudaStreamSynchronize(s));
+        rel = h->h_sc->relres;
+        if (rel <= tol) break;
+        if ((st = ic_apply(h, h->r, h->z, s))) return st;
+        ++nl;
+        CK(pcg_dot(h->r, h->z, n, h->partial, parts, s));
+        ++nl;
+        CK(pcg_finish(h->partial, parts, h->sc, 2, s));
+        ++nl;
+        CK(pcg_step_p(n, h->p, h->z, h->sc, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    {
+        int ctr[4];
+        CK(cudaMemcpy(ctr, h->sp.counter, sizeof(ctr), cudaMemcpyDeviceToHost));
+        if (ctr[2]) return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
+    }
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    if (!(rel <= tol)) return fail(IC_ERR_NOCONV, "PCG reached maxit");
+    return IC_OK;
+}
+
+int ic_get_factor(ic_handle* h, int64_t* rowptr, int32_t* colind, double* vals, int32_t* levels) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    const HostPlan& P = h->hp;
+    const int64_t n = P.n;
+    std::vector<double> u;
+    if (vals) {
+        if (!h->factored) return fail(IC_ERR_STATE, "no successful ic_numeric");
+        DeviceGuard g(h->device);
+        u.resize(P.nnz_u);
+        CK(cudaMemcpy(u.data(), h->dp.uval, u.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    // L row i = U column i: pivots p < i in ascending order, then the diagonal
+    int64_t pos = 0;
+    if (rowptr) rowptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int32_t e = P.cptr[i]; e < P.cptr[i + 1]; ++e, ++pos) {
+            const int2 pe = P.csc[e];
+            if (colind) colind[pos] = pe.x;
+            if (vals) vals[pos] = u[pe.y];
+            if (levels) levels[pos] = P.ulev[pe.y];
+        }
+        if (colind) colind[pos] = int32_t(i);
+        if (vals) vals[pos] = u[P.urp[i]];
+        if (levels) levels[pos] = 0;
+        ++pos;
+        if (rowptr) rowptr[i + 1] = pos;
+    }
+    return IC_OK;
+}
+
+int ic_stats(const ic_handle* h, ic_stats_t* out) {
+    if (!h || !out) return fail(IC_ERR_ARG, "NULL argument");
+    const HostPlan& P = h->hp;
+    std::memset(out, 0, sizeof(*out));
+    out->n = P.n;
+    out->nnz_a = P.nnz_a;
+    out->nnz_l = P.nnz_u;
+    out->nranges = int64_t(P.ranges.size()) - 1;
+    out->nblocks = int64_t(P.bcol.size());
+    out->ntasks = int64_t(P.task.size());
+    for (int t = 0; t < 4; ++t) out->ntasks_type[t] = P.ntype[t];
+    out->nitems = P.total_items;
+    out->critical_path = P.critical_path;
+    out->max_level = P.max_level;
+    out->flops = P.flops;
+    out->bytes = P.bytes;
+    out->symbolic_s = h->symbolic_s;
+    out->grid_ctas = h->grid_numeric;
+    return IC_OK;
+}
+
+static int export_dag(const std::vector<int4>& task, const std::vector<int64_t>& pred_ptr,
+                      const std::vector<int32_t>& pred, int32_t* type, int32_t* tk, int32_t* ti,
+                      int32_t* tj, int64_t* pp, int32_t* pr, int64_t* ntasks, int64_t* npred) {
+    if (ntasks) *ntasks = int64_t(task.size());
+    if (npred) *npred = int64_t(pred.size());
+    for (size_t t = 0; t < task.size(); ++t) {
+        if (type) type[t] = task[t].x;
+        if (tk) tk[t] = task[t].y;
+        if (ti) ti[t] = task[t].z;
+        if (tj) tj[t] = task[t].w;
+    }
+    if (pp) std::memcpy(pp, pred_ptr.data(), pred_ptr.size() * sizeof(int64_t));
+    if (pr && !pred.empty()) std::memcpy(pr, pred.data(), pred.size() * sizeof(int32_t));
+    return IC_OK;
+}
+
+int ic_get_tasks(const ic_handle* h, int32_t* type, int32_t* tk, int32_t* ti, int32_t* tj,
+                 int64_t* pred_ptr, int32_t* pred, int64_t* ntasks, int64_t* npred) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    return export_dag(h->hp.task, h->hp.pred_ptr, h->hp.pred, type, tk, ti, tj, pred_ptr, pred,
+                      ntasks, npred);
+}
+
+int ic_block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, int32_t* type, int32_t* tk,
+                 int32_t* ti, int32_t* tj, int64_t* pred_ptr, int32_t* pred, int64_t* ntasks,
+                 int64_t* npred) {
+    std::vector<int4> task;
+    std::vector<int64_t> pp;
+    std::vector<int32_t> pr;
+    try {
+        int st = block_dag(nb, bptr, bcol, task, pp, pr);
+        if (st) return fail(st, "bad block pattern");
+    } catch (const std::bad_alloc&) {
+        return fail(IC_ERR_NOMEM, "host allocation failed");
+    }
+    return export_dag(task, pp, pr, type, tk, ti, tj, pred_ptr, pred, ntasks, npred);
+}
+
+int ic_get_task_targets(const ic_handle* h, int64_t t, int32_t* tgt5, int64_t* count) {
+    if (!h || !count) return fail(IC_ERR_ARG, "NULL argument");
+    const HostPlan& P = h->hp;
+    if (t < 0 || t >= int64_t(P.task.size())) return fail(IC_ERR_ARG, "task out of range");
+    const int32_t a = P.tgt_ptr[t], b = P.tgt_ptr[t + 1];
+    *count = b - a;
+    if (tgt5)
+        for (int32_t e = a; e < b; ++e) {
+            int32_t* o = tgt5 + 5 * (e - a);
+            o[0] = P.tgt[e].x;
+            o[1] = P.tgt[e].y;
+            o[2] = P.tgt[e].z;
+            o[3] = P.tgt[e].w;
+            o[4] = P.tgt_end[e];
+        }
+    return IC_OK;
+}
+
+int ic_get_upper(const ic_handle* h, int64_t* urp, int32_t* ucol, int64_t* cptr, int32_t* cp,
+                 int32_t* cpos) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    const HostPlan& P = h->hp;
+    if (urp) std::memcpy(urp, P.urp.data(), P.urp.size() * sizeof(int64_t));
+    if (ucol && P.nnz_u) std::memcpy(ucol, P.ucol.data(), P.ucol.size() * sizeof(int32_t));
+    if (cptr)
+        for (size_t i = 0; i < P.cptr.size(); ++i) cptr[i] = P.cptr[i];
+    for (size_t e = 0; e < P.csc.size(); ++e) {
+        if (cp) cp[e] = P.csc[e].x;
+        if (cpos) cpos[e] = P.csc[e].y;
+    }
+    return IC_OK;
+}
+
+int ic_get_blocks(const ic_handle* h, int64_t* ranges, int64_t* bptr, int32_t* bcol) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    const HostPlan& P = h->hp;
+    if (ranges)
+        for (size_t b = 0; b < P.ranges.size(); ++b) ranges[b] = P.ranges[b];
+    if (bptr) std::memcpy(bptr, P.bptr.data(), P.bptr.size() * sizeof(int64_t));
+    if (bcol && !P.bcol.empty()) std::memcpy(bcol, P.bcol.data(), P.bcol.size() * sizeof(int32_t));
+    return IC_OK;
+}
+
+int ic_set_timing(ic_handle* h, int on) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    if (h->device < 0) return fail(IC_ERR_STATE, "host-only handle");
+    DeviceGuard g(h->device);
+    if (on && !h->ev[0])
+        for (cudaEvent_t& e : h->ev) CK(cudaEventCreate(&e));
+    h->timing = on != 0;
+    return IC_OK;
+}
+
+int ic_reset_timing(ic_handle* h) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    if (h->timing) {
+        int st = fold_apply_time(h);
+        if (st) return st;
+    }
+    h->tm = ic_timing_t{};
+    return IC_OK;
+}
+
+int ic_get_timing(const ic_handle* hc, ic_timing_t* out) {
+    if (!hc || !out) return fail(IC_ERR_ARG, "NULL argument");
+    ic_handle* h = const_cast<ic_handle*>(hc);
+    if (h->timing) {
+        DeviceGuard g(h->device);
+        int st = fold_apply_time(h);
+        if (st) return st;
+    }
+    *out = h->tm;
+    return IC_OK;
+}
+
+int ic_test_hold_task(ic_handle* h, int64_t t, int extra) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    if (h->device < 0) return fail(IC_ERR_STATE, "host-only handle");
+    if (t < 0 || t >= int64_t(h->hp.task.size()) || extra < 0) return fail(IC_ERR_ARG, "task out of range");
+    DeviceGuard g(h->device);
+    const int v = h->hp.indeg0[t] + extra;
+    CK(cudaMemcpy(const_cast<int*>(h->dp.indeg0) + t, &v, sizeof(int), cudaMemcpyHostToDevice));
+    // a held task that had no predecessor must also leave the seed list
+    int nseed = 0;
+    std::vector<int2> seeds;
+    for (size_t u = 0; u < h->hp.task.size(); ++u) {
+        const int deg = (int64_t(u) == t) ? v : h->hp.indeg0[u];
+        if (deg == 0)
+            for (int c = 0; c < h->hp.nitems[u]; ++c) seeds.push_back(make_int2(int(u), c));
+    }
+    nseed = int(seeds.size());
+    if (!seeds.empty())
+        CK(cudaMemcpy(const_cast<int2*>(h->dp.seeds), seeds.data(), seeds.size() * sizeof(int2),
+                      cudaMemcpyHostToDevice));
+    h->dp.nseeds = nseed;
+    return IC_OK;
+}
+
+void ic_destroy(ic_handle* h) {
+    if (!h) return;
+    if (h->device >= 0) {
+        DeviceGuard g(h->device);
+        delete h;
+    } else {
+        delete h;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,558 @@
+// Host side of the symbolic phase (Algorithm 1 of Section 3.1, Sections 3.2-3.3):
+// geometric nested dissection, the level-k fill pattern by per-row breadth-first
+// search, the 2D sparse partitioned-block matrix, the Cholesky-by-blocks task DAG
+// and the per-task work lists the persistent numeric kernel consumes.
+#include <omp.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "ick_internal.h"
+
+namespace ick {
+
+// --------------------------------------------------------------------------- ND
+
+namespace {
+
+struct NdCtx {
+    int nx, ny, nz, dof, leaf_rows;
+    const uint8_t* keep;
+    const int64_t* kept_index;  // grid dof -> index among kept dofs, -1 if dropped
+    int32_t* perm;
+    int64_t next;
+    int64_t* ranges;
+    int64_t nranges;
+};
+
+int64_t count_rows(const NdCtx& c, const int lo[3], const int hi[3]) {
+    int64_t nodes = int64_t(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+    if (!c.keep) return nodes * c.dof;
+    int64_t cnt = 0;
+    for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y)
+            for (int x = lo[0]; x < hi[0]; ++x) {
+                int64_t base = (x + int64_t(c.nx) * (y + int64_t(c.ny) * z)) * c.dof;
+                for (int d = 0; d < c.dof; ++d) cnt += c.keep[base + d] != 0;
+            }
+    return cnt;
+}
+
+void number_part(NdCtx& c, const int lo[3], const int hi[3]) {
+    const int64_t first = c.next;
+    for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y)
+            for (int x = lo[0]; x < hi[0]; ++x) {
+                int64_t base = (x + int64_t(c.nx) * (y + int64_t(c.ny) * z)) * c.dof;
+                for (int d = 0; d < c.dof; ++d) {
+                    int64_t idx = c.kept_index[base + d];
+                    if (idx >= 0) c.perm[c.next++] = int32_t(idx);
+                }
+            }
+    if (c.next > first) {
+        ++c.nranges;
+        if (c.ranges) c.ranges[c.nranges] = c.next;
+    }
+}
+
+// Iterative ND over boxes: each stack frame is a box, or a plane to be numbered
+// after its two halves (post-order: low, high, separator).
+void dissect(NdCtx& c) {
+    struct Frame { int lo[3], hi[3]; bool plane; };
+    std::vector<Frame> st;
+    st.push_back({{0, 0, 0}, {c.nx, c.ny, c.nz}, false});
+    while (!st.empty()) {
+        Frame f = st.back();
+        st.pop_back();
+        if (f.hi[0] <= f.lo[0] || f.hi[1] <= f.lo[1] || f.hi[2] <= f.lo[2]) continue;
+        if (f.plane) { number_part(c, f.lo, f.hi); continue; }
+        int ext[3] = {f.hi[0] - f.lo[0], f.hi[1] - f.lo[1], f.hi[2] - f.lo[2]};
+        int ax = 0;
+        if (ext[1] > ext[ax]) ax = 1;
+        if (ext[2] > ext[ax]) ax = 2;
+        if (ext[ax] < 3 || count_rows(c, f.lo, f.hi) <= c.leaf_rows) {
+            number_part(c, f.lo, f.hi);
+            continue;
+        }
+        int m = f.lo[ax] + (f.hi[ax] - f.lo[ax]) / 2;
+        Frame low = f, high = f, sep = f;
+        low.hi[ax] = m;
+        high.lo[ax] = m + 1;
+        sep.lo[ax] = m;
+        sep.hi[ax] = m + 1;
+        sep.plane = true;
+        st.push_back(sep);   // popped last
+        st.push_back(high);
+        st.push_back(low);   // popped first
+    }
+}
+
+}  // namespace
+
+int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep, int32_t* perm,
+            int64_t* ranges, int64_t* nranges, int64_t* n_out) {
+    if (nx <= 0 || ny <= 0 || nz <= 0 || dof <= 0 || leaf_rows <= 0 || !perm) return IC_ERR_ARG;
+    const int64_t nfull = int64_t(nx) * ny * nz * dof;
+    if (nfull > INT32_MAX) return IC_ERR_ARG;
+    std::vector<int64_t> kept(nfull);
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < nfull; ++i) kept[i] = (!keep || keep[i]) ? cnt++ : -1;
+    NdCtx c{nx, ny, nz, dof, leaf_rows, keep, kept.data(), perm, 0, ranges, 0};
+    if (ranges) ranges[0] = 0;
+    dissect(c);
+    if (nranges) *nranges = c.nranges;
+    if (n_out) *n_out = c.next;
+    return IC_OK;
+}
+
+// --------------------------------------------------------------------------- DAG
+
+// Cholesky-by-blocks task generation (Section 3.3, task generator figure): for each
+// block column k, Chol on (k,k), Trsm on every existing (k,j), j > k, and for every
+// pair i <= j of those j an update of (i,j) if that block exists (Herk when i == j,
+// Gemm otherwise).  Each block records the last task that wrote it (its future); a
+// new task depends on the futures of the blocks it reads and writes, so updates to
+// one block are serialised in k order.
+int block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, std::vector<int4>& task,
+              std::vector<int64_t>& pred_ptr, std::vector<int32_t>& pred) {
+    task.clear();
+    pred.clear();
+    pred_ptr.assign(1, 0);
+    if (nb < 0 || (nb > 0 && (!bptr || !bcol))) return IC_ERR_ARG;
+    if (nb == 0) return IC_OK;
+    if (bptr[0] != 0) return IC_ERR_PATTERN;
+    for (int64_t b = 0; b < nb; ++b) {
+        if (bptr[b + 1] <= bptr[b]) return IC_ERR_PATTERN;
+        if (bcol[bptr[b]] != b) return IC_ERR_PATTERN;  // diagonal block first
+        for (int64_t e = bptr[b] + 1; e < bptr[b + 1]; ++e)
+            if (bcol[e] <= bcol[e - 1] || bcol[e] >= nb) return IC_ERR_PATTERN;
+    }
+    auto find = [&](int64_t i, int64_t j) -> int64_t {
+        const int32_t* b = bcol + bptr[i];
+        const int32_t* e = bcol + bptr[i + 1];
+        const int32_t* p = std::lower_bound(b, e, int32_t(j));
+        return (p != e && *p == j) ? int64_t(p - bcol) : -1;
+    };
+    std::vector<int32_t> last(bptr[nb], -1);
+    auto add = [&](int type, int k, int i, int j, std::initializer_list<int64_t> blocks) {
+        int32_t t = int32_t(task.size());
+        task.push_back(make_int4(type, k, i, j));
+        int32_t deps[3];
+        int nd = 0;
+        for (int64_t b : blocks) {
+            int32_t d = last[b];
+            if (d < 0) continue;
+            bool dup = false;
+            for (int q = 0; q < nd; ++q) dup |= deps[q] == d;
+            if (!dup) deps[nd++] = d;
+        }
+        for (int a = 1; a < nd; ++a)  // at most three entries: insertion sort
+            for (int b = a; b > 0 && deps[b - 1] > deps[b]; --b) std::swap(deps[b - 1], deps[b]);
+        for (int q = 0; q < nd; ++q) pred.push_back(deps[q]);
+        pred_ptr.push_back(int64_t(pred.size()));
+        return t;
+    };
+    for (int64_t k = 0; k < nb; ++k) {
+        const int64_t bkk = bptr[k];
+        last[bkk] = add(T_CHOL, int(k), int(k), int(k), {bkk});
+        for (int64_t e = bptr[k] + 1; e < bptr[k + 1]; ++e)
+            last[e] = add(T_TRSM, int(k), int(k), bcol[e], {bkk, e});
+        for (int64_t ei = bptr[k] + 1; ei < bptr[k + 1]; ++ei) {
+            const int64_t i = bcol[ei];
+            for (int64_t ej = ei; ej < bptr[k + 1]; ++ej) {
+                const int64_t j = bcol[ej];
+                const int64_t bij = find(i, j);
+                if (bij < 0) continue;
+                last[bij] = add(i == j ? T_HERK : T_GEMM, int(k), int(i), int(j), {ei, ej, bij});
+            }
+        }
+    }
+    return IC_OK;
+}
+
+// ----------------------------------------------------------------------- symbolic
+
+namespace {
+
+int check_pattern(const ic_csr_pattern* A, std::string& err) {
+    const int64_t n = A->n;
+    if (n < 0 || n > INT32_MAX - 1) { err = "n out of range"; return IC_ERR_ARG; }
+    if (n == 0) return IC_OK;
+    if (!A->rowptr || !A->colind) { err = "NULL rowptr/colind"; return IC_ERR_ARG; }
+    if (A->rowptr[0] != 0) { err = "rowptr[0] != 0"; return IC_ERR_PATTERN; }
+    for (int64_t i = 0; i < n; ++i)
+        if (A->rowptr[i + 1] < A->rowptr[i]) { err = "rowptr decreases"; return IC_ERR_PATTERN; }
+    const int64_t nnz = A->rowptr[n];
+    if (nnz > INT32_MAX) { err = "nnz(A) above 2^31-1"; return IC_ERR_ARG; }
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        bool diag = false;
+        for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+            int32_t c = A->colind[e];
+            if (c < 0 || c >= n) { err = "column index out of range"; return IC_ERR_PATTERN; }
+            if (e > A->rowptr[i] && c <= A->colind[e - 1]) {
+                err = "columns not strictly increasing in row " + std::to_string(i);
+                return IC_ERR_PATTERN;
+            }
+            diag |= c == i;
+            ++cnt[c + 1];
+        }
+        if (!diag) { err = "missing diagonal in row " + std::to_string(i); return IC_ERR_PATTERN; }
+    }
+    // symmetry: the transpose, built row by row, must equal the pattern itself
+    for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    for (int64_t i = 0; i < n; ++i)
+        if (cnt[i + 1] - cnt[i] != A->rowptr[i + 1] - A->rowptr[i]) {
+            err = "asymmetric pattern (row/column counts differ at " + std::to_string(i) + ")";
+            return IC_ERR_PATTERN;
+        }
+    std::vector<int32_t> trow(nnz);
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) trow[fill[A->colind[e]]++] = int32_t(i);
+    for (int64_t e = 0; e < nnz; ++e)
+        if (trow[e] != A->colind[e]) { err = "asymmetric pattern"; return IC_ERR_PATTERN; }
+    return IC_OK;
+}
+
+}  // namespace
+
+int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
+               int64_t nranges, int block_rows, int rows_per_item, int threads, HostPlan& P,
+               std::string& err) {
+    if (!A) { err = "NULL pattern"; return IC_ERR_ARG; }
+    if (k < 0) { err = "k < 0"; return IC_ERR_ARG; }
+    if (block_rows <= 0 || block_rows > kMaxBlockRows) { err = "block_rows out of range"; return IC_ERR_ARG; }
+    int st = check_pattern(A, err);
+    if (st) return st;
+    const int64_t n = A->n;
+    const int nthr = threads > 0 ? threads : omp_get_max_threads();
+    P.n = n;
+    P.k = k;
+    P.rows_per_item = rows_per_item;
+    P.nnz_a = n ? A->rowptr[n] : 0;
+    P.arp.assign(A->rowptr, A->rowptr + n + 1);
+    if (n == 0) P.arp.assign(1, 0);
+    P.acol.assign(A->colind, A->colind + P.nnz_a);
+
+    // permutation
+    P.perm.resize(n);
+    P.iperm.assign(n, -1);
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t o = perm ? perm[i] : int32_t(i);
+        if (o < 0 || o >= n || P.iperm[o] != -1) { err = "perm is not a permutation"; return IC_ERR_ARG; }
+        P.perm[i] = o;
+        P.iperm[o] = int32_t(i);
+    }
+
+    // graph of B = P^T A P without the diagonal, rows sorted; source index per edge
+    std::vector<int64_t> gptr(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t o = P.perm[i];
+        gptr[i + 1] = gptr[i] + (A->rowptr[o + 1] - A->rowptr[o] - 1);
+    }
+    std::vector<int32_t> gadj(gptr[n]);
+    std::vector<int32_t> gsrc_e(gptr[n]);
+    P.udiag_src.resize(n);
+#pragma omp parallel for num_threads(nthr) schedule(static, 4096)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t o = P.perm[i], p = gptr[i];
+        std::vector<std::pair<int32_t, int32_t>> row;
+        row.reserve(A->rowptr[o + 1] - A->rowptr[o]);
+        for (int64_t e = A->rowptr[o]; e < A->rowptr[o + 1]; ++e) {
+            if (A->colind[e] == o) { P.udiag_src[i] = int32_t(e); continue; }
+            row.emplace_back(P.iperm[A->colind[e]], int32_t(e));
+        }
+        std::sort(row.begin(), row.end());
+        for (auto& pr : row) { gadj[p] = pr.first; gsrc_e[p] = pr.second; ++p; }
+    }
+
+    // level-k pattern of U row by row: breadth-first search from i through vertices
+    // < i; a vertex j > i reached after d+1 edges is fill of level d (<= k).
+    const int64_t chunk = 1024;
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    std::vector<std::vector<int32_t>> ccol(nchunks), clev(nchunks);
+    std::vector<int32_t> rowlen(n);
+    int64_t maxlev = 0;
+#pragma omp parallel num_threads(nthr) reduction(max : maxlev)
+    {
+        std::vector<int32_t> mark(n, 0);
+        std::vector<int32_t> fr, nx;
+        std::vector<std::pair<int32_t, int32_t>> out;
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t c = 0; c < nchunks; ++c) {
+            const int64_t r0 = c * chunk, r1 = std::min(n, r0 + chunk);
+            auto& cc = ccol[c];
+            auto& cl = clev[c];
+            for (int64_t i = r0; i < r1; ++i) {
+                const int32_t stamp = int32_t(i + 1);
+                out.clear();
+                fr.clear();
+                fr.push_back(int32_t(i));
+                mark[i] = stamp;
+                for (int d = 0; d <= k && !fr.empty(); ++d) {
+                    nx.clear();
+                    for (int32_t v : fr)
+                        for (int64_t e = gptr[v]; e < gptr[v + 1]; ++e) {
+                            int32_t w = gadj[e];
+                            if (mark[w] == stamp) continue;
+                            mark[w] = stamp;
+                            if (w > i) out.emplace_back(w, d);
+                            else if (d + 1 <= k) nx.push_back(w);
+                        }
+                    std::swap(fr, nx);
+                }
+                std::sort(out.begin(), out.end());
+                cc.push_back(int32_t(i));
+                cl.push_back(0);
+                for (auto& pr : out) {
+                    cc.push_back(pr.first);
+                    cl.push_back(pr.second);
+                    if (pr.second > maxlev) maxlev = pr.second;
+                }
+                rowlen[i] = int32_t(out.size() + 1);
+            }
+        }
+    }
+    P.max_level = maxlev;
+    P.urp.assign(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) P.urp[i + 1] = P.urp[i] + rowlen[i];
+    P.nnz_u = P.urp[n];
+    if (P.nnz_u > INT32_MAX) { err = "nnz(L) above 2^31-1"; return IC_ERR_ARG; }
+    P.ucol.resize(P.nnz_u);
+    P.ulev.resize(P.nnz_u);
+#pragma omp parallel for num_threads(nthr) schedule(dynamic, 1)
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int64_t base = P.urp[c * chunk];
+        std::copy(ccol[c].begin(), ccol[c].end(), P.ucol.begin() + base);
+        std::copy(clev[c].begin(), clev[c].end(), P.ulev.begin() + base);
+        std::vector<int32_t>().swap(ccol[c]);
+        std::vector<int32_t>().swap(clev[c]);
+    }
+
+    // value gather map: U position -> index of A's value (fill: -1)
+    P.gsrc.assign(P.nnz_u, -1);
+#pragma omp parallel for num_threads(nthr) schedule(static, 4096)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t u = P.urp[i];
+        P.gsrc[u] = -2 - P.udiag_src[i];
+        ++u;
+        for (int64_t e = gptr[i]; e < gptr[i + 1]; ++e) {
+            int32_t j = gadj[e];
+            if (j < i) continue;
+            while (P.ucol[u] < j) ++u;  // every structural entry has level 0, so it is present
+            P.gsrc[u] = gsrc_e[e];
+        }
+    }
+
+    // block ranges: given ranges split into pieces of at most block_rows rows
+    P.ranges.assign(1, 0);
+    if (ranges) {
+        if (nranges < 0 || ranges[0] != 0 || ranges[nranges] != n) { err = "ranges must run from 0 to n"; return IC_ERR_ARG; }
+        for (int64_t b = 0; b < nranges; ++b) {
+            int64_t lo = ranges[b], hi = ranges[b + 1];
+            if (hi <= lo) { err = "ranges must increase"; return IC_ERR_ARG; }
+            int64_t len = hi - lo, pieces = (len + block_rows - 1) / block_rows;
+            for (int64_t q = 1; q <= pieces; ++q) P.ranges.push_back(int32_t(lo + (len * q) / pieces));
+        }
+    } else {
+        for (int64_t r = block_rows; r < n; r += block_rows) P.ranges.push_back(int32_t(r));
+        if (n > 0) P.ranges.push_back(int32_t(n));
+    }
+    const int64_t nb = int64_t(P.ranges.size()) - 1;
+    P.blk_of.resize(n);
+    for (int64_t b = 0; b < nb; ++b)
+        for (int64_t r = P.ranges[b]; r < P.ranges[b + 1]; ++r) P.blk_of[r] = int32_t(b);
+
+    // per-row block segments of U
+    P.rseg_ptr.assign(n + 1, 0);
+    for (int64_t p = 0; p < n; ++p) {
+        int32_t cnt = 0, prev = -1;
+        for (int64_t e = P.urp[p]; e < P.urp[p + 1]; ++e) {
+            int32_t b = P.blk_of[P.ucol[e]];
+            if (b != prev) { ++cnt; prev = b; }
+        }
+        P.rseg_ptr[p + 1] = P.rseg_ptr[p] + cnt;
+    }
+    P.rseg_blk.resize(P.rseg_ptr[n]);
+    P.rseg_se.resize(P.rseg_ptr[n]);
+    for (int64_t p = 0; p < n; ++p) {
+        int32_t s = P.rseg_ptr[p] - 1, prev = -1;
+        for (int64_t e = P.urp[p]; e < P.urp[p + 1]; ++e) {
+            int32_t b = P.blk_of[P.ucol[e]];
+            if (b != prev) {
+                ++s;
+                P.rseg_blk[s] = b;
+                P.rseg_se[s] = make_int2(int(e), int(e));
+                prev = b;
+            }
+            P.rseg_se[s].y = int(e + 1);
+        }
+    }
+    auto seg = [&](int64_t r, int32_t b) -> int2 {
+        for (int32_t s = P.rseg_ptr[r]; s < P.rseg_ptr[r + 1]; ++s)
+            if (P.rseg_blk[s] == b) return P.rseg_se[s];
+        return make_int2(0, 0);
+    };
+
+    // column lists of U: entries (p, pos) with p < r for every column r, ascending p
+    P.cptr.assign(n + 1, 0);
+    for (int64_t p = 0; p < n; ++p)
+        for (int64_t e = P.urp[p] + 1; e < P.urp[p + 1]; ++e) ++P.cptr[P.ucol[e] + 1];
+    for (int64_t r = 0; r < n; ++r) P.cptr[r + 1] += P.cptr[r];
+    P.csc.resize(P.cptr[n]);
+    {
+        std::vector<int32_t> fill(P.cptr.begin(), P.cptr.end() - 1);
+        for (int64_t p = 0; p < n; ++p)
+            for (int64_t e = P.urp[p] + 1; e < P.urp[p + 1]; ++e)
+                P.csc[fill[P.ucol[e]]++] = make_int2(int(p), int(e));
+    }
+
+    // block pattern: block (bi, bj), bi <= bj, exists iff S has an entry in it
+    {
+        std::vector<std::vector<int32_t>> brow(nb);
+        for (int64_t p = 0; p < n; ++p) {
+            auto& v = brow[P.blk_of[p]];
+            for (int32_t s = P.rseg_ptr[p]; s < P.rseg_ptr[p + 1]; ++s) v.push_back(P.rseg_blk[s]);
+        }
+        P.bptr.assign(nb + 1, 0);
+        P.bcol.clear();
+        for (int64_t b = 0; b < nb; ++b) {
+            auto& v = brow[b];
+            std::sort(v.begin(), v.end());
+            v.erase(std::unique(v.begin(), v.end()), v.end());
+            P.bcol.insert(P.bcol.end(), v.begin(), v.end());
+            P.bptr[b + 1] = int64_t(P.bcol.size());
+        }
+    }
+    st = block_dag(nb, P.bptr.data(), P.bcol.data(), P.task, P.pred_ptr, P.pred);
+    if (st) { err = "block DAG generation failed"; return st; }
+    const int64_t nt = int64_t(P.task.size());
+
+    // column groups: for column r, the pivots p of one block k form a contiguous run
+    // of its column list.  Diagonal-block runs are kept per row; off-diagonal runs are
+    // collected per block (k, blk(r)).
+    auto block_id = [&](int64_t i, int64_t j) -> int64_t {
+        auto b = P.bcol.begin() + P.bptr[i], e = P.bcol.begin() + P.bptr[i + 1];
+        auto it = std::lower_bound(b, e, int32_t(j));
+        return (it != e && *it == j) ? int64_t(it - P.bcol.begin()) : -1;
+    };
+    std::vector<int2> diag_run(n, make_int2(0, 0));
+    std::vector<std::vector<int4>> off_runs(P.bcol.size());  // (r, a, b, 0)
+    for (int64_t r = 0; r < n; ++r) {
+        int32_t a = P.cptr[r];
+        const int32_t e = P.cptr[r + 1];
+        diag_run[r] = make_int2(P.cptr[r], P.cptr[r]);
+        while (a < e) {
+            const int32_t kb = P.blk_of[P.csc[a].x];
+            int32_t b = a;
+            while (b < e && P.blk_of[P.csc[b].x] == kb) ++b;
+            if (kb == P.blk_of[r]) diag_run[r] = make_int2(a, b);
+            else off_runs[block_id(kb, P.blk_of[r])].push_back(make_int4(int(r), a, b, 0));
+            a = b;
+        }
+    }
+
+    // work lists of every task
+    std::vector<std::vector<int4>> ttgt(nt);
+    std::vector<std::vector<int32_t>> tend(nt);
+#pragma omp parallel for num_threads(nthr) schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        const int4 T = P.task[t];
+        auto& out = ttgt[t];
+        auto& oe = tend[t];
+        if (T.x == T_CHOL || T.x == T_TRSM) {
+            const int32_t blk = T.y, tb = (T.x == T_CHOL) ? T.y : T.w;
+            for (int64_t r = P.ranges[blk]; r < P.ranges[blk + 1]; ++r) {
+                int2 s = seg(r, tb);
+                if (s.y <= s.x) continue;
+                out.push_back(make_int4(int(r), diag_run[r].x, diag_run[r].y, s.x));
+                oe.push_back(s.y);
+            }
+        } else {
+            const int64_t bki = block_id(T.y, T.z);
+            for (const int4& run : off_runs[bki]) {
+                int2 s = seg(run.x, T.w);
+                if (s.y <= s.x) continue;
+                out.push_back(make_int4(run.x, run.y, run.z, s.x));
+                oe.push_back(s.y);
+            }
+        }
+    }
+    P.tgt_ptr.assign(nt + 1, 0);
+    for (int64_t t = 0; t < nt; ++t) P.tgt_ptr[t + 1] = P.tgt_ptr[t] + int32_t(ttgt[t].size());
+    P.tgt.resize(P.tgt_ptr[nt]);
+    P.tgt_end.resize(P.tgt_ptr[nt]);
+    for (int64_t t = 0; t < nt; ++t) {
+        std::copy(ttgt[t].begin(), ttgt[t].end(), P.tgt.begin() + P.tgt_ptr[t]);
+        std::copy(tend[t].begin(), tend[t].end(), P.tgt_end.begin() + P.tgt_ptr[t]);
+    }
+
+    // items, successors, in-degrees, seeds, critical path, type counts
+    P.nitems.resize(nt);
+    P.indeg0.resize(nt);
+    P.total_items = 0;
+    for (int k2 = 0; k2 < 4; ++k2) P.ntype[k2] = 0;
+    for (int64_t t = 0; t < nt; ++t) {
+        const int4 T = P.task[t];
+        const int32_t cnt = P.tgt_ptr[t + 1] - P.tgt_ptr[t];
+        P.nitems[t] = (T.x == T_CHOL || T.x == T_TRSM) ? 1
+                      : std::max<int32_t>(1, (cnt + rows_per_item - 1) / rows_per_item);
+        P.total_items += P.nitems[t];
+        P.indeg0[t] = int32_t(P.pred_ptr[t + 1] - P.pred_ptr[t]);
+        ++P.ntype[T.x];
+    }
+    if (P.total_items > INT32_MAX / 2) { err = "too many work items"; return IC_ERR_ARG; }
+    P.succ_ptr.assign(nt + 1, 0);
+    for (int32_t d : P.pred) ++P.succ_ptr[d + 1];
+    for (int64_t t = 0; t < nt; ++t) P.succ_ptr[t + 1] += P.succ_ptr[t];
+    P.succ.resize(P.pred.size());
+    {
+        std::vector<int32_t> fill(P.succ_ptr.begin(), P.succ_ptr.end() - 1);
+        for (int64_t t = 0; t < nt; ++t)
+            for (int64_t e = P.pred_ptr[t]; e < P.pred_ptr[t + 1]; ++e) P.succ[fill[P.pred[e]]++] = int32_t(t);
+    }
+    P.seeds.clear();
+    for (int64_t t = 0; t < nt; ++t)
+        if (P.indeg0[t] == 0)
+            for (int32_t c = 0; c < P.nitems[t]; ++c) P.seeds.push_back(make_int2(int(t), c));
+    {
+        std::vector<int64_t> depth(nt, 1);
+        int64_t best = nt ? 1 : 0;
+        for (int64_t t = 0; t < nt; ++t) {
+            for (int64_t e = P.pred_ptr[t]; e < P.pred_ptr[t + 1]; ++e)
+                depth[t] = std::max(depth[t], depth[P.pred[e]] + 1);
+            best = std::max(best, depth[t]);
+        }
+        P.critical_path = best;
+    }
+
+    // algorithmic flops: per pivot p, one sqrt, |S_p|-1 divides, and two flops for each
+    // pair (r, c), r <= c, of row p's off-diagonal columns that lands in S
+    double upd = 0.0;
+#pragma omp parallel for num_threads(nthr) schedule(dynamic, 256) reduction(+ : upd)
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t b = P.urp[p] + 1, e = P.urp[p + 1];
+        for (int64_t x = b; x < e; ++x) {
+            const int32_t r = P.ucol[x];
+            // |{c in row p, c >= r} intersect row r|
+            int64_t a1 = x, a2 = P.urp[r], cnt = 0;
+            const int64_t e2 = P.urp[r + 1];
+            while (a1 < e && a2 < e2) {
+                if (P.ucol[a1] < P.ucol[a2]) ++a1;
+                else if (P.ucol[a1] > P.ucol[a2]) ++a2;
+                else { ++cnt; ++a1; ++a2; }
+            }
+            upd += double(cnt);
+        }
+    }
+    P.flops = double(n) + double(P.nnz_u - n) + 2.0 * upd;
+    // compulsory bytes: read the lower triangle of A (values and column indices),
+    // write L (values and column indices) and its row pointers
+    const double nnz_low = double(P.nnz_a + n) / 2.0;
+    P.bytes = nnz_low * (8 + 4) + double(P.nnz_u) * (8 + 4) + double(n + 1) * 8;
+    return IC_OK;
+}
+
+}  // namespace ick

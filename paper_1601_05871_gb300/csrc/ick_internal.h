@@ -1,0 +1,156 @@
+// Internal declarations shared by the host C++ (symbolic phase, C ABI) and the CUDA
+// kernels of libick.so.  Not part of the public interface (include/ick.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ick.h"
+
+namespace ick {
+
+// Block task types of the Cholesky-by-blocks generator (Section 3.3).
+enum TaskType : int { T_CHOL = 0, T_TRSM = 1, T_HERK = 2, T_GEMM = 3 };
+
+constexpr int kMaxBlockRows = 8192;  // per-row completion flags of one block live in shared memory
+constexpr int kSegCap = 128;         // target-segment entries staged per warp in shared memory
+
+// Everything the symbolic phase produces, in host memory.
+struct HostPlan {
+    int64_t n = 0, nnz_a = 0, nnz_u = 0;
+    int k = 0;
+    std::vector<int32_t> perm, iperm;
+    std::vector<int64_t> arp;       // A pattern (original order), for SpMV in PCG
+    std::vector<int32_t> acol;
+    // U = L^T, upper CSR in permuted order, diagonal first in every row
+    std::vector<int64_t> urp;
+    std::vector<int32_t> ucol;
+    std::vector<int32_t> ulev;      // level of fill of each entry
+    std::vector<int32_t> gsrc;      // per U position: A value index; -1 fill; -2-idx diagonal
+    std::vector<int32_t> udiag_src; // per row: index of A's diagonal entry
+    // 2D block matrix: block ranges and per-row block segments
+    std::vector<int32_t> ranges;    // nb + 1 boundaries
+    std::vector<int32_t> blk_of;    // block of each row
+    std::vector<int32_t> rseg_ptr;  // n + 1
+    std::vector<int32_t> rseg_blk;  // block column of each segment
+    std::vector<int2> rseg_se;      // [begin, end) positions of each segment in U
+    // column lists of U (strictly upper): for column r, pivot rows p < r ascending
+    std::vector<int32_t> cptr;      // n + 1
+    std::vector<int2> csc;          // (p, position of U_pr)
+    // block pattern (upper), bptr: nb + 1
+    std::vector<int64_t> bptr;
+    std::vector<int32_t> bcol;
+    // tasks in generation order
+    std::vector<int4> task;         // (type, k, i, j)
+    std::vector<int64_t> pred_ptr;
+    std::vector<int32_t> pred;
+    std::vector<int32_t> succ_ptr, succ;
+    std::vector<int32_t> indeg0, nitems;
+    std::vector<int32_t> tgt_ptr;   // ntasks + 1
+    std::vector<int4> tgt;          // (r, csc_a, csc_b, seg_begin)
+    std::vector<int32_t> tgt_end;   // seg_end
+    std::vector<int2> seeds;        // (task, chunk) items ready at start
+    int64_t total_items = 0;
+    int64_t critical_path = 0;
+    int64_t max_level = 0;
+    int64_t ntype[4] = {0, 0, 0, 0};
+    double flops = 0.0, bytes = 0.0;
+    int rows_per_item = 32;
+};
+
+// Plain pointers handed to the kernels by value.
+struct DevPlan {
+    int n, nnz_u, nb, ntasks, total_items, nseeds, rows_per_item;
+    const long long* urp;
+    const int* ucol;
+    const int* gsrc;
+    const int* ranges;
+    const int* rseg_ptr;
+    const int* rseg_blk;
+    const int2* rseg_se;
+    const int* cptr;
+    const int2* csc;
+    const int4* task;
+    const int* tgt_ptr;
+    const int4* tgt;
+    const int* tgt_end;
+    const int* nitems;
+    const int* succ_ptr;
+    const int* succ;
+    const int* indeg0;
+    const int2* seeds;
+    // mutable state
+    void* uval;            // factor values (double for IC_F64)
+    int* indeg;
+    int* items_left;
+    int2* queue;
+    int* qstamp;
+    int* counters;         // [0] queue head, [1] queue tail, [2] status bits, [3] abort
+    long long* brk_row;    // smallest breakdown row
+    int* diag;             // [0] items completed, [1] timeout site
+};
+
+// Status bits written by the kernels into counters[2].
+constexpr int kStBreakdown = 1;
+constexpr int kStTimeout = 2;
+
+// Device-side buffers of the triangular solves and PCG.
+struct SolvePlan {
+    int n;
+    long long nnz_a;
+    const long long* urp;
+    const int* ucol;
+    const int* cptr;
+    const int2* csc;
+    const double* uval;
+    const int* perm;
+    const long long* arp;
+    const int* acol;
+    double* y;       // permuted work vector
+    int* flag;       // per-row completion stamps of the solves
+    int* counter;    // [0] forward row claim, [1] backward row claim, [2] abort/timeout
+};
+
+// Kernel entry points (numeric.cu, solve.cu).
+cudaError_t launch_numeric_prepare(const DevPlan& P, const double* avals, double shift_alpha,
+                                   int epoch, cudaStream_t s);
+cudaError_t launch_numeric(const DevPlan& P, int epoch, int warps, bool exact, int grid,
+                           unsigned long long timeout_ns, cudaStream_t s);
+cudaError_t numeric_blocks_per_sm(int warps, bool exact, int* blocks);
+
+cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epoch,
+                         unsigned long long timeout_ns, int grid, cudaStream_t s);
+cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, double* y,
+                        cudaStream_t s);
+cudaError_t apply_blocks_per_sm(int* blocks);
+
+// PCG vector kernels (solve.cu): scalars live in a small device struct.  Reductions
+// are two-stage and deterministic: nparts block partials, then one block sums them in
+// a fixed order and applies `op` (0: alpha = rz/pq, 1: relres = sqrt(rr)/|b|,
+// 2: beta = rz_new/rz and rz = rz_new, 3: rz, 4: |b|).
+struct PcgScalars {
+    double rz, rz_new, pq, rr, bnorm, alpha, beta, relres;
+};
+constexpr int kMaxParts = 1024;
+int pcg_parts(int n);
+cudaError_t pcg_dot(const double* a, const double* b, int n, double* partial, int nparts,
+                    cudaStream_t s);
+cudaError_t pcg_finish(const double* partial, int nparts, PcgScalars* sc, int op, cudaStream_t s);
+cudaError_t pcg_step_x_r(int n, double* x, double* r, const double* p, const double* q,
+                         PcgScalars* sc, double* partial, int nparts, cudaStream_t s);
+cudaError_t pcg_step_p(int n, double* p, const double* z, PcgScalars* sc, cudaStream_t s);
+cudaError_t pcg_init(int n, const double* b, double* x, double* r, cudaStream_t s);
+
+// Host symbolic phase (host.cpp).
+int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
+               int64_t nranges, int block_rows, int rows_per_item, int threads, HostPlan& P,
+               std::string& err);
+int block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, std::vector<int4>& task,
+              std::vector<int64_t>& pred_ptr, std::vector<int32_t>& pred);
+int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep, int32_t* perm,
+            int64_t* ranges, int64_t* nranges, int64_t* n_out);
+
+}  // namespace ick

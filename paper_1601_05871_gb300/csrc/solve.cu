@@ -1,0 +1,272 @@
+// Preconditioner application and PCG on sm_103a (the use of IC(k) named in Section 1;
+// the paper does not describe the solves, so they follow the textbook definitions).
+//
+// ic_apply: z = P (U^T U)^{-1} P^T r.  The forward solve U^T y = P^T r gathers column i
+// of U (the column lists built by the symbolic phase); the backward solve U z = y
+// gathers row i of U.  Both are synchronisation-free: warps claim rows in dependency
+// order from an atomic counter (ascending for the forward solve, descending for the
+// backward one) and spin, with a bounded wait, on per-row completion stamps of the
+// rows they depend on.  Because claims are ordered, the lowest unfinished claimed row
+// always has its inputs and no warp waits on a row that no running warp owns.
+#include <cstdint>
+
+#include "ick_internal.h"
+
+namespace ick {
+namespace {
+
+constexpr int kApplyThreads = 256;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Spin until flag[i] == want; false on timeout or abort.
+__device__ __forceinline__ bool wait_flag(const int* flag, int i, int want, int* abort_word,
+                                          unsigned long long deadline) {
+    const volatile int* f = flag + i;
+    unsigned spins = 0;
+    while (*f != want) {
+        if ((++spins & 255) == 0) {
+            if (*(volatile int*)abort_word) return false;
+            if (gtimer() > deadline) { atomicExch(abort_word, 1); return false; }
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kApplyThreads)
+forward_solve(SolvePlan S, const double* __restrict__ r, int stamp, unsigned long long timeout_ns) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long deadline = gtimer() + timeout_ns;
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = atomicAdd(S.counter + 0, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= S.n) break;
+        const int a = __ldg(S.cptr + i), b = __ldg(S.cptr + i + 1);
+        double acc = 0.0;
+        bool ok = true;
+        for (int e = a + lane; e < b; e += 32) {
+            const int2 pe = __ldg(S.csc + e);
+            ok = ok && wait_flag(S.flag, pe.x, stamp, S.counter + 2, deadline);
+            acc = fma(__ldg(S.uval + pe.y), __ldcg(S.y + pe.x), acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double v = (__ldg(r + __ldg(S.perm + i)) - acc) / __ldg(S.uval + __ldg(S.urp + i));
+            S.y[i] = v;
+            __threadfence();
+            *(volatile int*)(S.flag + i) = stamp;
+        }
+        if (__any_sync(0xffffffffu, !ok)) break;
+    }
+}
+
+__global__ void __launch_bounds__(kApplyThreads)
+backward_solve(SolvePlan S, double* __restrict__ z, int stamp, unsigned long long timeout_ns) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long deadline = gtimer() + timeout_ns;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(S.counter + 1, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        const int i = S.n - 1 - t;
+        if (i < 0) break;
+        const long long a = __ldg(S.urp + i), b = __ldg(S.urp + i + 1);
+        double acc = 0.0;
+        bool ok = true;
+        for (long long e = a + 1 + lane; e < b; e += 32) {
+            const int c = __ldg(S.ucol + e);
+            ok = ok && wait_flag(S.flag, c, stamp, S.counter + 2, deadline);
+            acc = fma(__ldg(S.uval + e), __ldcg(S.y + c), acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double v = (__ldcg(S.y + i) - acc) / __ldg(S.uval + a);
+            S.y[i] = v;
+            z[__ldg(S.perm + i)] = v;
+            __threadfence();
+            *(volatile int*)(S.flag + i) = stamp;
+        }
+        if (__any_sync(0xffffffffu, !ok)) break;
+    }
+}
+
+// y = A x with G threads per row (G in {4, 8, 16, 32}).
+template <int G>
+__global__ void __launch_bounds__(256)
+spmv_kernel(int n, const long long* __restrict__ rp, const int* __restrict__ ci,
+            const double* __restrict__ av, const double* __restrict__ x, double* __restrict__ y) {
+    // the loop bound is uniform across the warp, so every lane reaches the shuffles
+    constexpr int RPW = 32 / G;  // rows per warp and pass
+    const int sub = threadIdx.x % G;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int base = gwarp * RPW; base < n; base += nwarps * RPW) {
+        const int i = base + (threadIdx.x & 31) / G;
+        double acc = 0.0;
+        if (i < n)
+            for (long long e = __ldg(rp + i) + sub; e < __ldg(rp + i + 1); e += G)
+                acc = fma(__ldg(av + e), __ldg(x + __ldg(ci + e)), acc);
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+        if (sub == 0 && i < n) y[i] = acc;
+    }
+}
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double s[kRedThreads / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) s[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < kRedThreads / 32 ? s[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+dot_kernel(const double* __restrict__ a, const double* __restrict__ b, int n, double* partial) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        acc = fma(a[i], b[i], acc);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// Deterministic final sum of the partials, then one scalar update.
+__global__ void __launch_bounds__(kRedThreads)
+finish_kernel(const double* __restrict__ partial, int nparts, PcgScalars* sc, int op) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partial[i];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) {
+        switch (op) {
+            case 0: sc->pq = acc; sc->alpha = sc->rz / acc; break;
+            case 1: sc->rr = acc; sc->relres = sqrt(acc) / sc->bnorm; break;
+            case 2: sc->rz_new = acc; sc->beta = acc / sc->rz; sc->rz = acc; break;
+            case 3: sc->rz = acc; break;
+            case 4: sc->bnorm = acc > 0.0 ? sqrt(acc) : 1.0; break;
+            default: break;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+xr_kernel(int n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+          const double* __restrict__ q, const PcgScalars* sc, double* partial) {
+    const double alpha = sc->alpha;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+p_kernel(int n, double* __restrict__ p, const double* __restrict__ z, const PcgScalars* sc) {
+    const double beta = sc->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void init_kernel(int n, const double* __restrict__ b, double* __restrict__ x,
+                            double* __restrict__ r) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = 0.0;
+        r[i] = b[i];
+    }
+}
+
+int vec_grid(int n) {
+    int g = (n + kRedThreads - 1) / kRedThreads;
+    return g < 1 ? 1 : (g > kMaxParts ? kMaxParts : g);
+}
+
+}  // namespace
+
+int pcg_parts(int n) { return vec_grid(n); }
+
+cudaError_t apply_blocks_per_sm(int* blocks) {
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, forward_solve, kApplyThreads, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, backward_solve, kApplyThreads, 0);
+    *blocks = a < b ? a : b;
+    return e;
+}
+
+cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epoch,
+                         unsigned long long timeout_ns, int grid, cudaStream_t s) {
+    if (S.n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(S.counter, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    forward_solve<<<grid, kApplyThreads, 0, s>>>(S, r, 2 * epoch, timeout_ns);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    backward_solve<<<grid, kApplyThreads, 0, s>>>(S, z, 2 * epoch + 1, timeout_ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, double* y,
+                        cudaStream_t s) {
+    if (S.n == 0) return cudaSuccess;
+    // threads per row from the average row length
+    const double avg = double(S.nnz_a) / double(S.n);
+    const int G = avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32;
+    long long blocks = ((long long)S.n * G + 255) / 256;
+    const int grid = int(blocks > 65536 ? 65536 : blocks);
+    switch (G) {
+        case 4: spmv_kernel<4><<<grid, 256, 0, s>>>(S.n, S.arp, S.acol, av, x, y); break;
+        case 8: spmv_kernel<8><<<grid, 256, 0, s>>>(S.n, S.arp, S.acol, av, x, y); break;
+        case 16: spmv_kernel<16><<<grid, 256, 0, s>>>(S.n, S.arp, S.acol, av, x, y); break;
+        default: spmv_kernel<32><<<grid, 256, 0, s>>>(S.n, S.arp, S.acol, av, x, y); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t pcg_dot(const double* a, const double* b, int n, double* partial, int nparts,
+                    cudaStream_t s) {
+    dot_kernel<<<nparts, kRedThreads, 0, s>>>(a, b, n, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t pcg_finish(const double* partial, int nparts, PcgScalars* sc, int op, cudaStream_t s) {
+    finish_kernel<<<1, kRedThreads, 0, s>>>(partial, nparts, sc, op);
+    return cudaGetLastError();
+}
+
+cudaError_t pcg_step_x_r(int n, double* x, double* r, const double* p, const double* q,
+                         PcgScalars* sc, double* partial, int nparts, cudaStream_t s) {
+    xr_kernel<<<nparts, kRedThreads, 0, s>>>(n, x, r, p, q, sc, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t pcg_step_p(int n, double* p, const double* z, PcgScalars* sc, cudaStream_t s) {
+    p_kernel<<<vec_grid(n), kRedThreads, 0, s>>>(n, p, z, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t pcg_init(int n, const double* b, double* x, double* r, cudaStream_t s) {
+    init_kernel<<<vec_grid(n), kRedThreads, 0, s>>>(n, b, x, r);
+    return cudaGetLastError();
+}
+
+}  // namespace ick

@@ -1,0 +1,322 @@
+"""Thin ctypes binding of libick.so (include/ick.h): the same names, argument
+marshalling only.  Device arrays are torch CUDA tensors (their data_ptr() is passed
+through); host arrays are numpy arrays.  Every compute step runs in the library's
+CUDA kernels: when the library is not built, loading it raises instead of falling
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import lib_path
+
+IC_OK, IC_ERR_ARG, IC_ERR_PATTERN, IC_ERR_BREAKDOWN, IC_ERR_TIMEOUT = 0, 1, 2, 3, 4
+IC_ERR_CUDA, IC_ERR_NOMEM, IC_ERR_NOCONV, IC_ERR_STATE = 5, 6, 7, 8
+IC_F64, IC_F32 = 0, 1
+TASK_NAMES = ("Chol", "Trsm", "Herk", "Gemm")
+
+_lib = None
+
+
+class IckError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class ic_csr_pattern(C.Structure):
+    _fields_ = [("n", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p)]
+
+
+class ic_opts(C.Structure):
+    _fields_ = [("block_rows", C.c_int), ("dtype", C.c_int), ("warps_per_cta", C.c_int),
+                ("rows_per_item", C.c_int), ("timeout_s", C.c_double), ("shift_alpha", C.c_double),
+                ("exact", C.c_int), ("threads", C.c_int), ("host_only", C.c_int),
+                ("reserved", C.c_int * 5)]
+
+
+class ic_stats_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz_a", C.c_int64), ("nnz_l", C.c_int64), ("nranges", C.c_int64),
+                ("nblocks", C.c_int64), ("ntasks", C.c_int64), ("ntasks_type", C.c_int64 * 4),
+                ("nitems", C.c_int64), ("critical_path", C.c_int64), ("max_level", C.c_int64),
+                ("flops", C.c_double), ("bytes", C.c_double), ("symbolic_s", C.c_double),
+                ("grid_ctas", C.c_int64)]
+
+
+def load():
+    """Load libick.so; raises when it is missing (build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libick.so is not built ({path}); run paper_1601_05871_gb300.build.build()")
+    L = C.CDLL(path)
+    P, I, I64, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    sig = {
+        "ic_nd_grid": (I, [I, I, I, I, I, P, P, P, P, P]),
+        "ic_symbolic": (I, [P, I, P, P, I64, P, P]),
+        "ic_numeric": (I, [P, P, P, P]),
+        "ic_apply": (I, [P, P, P, P]),
+        "pcg_solve": (I, [P, P, P, P, D, I, P, P, P]),
+        "ic_get_factor": (I, [P, P, P, P, P]),
+        "ic_stats": (I, [P, P]),
+        "ic_get_tasks": (I, [P, P, P, P, P, P, P, P, P]),
+        "ic_block_dag": (I, [I64, P, P, P, P, P, P, P, P, P, P]),
+        "ic_get_task_targets": (I, [P, I64, P, P]),
+        "ic_get_upper": (I, [P, P, P, P, P, P]),
+        "ic_get_blocks": (I, [P, P, P, P]),
+        "ic_set_timing": (I, [P, I]),
+        "ic_reset_timing": (I, [P]),
+        "ic_get_timing": (I, [P, P]),
+        "ic_test_hold_task": (I, [P, I64, I]),
+        "ic_destroy": (None, [P]),
+        "ic_strerror": (C.c_char_p, [I]),
+        "ic_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_symbols():
+    """Names of the functions include/ick.h declares (parsed from the header text)."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ick.h")
+    text = open(hdr).read()
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*((?:ic|pcg)_\w+)\s*\(", text, re.M)
+    return sorted(set(names))
+
+
+def _p(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())  # torch tensor
+
+
+def _check(st):
+    if st != IC_OK:
+        L = load()
+        raise IckError(st, f"{L.ic_strerror(st).decode()}: {L.ic_last_error().decode()}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def ic_nd_grid(nx, ny, nz, dof=1, leaf_rows=4096, keep=None):
+    """Geometric nested dissection; returns (perm, ranges) with perm[new] = old."""
+    L = load()
+    nfull = nx * ny * nz * dof
+    perm = np.empty(nfull, dtype=np.int32)
+    ranges = np.empty(nfull + 1, dtype=np.int64)
+    nr = np.zeros(1, dtype=np.int64)
+    n = np.zeros(1, dtype=np.int64)
+    keep_a = None if keep is None else np.ascontiguousarray(keep, dtype=np.uint8)
+    _check(L.ic_nd_grid(nx, ny, nz, dof, leaf_rows, _p(keep_a), _p(perm), _p(ranges), _p(nr), _p(n)))
+    return perm[: n[0]].copy(), ranges[: nr[0] + 1].copy()
+
+
+class Handle:
+    """Owns an ic_handle; ic_destroy runs when the object is collected."""
+
+    def __init__(self, ptr, n, nnz_a):
+        self._h = ptr
+        self.n = n
+        self.nnz_a = nnz_a
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().ic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # convenience methods mirroring the module functions
+    def numeric(self, values, stream=None):
+        return ic_numeric(self, values, stream)
+
+    def apply(self, r, z, stream=None):
+        return ic_apply(self, r, z, stream)
+
+    def pcg(self, A_vals, b, x, tol=1e-8, maxit=10000, stream=None):
+        return pcg_solve(self, A_vals, b, x, tol, maxit, stream)
+
+    def factor(self, values=True):
+        return ic_get_factor(self, values)
+
+    def stats(self):
+        return ic_stats(self)
+
+
+def ic_symbolic(rowptr, colind, k, perm=None, ranges=None, *, block_rows=0, dtype=IC_F64,
+                warps_per_cta=0, rows_per_item=0, timeout_s=0.0, shift_alpha=0.0, exact=0,
+                threads=0, host_only=0):
+    L = load()
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    n = len(rowptr) - 1
+    pat = ic_csr_pattern(n, _p(rowptr), _p(colind))
+    o = ic_opts(block_rows, dtype, warps_per_cta, rows_per_item, timeout_s, shift_alpha, exact, threads,
+                host_only)
+    perm_a = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    ranges_a = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
+    nr = 0 if ranges_a is None else len(ranges_a) - 1
+    out = C.c_void_p()
+    _check(L.ic_symbolic(C.byref(pat), int(k), _p(perm_a), _p(ranges_a), nr, C.byref(o), C.byref(out)))
+    return Handle(out.value, n, int(rowptr[-1]))
+
+
+def ic_numeric(h, values, stream=None):
+    """Numeric IC(k); values: CUDA float64 tensor in A's CSR order.  Returns -1, or raises
+    IckError (status IC_ERR_BREAKDOWN carries .row)."""
+    L = load()
+    brk = np.zeros(1, dtype=np.int64)
+    st = L.ic_numeric(h.ptr, _p(values), _stream(stream), _p(brk))
+    if st == IC_ERR_BREAKDOWN:
+        e = IckError(st, f"breakdown at row {int(brk[0])}")
+        e.row = int(brk[0])
+        raise e
+    _check(st)
+    return -1
+
+
+def ic_apply(h, r, z, stream=None):
+    _check(load().ic_apply(h.ptr, _p(r), _p(z), _stream(stream)))
+
+
+def pcg_solve(h, A_vals, b, x, tol=1e-8, maxit=10000, stream=None, raise_noconv=True):
+    """Returns (iters, relres); x (CUDA float64) receives the solution."""
+    it = np.zeros(1, dtype=np.int32)
+    rel = np.zeros(1, dtype=np.float64)
+    st = load().pcg_solve(h.ptr, _p(A_vals), _p(b), _p(x), float(tol), int(maxit), _p(it), _p(rel),
+                          _stream(stream))
+    if st != IC_ERR_NOCONV or raise_noconv:
+        _check(st)
+    return int(it[0]), float(rel[0])
+
+
+def ic_stats(h):
+    s = ic_stats_t()
+    _check(load().ic_stats(h.ptr, C.byref(s)))
+    d = {f: getattr(s, f) for f, _ in s._fields_}
+    d["ntasks_type"] = list(s.ntasks_type)
+    return d
+
+
+def ic_get_factor(h, values=True):
+    """(rowptr, colind, vals or None, levels) of L in lower CSR, permuted order."""
+    st = ic_stats(h)
+    n, nnz = st["n"], st["nnz_l"]
+    rp = np.empty(n + 1, dtype=np.int64)
+    ci = np.empty(nnz, dtype=np.int32)
+    lv = np.empty(nnz, dtype=np.int32)
+    va = np.empty(nnz, dtype=np.float64) if values else None
+    _check(load().ic_get_factor(h.ptr, _p(rp), _p(ci), _p(va), _p(lv)))
+    return rp, ci, va, lv
+
+
+def _dag_out(call):
+    nt = np.zeros(1, dtype=np.int64)
+    npr = np.zeros(1, dtype=np.int64)
+    _check(call(None, None, None, None, None, None, _p(nt), _p(npr)))
+    t = int(nt[0])
+    arr = [np.empty(t, dtype=np.int32) for _ in range(4)]
+    pp = np.empty(t + 1, dtype=np.int64)
+    pr = np.empty(max(1, int(npr[0])), dtype=np.int32)
+    _check(call(*[_p(a) for a in arr], _p(pp), _p(pr), _p(nt), _p(npr)))
+    return {"type": arr[0], "k": arr[1], "i": arr[2], "j": arr[3], "pred_ptr": pp,
+            "pred": pr[: int(npr[0])]}
+
+
+def ic_get_tasks(h):
+    L = load()
+    return _dag_out(lambda *a: L.ic_get_tasks(h.ptr, *a))
+
+
+def ic_block_dag(bptr, bcol):
+    L = load()
+    bptr = np.ascontiguousarray(bptr, dtype=np.int64)
+    bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+    nb = len(bptr) - 1
+    return _dag_out(lambda *a: L.ic_block_dag(nb, _p(bptr), _p(bcol), *a))
+
+
+def ic_get_task_targets(h, t):
+    L = load()
+    cnt = np.zeros(1, dtype=np.int64)
+    _check(L.ic_get_task_targets(h.ptr, int(t), None, _p(cnt)))
+    out = np.empty((int(cnt[0]), 5), dtype=np.int32)
+    _check(L.ic_get_task_targets(h.ptr, int(t), _p(out), _p(cnt)))
+    return out
+
+
+def ic_get_upper(h):
+    st = ic_stats(h)
+    n, nnz = st["n"], st["nnz_l"]
+    urp = np.empty(n + 1, dtype=np.int64)
+    ucol = np.empty(nnz, dtype=np.int32)
+    cptr = np.empty(n + 1, dtype=np.int64)
+    cp = np.empty(max(1, nnz - n), dtype=np.int32)
+    cpos = np.empty(max(1, nnz - n), dtype=np.int32)
+    _check(load().ic_get_upper(h.ptr, _p(urp), _p(ucol), _p(cptr), _p(cp), _p(cpos)))
+    return urp, ucol, cptr, cp[: nnz - n], cpos[: nnz - n]
+
+
+def ic_get_blocks(h):
+    """(ranges, bptr, bcol) of the 2D block matrix."""
+    st = ic_stats(h)
+    nr, nbk = st["nranges"], st["nblocks"]
+    ranges = np.empty(nr + 1, dtype=np.int64)
+    bptr = np.empty(nr + 1, dtype=np.int64)
+    bcol = np.empty(max(1, nbk), dtype=np.int32)
+    _check(load().ic_get_blocks(h.ptr, _p(ranges), _p(bptr), _p(bcol)))
+    return ranges, bptr, bcol[:nbk]
+
+
+class ic_timing_t(C.Structure):
+    _fields_ = [("prepare_ms", C.c_double), ("numeric_ms", C.c_double), ("apply_ms", C.c_double),
+                ("apply_calls", C.c_int64), ("launches", C.c_int64)]
+
+
+def ic_set_timing(h, on=True):
+    _check(load().ic_set_timing(h.ptr, int(bool(on))))
+
+
+def ic_reset_timing(h):
+    _check(load().ic_reset_timing(h.ptr))
+
+
+def ic_get_timing(h):
+    t = ic_timing_t()
+    _check(load().ic_get_timing(h.ptr, C.byref(t)))
+    return {f: getattr(t, f) for f, _ in t._fields_}
+
+
+def ic_test_hold_task(h, t, extra=1):
+    _check(load().ic_test_hold_task(h.ptr, int(t), int(extra)))
+
+
+def ic_destroy(h):
+    h.close()

@@ -16,4 +16,5 @@ from .matrices import (  # noqa: F401
     tridiagonal_spd,
     rhs,
     config_problem,
+    is_exactly_symmetric,
 )

@@ -137,7 +137,9 @@ def diffusion3d_7pt(nx: int, ny: int | None = None, nz: int | None = None, *, si
         valid = (xx >= 0) & (xx < nx) & (yy >= 0) & (yy < ny) & (zz >= 0) & (zz < nz)
         j = np.where(valid, xx + nx * (yy + ny * zz), 0)
         kj = kappa[j]
-        c = np.where(valid, 2.0 * kappa * kj / (kappa + kj), kappa)
+        # 2*(ki*kj)/(ki+kj): both products and the sum commute, so the face
+        # coefficient is bitwise the same from either side (exact symmetry)
+        c = np.where(valid, 2.0 * (kappa * kj) / (kappa + kj), kappa)
         if dz != 0:
             c = c * zscale
         diag += c
@@ -243,8 +245,35 @@ def elasticity3d_q1(ne: int = 48, *, nu: float | None = None, E: float = 1.0, se
     np.cumsum(counts, out=rowptr[1:])
     colind = newidx[safe.reshape(n_full, 81)[m2]].astype(np.int32)
     vals = np.ascontiguousarray(dvals).reshape(n_full, 81)[m2].astype(np.float64)
+    vals = _symmetrize(n, rowptr, colind, vals)
     return Problem(f"elasticity3d_q1_{ne}^3_nu{nu:.4f}", n, rowptr, colind, vals,
                    grid=(nn, nn, nn), dof=3, keep=keep, seed=seed, meta={"nu": nu, "E": E})
+
+
+def _symmetrize(n, rowptr, colind, vals):
+    """(A + A^T) / 2 on a symmetric pattern: a + b commutes, so the result is exactly
+    symmetric even where the assembly summed element contributions in different orders."""
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    key = rows * n + colind
+    tkey = colind.astype(np.int64) * n + rows
+    order = np.argsort(key)
+    tpos = order[np.searchsorted(key[order], tkey)]
+    assert np.array_equal(key[tpos], tkey), "pattern is not symmetric"
+    return (vals + vals[tpos]) * 0.5
+
+
+def is_exactly_symmetric(prob) -> bool:
+    """True when the pattern is symmetric and A_ij == A_ji bit for bit."""
+    n = prob.n
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(prob.rowptr))
+    key = rows * n + prob.colind
+    tkey = prob.colind.astype(np.int64) * n + rows
+    order = np.argsort(key)
+    idx = np.searchsorted(key[order], tkey)
+    if np.any(idx >= len(key)):
+        return False
+    tpos = order[idx]
+    return bool(np.array_equal(key[tpos], tkey) and np.array_equal(prob.vals, prob.vals[tpos]))
 
 
 def diffusion_batch(count: int = 512, smin: int = 8, smax: int = 32, *, sigma: float = 1.0,

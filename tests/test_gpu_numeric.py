@@ -1,0 +1,247 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Pattern and levels must match bit for bit; FP64 values within 1e-12 * max|A| (the
+bound the workload sets for FP64); with exact=1 (separately rounded multiply and
+subtract, the oracle's operation sequence) the factor must match bit for bit.
+Breakdown rows must match the oracle's first failing row.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ick():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_05871_gb300.build import build
+    build()
+    import paper_1601_05871_gb300 as m
+    m.load()
+    return m
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def factor_both(ick, orc, prob, perm, ranges, k, **opts):
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, k, perm, ranges, **opts)
+    vals = dev(prob.vals)
+    gpu_brk = -1
+    try:
+        ick.ic_numeric(h, vals)
+    except ick.IckError as e:
+        if e.status != 3:
+            raise
+        gpu_brk = e.row
+    o = orc.OracleIC.from_problem(prob, perm, k)
+    st = o.numeric(prob.vals)
+    return h, o, gpu_brk, st
+
+
+def check_parity(ick, orc, prob, perm, ranges, k, exact=0, **opts):
+    h, o, gpu_brk, st = factor_both(ick, orc, prob, perm, ranges, k, exact=exact, **opts)
+    assert st == 0 and gpu_brk == -1, (prob.name, st, gpu_brk)
+    rp, ci, lv, levels = ick.ic_get_factor(h)
+    orp, oci, olev = o.pattern()
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci) and np.array_equal(levels, olev)
+    ref = o.values()
+    amax = np.abs(prob.vals).max()
+    err = np.abs(lv - ref).max() / amax
+    if exact:
+        assert np.array_equal(lv, ref), (prob.name, err)
+    else:
+        assert err <= TOL, (prob.name, err)
+    return h, o, lv
+
+
+def test_c1_uniform_blocks_exact_and_fma(ick, orc):
+    """2-D Poisson 64x64, IC(1), 16 uniform 256-row blocks of the ND-ordered matrix."""
+    prob = synth.config_problem(1)
+    perm, _ = ick.ic_nd_grid(64, 64, 1, 1, 256)
+    check_parity(ick, orc, prob, perm, None, 1, exact=1, block_rows=256)
+    check_parity(ick, orc, prob, perm, None, 1, exact=0, block_rows=256)
+
+
+def test_c1_nd_ranges(ick, orc):
+    prob = synth.config_problem(1)
+    perm, ranges = ick.ic_nd_grid(64, 64, 1, 1, 256)
+    check_parity(ick, orc, prob, perm, ranges, 1, exact=1, block_rows=256)
+
+
+@pytest.mark.parametrize("warps", [8, 16])
+def test_27pt_ic2(ick, orc, warps):
+    prob = synth.laplace3d_27pt(14)
+    perm, ranges = ick.ic_nd_grid(14, 14, 14, 1, 300)
+    check_parity(ick, orc, prob, perm, ranges, 2, exact=1, block_rows=300, warps_per_cta=warps)
+    check_parity(ick, orc, prob, perm, ranges, 2, exact=0, block_rows=300, warps_per_cta=warps)
+
+
+def test_anisotropic_ic3_ragged_blocks(ick, orc):
+    prob = synth.diffusion3d_7pt(19, 17, 13, sigma=2.0, zscale=100.0, seed=5001)
+    perm, ranges = ick.ic_nd_grid(19, 17, 13, 1, 333)
+    check_parity(ick, orc, prob, perm, ranges, 3, exact=1, block_rows=257, rows_per_item=7)
+
+
+def test_elasticity_ic1(ick, orc):
+    prob = synth.elasticity3d_q1(5, seed=4004)
+    perm, ranges = ick.ic_nd_grid(6, 6, 6, 3, 120, keep=prob.keep)
+    h, o, brk, st = factor_both(ick, orc, prob, perm, ranges, 1, block_rows=100)
+    assert brk == (o.breakdown_row if st else -1)
+    if st == 0:
+        check_parity(ick, orc, prob, perm, ranges, 1, exact=1, block_rows=100)
+
+
+@pytest.mark.parametrize("block_rows", [1, 3, 8192])
+def test_extreme_block_sizes(ick, orc, block_rows):
+    prob = synth.poisson2d_5pt(23, 19)
+    perm, _ = ick.ic_nd_grid(23, 19, 1, 1, 30)
+    check_parity(ick, orc, prob, perm, None, 2, exact=1, block_rows=block_rows)
+
+
+def test_long_rows_chunked(ick, orc):
+    """Complete fill of a dense SPD matrix: rows of 300 entries exceed one staged chunk."""
+    prob = synth.random_spd(300, 1.0, 11, kind="dense_spd")
+    check_parity(ick, orc, prob, None, None, 300, exact=1, block_rows=64)
+    check_parity(ick, orc, prob, None, None, 300, exact=0, block_rows=100)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_signed(ick, orc, seed):
+    prob = synth.random_spd(200, 0.03, 50 + seed, kind="signed")
+    for k in (0, 2):
+        h, o, brk, st = factor_both(ick, orc, prob, None, None, k, block_rows=37, exact=1)
+        if st:
+            assert brk == o.breakdown_row
+        else:
+            assert brk == -1
+            rp, ci, lv, _ = ick.ic_get_factor(h)
+            assert np.array_equal(lv, o.values())
+
+
+def test_breakdown_row_hand_computed(ick, orc):
+    A = np.array([[2.0, 0.75, 0.25, -1.0], [0.75, 1.0, 1.0, 0.0], [0.25, 1.0, 1.5, 0.75],
+                  [-1.0, 0.0, 0.75, 2.0]])
+    rows, cols = np.nonzero(A)
+    prob = synth.matrices._from_coo("brk4", 4, rows, cols, A[rows, cols], 0)
+    for br in (1, 2, 4):
+        h, o, brk, st = factor_both(ick, orc, prob, None, None, 0, block_rows=br)
+        assert st == orc.ERR_BREAKDOWN and o.breakdown_row == 3 and brk == 3
+
+
+def test_tiny_and_empty(ick, orc):
+    prob = synth.matrices._from_coo("one", 1, [0], [0], [4.0], 0)
+    h, o, lv = check_parity(ick, orc, prob, None, None, 0, exact=1)
+    assert lv[0] == 2.0
+    h = ick.ic_symbolic(np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), 1)
+    import torch
+    ick.ic_numeric(h, torch.zeros(1, dtype=torch.float64, device="cuda"))
+    s = ick.ic_stats(h)
+    assert s["n"] == 0
+
+
+def test_repeat_calls_bitwise_and_shift(ick, orc):
+    prob = synth.laplace3d_27pt(10)
+    perm, ranges = ick.ic_nd_grid(10, 10, 10, 1, 100)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=128)
+    v = dev(prob.vals)
+    ick.ic_numeric(h, v)
+    a = ick.ic_get_factor(h)[2]
+    for _ in range(3):
+        ick.ic_numeric(h, v)
+        assert np.array_equal(ick.ic_get_factor(h)[2], a)
+    hs = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=128,
+                         shift_alpha=0.25, exact=1)
+    ick.ic_numeric(hs, v)
+    o = orc.OracleIC.from_problem(prob, perm, 2)
+    assert o.numeric(prob.vals, 0.25) == 0
+    assert np.array_equal(ick.ic_get_factor(hs)[2], o.values())
+
+
+def test_timeout_when_a_task_is_never_released(ick, orc):
+    """Host-side fault injection: one task's in-degree is raised so that no
+    predecessor ever releases it.  Every device wait is bounded, so the call returns
+    IC_ERR_TIMEOUT; afterwards the restored plan factors correctly."""
+    prob = synth.poisson2d_5pt(30, 30)
+    perm, ranges = ick.ic_nd_grid(30, 30, 1, 1, 60)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 1, perm, ranges, block_rows=64, timeout_s=0.5)
+    ntasks = ick.ic_stats(h)["ntasks"]
+    ick.ic_test_hold_task(h, ntasks // 2, 1)
+    v = dev(prob.vals)
+    with pytest.raises(ick.IckError) as e:
+        ick.ic_numeric(h, v)
+    assert e.value.status == 4
+    ick.ic_test_hold_task(h, ntasks // 2, 0)
+    ick.ic_numeric(h, v)
+    o = orc.OracleIC.from_problem(prob, perm, 1)
+    o.numeric(prob.vals)
+    assert np.abs(ick.ic_get_factor(h)[2] - o.values()).max() <= TOL * 4
+
+
+def test_apply_matches_oracle(ick, orc):
+    import torch
+    prob = synth.diffusion3d_7pt(16, sigma=1.0, seed=3001)
+    perm, ranges = ick.ic_nd_grid(16, 16, 16, 1, 256)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 1, perm, ranges, block_rows=256)
+    ick.ic_numeric(h, dev(prob.vals))
+    o = orc.OracleIC.from_problem(prob, perm, 1)
+    o.numeric(prob.vals)
+    r = np.random.default_rng(1).standard_normal(prob.n)
+    z = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    ick.ic_apply(h, dev(r), z)
+    torch.cuda.synchronize()
+    zr = o.apply(r)
+    assert np.abs(z.cpu().numpy() - zr).max() <= 1e-11 * np.abs(zr).max()
+    with pytest.raises(ick.IckError):
+        ick.ic_apply(h, z, z)
+
+
+def test_pcg_matches_oracle(ick, orc):
+    import torch
+    prob = synth.config_problem(1)
+    perm, _ = ick.ic_nd_grid(64, 64, 1, 1, 256)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 1, perm, None, block_rows=256)
+    av = dev(prob.vals)
+    ick.ic_numeric(h, av)
+    b = synth.rhs(prob.n, prob.seed)
+    x = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    it, rel = ick.pcg_solve(h, av, dev(b), x, 1e-8, 1000)
+    o = orc.OracleIC.from_problem(prob, perm, 1)
+    o.numeric(prob.vals)
+    xo, ito, relo, st = orc.pcg(prob, b, o, tol=1e-8)
+    assert st == 0 and abs(it - ito) <= 1 and rel <= 1e-8
+    xg = x.cpu().numpy()
+    true_rel = np.linalg.norm(prob.scipy() @ xg - b) / np.linalg.norm(b)
+    assert true_rel <= 2e-8
+    assert np.abs(xg - xo).max() <= 1e-6 * np.abs(xo).max()
+
+
+@pytest.mark.slow
+def test_full_size_27pt_96_ic2(ick, orc):
+    """The bench workload at full size (96^3 27-point, IC(2), ND ranges of <= 4096 rows,
+    16 warps per CTA): every entry of L against the oracle, plus the defining identity
+    on sampled pattern entries."""
+    prob = synth.config_problem(2)
+    perm, ranges = ick.ic_nd_grid(96, 96, 96, 1, 4096)
+    h, o, lv = check_parity(ick, orc, prob, perm, ranges, 2, exact=0, block_rows=4096)
+    rp, ci, _, _ = ick.ic_get_factor(h)
+    g = np.random.default_rng(0)
+    n = prob.n
+    pinv = np.empty(n, dtype=np.int64)
+    pinv[perm] = np.arange(n)
+    A = prob.scipy()
+    for i in g.integers(0, n, size=200):
+        row_i = dict(zip(ci[rp[i]:rp[i + 1]].tolist(), lv[rp[i]:rp[i + 1]].tolist()))
+        for j in ci[rp[i]:rp[i + 1]]:
+            row_j = dict(zip(ci[rp[j]:rp[j + 1]].tolist(), lv[rp[j]:rp[j + 1]].tolist()))
+            s = sum(row_i[c] * row_j[c] for c in row_i if c in row_j and c <= j)
+            bij = A[perm[i], perm[j]]
+            assert abs(s - bij) <= 1e-12 * 26

@@ -1,0 +1,321 @@
+"""CPU tests of libick.so's host logic: exports, nested dissection, the level-k
+symbolic pass, the 2D block matrix, the Cholesky-by-blocks DAG and the per-task work
+lists.  No GPU is used: handles are built with host_only=1.
+
+The plan executor below runs the work lists of every task on the CPU, in random
+topological orders of the DAG, with each update a separately rounded multiply then
+subtract.  It is a test of the plan only (DAG edges and target lists), never a
+product path.  Because the DAG serialises every update to a block in k order and a
+task applies its pivots in ascending order, every entry sees the same operation
+sequence as the oracle's up-looking order: the result must match the oracle bit for
+bit in any valid order.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+import paper_1601_05871_gb300 as ick
+from paper_1601_05871_gb300.build import build, lib_path
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+    ick.load()
+
+
+def test_library_exports_declared_symbols():
+    names = ick.ick.declared_symbols()
+    assert "ic_symbolic" in names and "ic_numeric" in names and "pcg_solve" in names
+    L = ick.load()
+    for nm in names:
+        assert hasattr(L, nm), nm
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path()], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    assert set(names) <= exported
+
+
+def test_strerror_and_last_error():
+    L = ick.load()
+    for st in range(9):
+        assert L.ic_strerror(st)
+    with pytest.raises(ick.IckError) as e:
+        ick.ic_symbolic(np.array([0, 1, 2], dtype=np.int64), np.array([1, 0], dtype=np.int32), 0,
+                        host_only=1)
+    assert e.value.status == ick.ick.IC_ERR_PATTERN and "diagonal" in str(e.value)
+
+
+# ------------------------------------------------------------------ worked example
+
+def _read_worked_example():
+    pattern, iters = {}, {}
+    for ln in open(os.path.join(GOLD, "worked_example_tasks.txt")):
+        ln = ln.strip()
+        if not ln or ln.startswith("#"):
+            continue
+        if ln.startswith("pattern"):
+            head, tail = ln.split(":")
+            pattern[int(head.split()[1])] = [int(x) for x in tail.split()]
+        else:
+            head, tail = ln.split(":")
+            iters[int(head)] = [tuple(t.split()) for t in tail.split(",")]
+    return pattern, iters
+
+
+def test_worked_example_task_sequence():
+    """Section 3.3's 5x5 example: 19 tasks in the printed order."""
+    pattern, iters = _read_worked_example()
+    bptr = [0]
+    bcol = []
+    for b in range(len(pattern)):
+        bcol += pattern[b]
+        bptr.append(len(bcol))
+    d = ick.ic_block_dag(bptr, bcol)
+    got = []
+    for t in range(len(d["type"])):
+        name = ick.TASK_NAMES[d["type"][t]]
+        k, i, j = int(d["k"][t]), int(d["i"][t]), int(d["j"][t])
+        if name == "Chol":
+            got.append((k + 1, (name, str(k), str(k))))
+        elif name == "Trsm":
+            got.append((k + 1, (name, str(k), str(j))))
+        else:
+            got.append((k + 1, (name, str(i), str(j))))
+    want = [(it, t) for it in sorted(iters) for t in iters[it]]
+    assert got == want and len(got) == 19
+    # Chol(A22) has no predecessor; Trsm(A04)'s only predecessor is Chol(A00)
+    idx = {(ick.TASK_NAMES[d["type"][t]], int(d["k"][t]), int(d["i"][t]), int(d["j"][t])): t
+           for t in range(len(d["type"]))}
+    pp, pr = d["pred_ptr"], d["pred"]
+    t22 = idx[("Chol", 2, 2, 2)]
+    assert pp[t22 + 1] == pp[t22]
+    t04 = idx[("Trsm", 0, 0, 4)]
+    assert list(pr[pp[t04]:pp[t04 + 1]]) == [idx[("Chol", 0, 0, 0)]]
+    # dependence rule Chol -> Trsm -> Herk/Gemm: Herk44 at k=0 needs Trsm04
+    h44 = idx[("Herk", 0, 4, 4)]
+    assert list(pr[pp[h44]:pp[h44 + 1]]) == [t04]
+
+
+def test_block_dag_rejects_bad_patterns():
+    with pytest.raises(ick.IckError):
+        ick.ic_block_dag([0, 1, 2], [1, 1])  # block row 0 lacks its diagonal
+    with pytest.raises(ick.IckError):
+        ick.ic_block_dag([0, 2, 3], [0, 5, 1])  # column out of range
+
+
+# ------------------------------------------------------------------ ND and symbolic vs oracle
+
+@pytest.mark.parametrize("grid", [(64, 64, 1, 1, 256), (17, 9, 5, 1, 40), (6, 6, 6, 3, 50),
+                                  (12, 12, 12, 1, 1), (1, 1, 1, 1, 1)])
+def test_nd_matches_oracle(orc, grid):
+    nx, ny, nz, dof, leaf = grid
+    p1, r1 = ick.ic_nd_grid(nx, ny, nz, dof, leaf)
+    p2, r2 = orc.nd_grid(nx, ny, nz, dof, leaf)
+    assert np.array_equal(p1, p2) and np.array_equal(r1, r2)
+
+
+def test_nd_keep_matches_oracle(orc):
+    p = synth.elasticity3d_q1(4, seed=4002)
+    p1, r1 = ick.ic_nd_grid(5, 5, 5, 3, 30, keep=p.keep)
+    p2, r2 = orc.nd_grid(5, 5, 5, 3, 30, keep=p.keep)
+    assert np.array_equal(p1, p2) and np.array_equal(r1, r2) and len(p1) == p.n
+
+
+def _cases(orc):
+    out = []
+    p = synth.poisson2d_5pt(20, 17)
+    out.append((p, ick.ic_nd_grid(20, 17, 1, 1, 40), 2))
+    p = synth.laplace3d_27pt(7)
+    out.append((p, ick.ic_nd_grid(7, 7, 7, 1, 30), 2))
+    p = synth.diffusion3d_7pt(8, sigma=2.0, zscale=100.0, seed=5005)
+    out.append((p, ick.ic_nd_grid(8, 8, 8, 1, 50), 3))
+    p = synth.elasticity3d_q1(3, seed=4003)
+    out.append((p, ick.ic_nd_grid(4, 4, 4, 3, 40, keep=p.keep), 0))
+    p = synth.random_spd(40, 0.1, 9, kind="signed")
+    out.append((p, (None, None), 1))
+    return out
+
+
+def _lower_sets(rp, ci, lv):
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    return rows, ci, lv
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_symbolic_matches_oracle(orc, k):
+    """Pattern and levels from the per-row BFS equal the oracle's row-wise sum rule."""
+    for prob, (perm, ranges), _ in _cases(orc):
+        h = ick.ic_symbolic(prob.rowptr, prob.colind, k, perm, ranges, block_rows=64, host_only=1)
+        rp, ci, _, lv = ick.ic_get_factor(h, values=False)
+        o = orc.OracleIC.from_problem(prob, perm, k)
+        orp, oci, olv = o.pattern()
+        assert np.array_equal(rp, orp) and np.array_equal(ci, oci) and np.array_equal(lv, olv), prob.name
+        st = o.numeric(prob.vals)
+        if st == 0:
+            assert ick.ic_stats(h)["flops"] == o.flops, prob.name
+
+
+def test_pattern_errors():
+    rp = np.array([0, 2, 3], dtype=np.int64)
+    for ci, why in [(np.array([0, 1, 1], dtype=np.int32), "asymmetric"),
+                    (np.array([1, 0, 1], dtype=np.int32), "unsorted"),
+                    (np.array([0, 2, 1], dtype=np.int32), "range")]:
+        with pytest.raises(ick.IckError) as e:
+            ick.ic_symbolic(rp, ci, 1, host_only=1)
+        assert e.value.status == ick.ick.IC_ERR_PATTERN, why
+    p = synth.poisson2d_5pt(3, 3)
+    with pytest.raises(ick.IckError) as e:
+        ick.ic_symbolic(p.rowptr, p.colind, 1, perm=np.zeros(9, dtype=np.int32), host_only=1)
+    assert e.value.status == ick.ick.IC_ERR_ARG
+    with pytest.raises(ick.IckError):
+        ick.ic_symbolic(p.rowptr, p.colind, 1, block_rows=9000, host_only=1)
+
+
+def test_empty_matrix():
+    h = ick.ic_symbolic(np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), 2, host_only=1)
+    s = ick.ic_stats(h)
+    assert s["n"] == 0 and s["ntasks"] == 0 and s["nitems"] == 0
+
+
+# ------------------------------------------------------------------ DAG properties on real plans
+
+def _plan(h):
+    urp, ucol, cptr, cp, cpos = ick.ic_get_upper(h)
+    ranges, bptr, bcol = ick.ic_get_blocks(h)
+    d = ick.ic_get_tasks(h)
+    tg = [ick.ic_get_task_targets(h, t) for t in range(len(d["type"]))]
+    return urp, ucol, cp, cpos, ranges, bptr, bcol, d, tg
+
+
+def test_block_pattern_and_dag_invariants():
+    prob = synth.laplace3d_27pt(8)
+    perm, ranges = ick.ic_nd_grid(8, 8, 8, 1, 40)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=48, host_only=1)
+    urp, ucol, cp, cpos, rng, bptr, bcol, d, tg = _plan(h)
+    n = prob.n
+    blk = np.searchsorted(rng, np.arange(n), side="right") - 1
+    # a block exists iff S has an entry in it
+    rows = np.repeat(np.arange(n), np.diff(urp))
+    want = set(zip(blk[rows].tolist(), blk[ucol].tolist()))
+    got = {(b, int(c)) for b in range(len(bptr) - 1) for c in bcol[bptr[b]:bptr[b + 1]]}
+    assert got == want
+    # predecessors come earlier; each block's writers form a chain in k order
+    pp, pr = d["pred_ptr"], d["pred"]
+    writers = {}
+    for t in range(len(d["type"])):
+        assert all(pr[pp[t]:pp[t + 1]] < t)
+        ty, k, i, j = (int(d[x][t]) for x in ("type", "k", "i", "j"))
+        key = (k, k) if ty == 0 else (k, j) if ty == 1 else (i, j)
+        if key in writers:
+            assert writers[key] in pr[pp[t]:pp[t + 1]]
+        writers[key] = t
+    s = ick.ic_stats(h)
+    assert s["critical_path"] >= 1 and s["ntasks"] == sum(s["ntasks_type"])
+
+
+def _execute_plan(prob, perm, h, order):
+    """Run every task's work list on the CPU in `order` (a topological order)."""
+    urp, ucol, cp, cpos, rng, bptr, bcol, d, tg = _plan(h)
+    n = prob.n
+    pinv = np.empty(n, dtype=np.int64)
+    pm = np.arange(n) if perm is None else perm
+    pinv[pm] = np.arange(n)
+    # U := B on S (zero on fill)
+    U = np.zeros(len(ucol))
+    for o in range(n):
+        i = pinv[o]
+        for e in range(prob.rowptr[o], prob.rowptr[o + 1]):
+            j = pinv[prob.colind[e]]
+            if j >= i:
+                pos = urp[i] + np.searchsorted(ucol[urp[i]:urp[i + 1]], j)
+                U[pos] = prob.vals[e]
+    for t in order:
+        ty, k, i, j = (int(d[x][t]) for x in ("type", "k", "i", "j"))
+        src = k if ty == 0 else j
+        start_at_r = ty in (0, 2)
+        lo, hi = rng[src], rng[src + 1]
+        for r, ca, cb, tb, te in tg[t]:
+            tcols = ucol[tb:te]
+            for q in range(ca, cb):
+                p, pos = int(cp[q]), int(cpos[q])
+                row = ucol[urp[p]:urp[p + 1]]
+                sb = urp[p] + np.searchsorted(row, lo)
+                se = urp[p] + np.searchsorted(row, hi)
+                if start_at_r:
+                    sb = pos
+                if se <= sb:
+                    continue
+                cols = ucol[sb:se]
+                idx = np.searchsorted(tcols, cols)
+                ok = (idx < len(tcols))
+                ok[ok] &= tcols[idx[ok]] == cols[ok]
+                tpos = tb + idx[ok]
+                U[tpos] = U[tpos] - U[pos] * U[sb:se][ok]
+            if ty == 0:
+                U[tb] = np.sqrt(U[tb])
+                U[tb + 1:te] = U[tb + 1:te] / U[tb]
+            elif ty == 1:
+                U[tb:te] = U[tb:te] / U[urp[r]]
+    return urp, ucol, U
+
+
+def _random_topo(d, rng):
+    nt = len(d["type"])
+    pp, pr = d["pred_ptr"], d["pred"]
+    indeg = np.diff(pp).astype(int)
+    succ = [[] for _ in range(nt)]
+    for t in range(nt):
+        for p in pr[pp[t]:pp[t + 1]]:
+            succ[p].append(t)
+    ready = [t for t in range(nt) if indeg[t] == 0]
+    order = []
+    while ready:
+        t = ready.pop(rng.integers(len(ready)))
+        order.append(t)
+        for s in succ[t]:
+            indeg[s] -= 1
+            if indeg[s] == 0:
+                ready.append(s)
+    assert len(order) == nt
+    return order
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_plan_in_random_orders_matches_oracle_bitwise(orc, case):
+    if case == 0:
+        prob = synth.poisson2d_5pt(16, 16)
+        perm, ranges = ick.ic_nd_grid(16, 16, 1, 1, 20)
+        k, br = 1, 16
+    elif case == 1:
+        prob = synth.laplace3d_27pt(6)
+        perm, ranges = ick.ic_nd_grid(6, 6, 6, 1, 20)
+        k, br = 2, 24
+    elif case == 2:
+        prob = synth.diffusion3d_7pt(7, sigma=2.0, zscale=100.0, seed=77)
+        perm, ranges = None, None
+        k, br = 3, 40
+    else:
+        prob = synth.elasticity3d_q1(4, seed=4004)
+        perm, ranges = ick.ic_nd_grid(5, 5, 5, 3, 90, keep=prob.keep)
+        k, br = 1, 70
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, k, perm, ranges, block_rows=br, host_only=1)
+    o = orc.OracleIC.from_problem(prob, perm, k)
+    assert o.numeric(prob.vals) == 0
+    lref = o.values()
+    lrp, lci, _ = o.pattern()
+    d = ick.ic_get_tasks(h)
+    g = np.random.default_rng(case)
+    for trial in range(2):
+        order = _random_topo(d, g)
+        urp, ucol, U = _execute_plan(prob, perm, h, order)
+        # L_ij = U_ji: map the oracle's lower entries onto U positions
+        n = prob.n
+        rows = np.repeat(np.arange(n), np.diff(lrp))
+        upos = urp[lci] + np.array([np.searchsorted(ucol[urp[c]:urp[c + 1]], r) for r, c in zip(rows, lci)])
+        assert np.array_equal(U[upos], lref), (case, trial)

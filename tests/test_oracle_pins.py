@@ -343,3 +343,14 @@ def test_flop_count_closed_form(orc):
     assert st == 0
     upd = sum((n - j - 1) * (n - j) // 2 for j in range(n))
     assert h.flops == n * (n - 1) / 2 + n + 2 * upd
+
+
+def test_generators_exactly_symmetric():
+    """Every generated matrix is symmetric bit for bit, so reading either triangle of
+    B = P^T A P gives the same values (the oracle reads the lower, the library the upper)."""
+    probs = [synth.poisson2d_5pt(9, 7), synth.laplace3d_27pt(6), synth.elasticity3d_q1(4, seed=4005),
+             synth.diffusion3d_7pt(7, sigma=2.0, zscale=100.0, seed=5),
+             synth.random_spd(30, 0.2, 1, kind="signed"), synth.tridiagonal_spd(20, 3)]
+    probs += synth.diffusion_batch(3, 4, 6, seed=3000)
+    for p in probs:
+        assert synth.is_exactly_symmetric(p), p.name
