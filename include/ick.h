@@ -88,6 +88,7 @@ typedef struct {
     double bytes;         /* compulsory HBM bytes of one numeric factorization       */
     double symbolic_s;    /* wall time of ic_symbolic                                */
     int64_t grid_ctas;    /* CTAs of the persistent kernel launch                    */
+    int64_t solve_depth[2];/* levels of the forward / backward solve's row DAG        */
 } ic_stats_t;
 
 typedef struct ic_handle ic_handle;
@@ -219,6 +220,14 @@ int ic_get_timing(const ic_handle* h, ic_timing_t* out);
  * ends in IC_ERR_TIMEOUT once opts.timeout_s has passed (every device wait is
  * bounded; nothing traps).  extra = 0 restores the plan.  Errors: IC_ERR_ARG, IC_ERR_CUDA. */
 int ic_test_hold_task(ic_handle* h, int64_t t, int extra);
+
+/* Task trace of the numeric kernel.  ic_set_trace(h, 1) allocates 4 uint64 words per
+ * work item; every later ic_numeric records, per queue slot, the %globaltimer start
+ * and end (ns) of the item, task | chunk << 32, and the SM that ran it.
+ * ic_get_trace copies nitems * 4 words (nitems from ic_stats) to the host buffer out.
+ * Errors: IC_ERR_ARG, IC_ERR_STATE (host-only handle or tracing off), IC_ERR_CUDA. */
+int ic_set_trace(ic_handle* h, int on);
+int ic_get_trace(const ic_handle* h, uint64_t* out);
 
 void ic_destroy(ic_handle* h);
 

@@ -21,6 +21,8 @@ from .ick import (  # noqa: F401
     ic_reset_timing,
     ic_get_timing,
     ic_test_hold_task,
+    ic_set_trace,
+    ic_get_trace,
     ic_destroy,
     load,
     IC_F64,

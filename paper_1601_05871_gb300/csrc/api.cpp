@@ -70,6 +70,7 @@ struct ic_handle {
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool apply_pending = false;  // ev[3]..ev[4] bracket an apply not yet added to tm
     ic_timing_t tm{};
+    unsigned long long* trace_buf = nullptr;  // ic_set_trace
 
     ~ic_handle() {
         for (cudaEvent_t e : ev)
@@ -132,7 +133,15 @@ int upload_plan(ic_handle* h) {
         if ((st = h->upload(&dptr, P.urp))) return st;
         D.urp = reinterpret_cast<const long long*>(dptr);
     }
-    if ((st = h->upload(&D.ucol, P.ucol))) return st;
+    {
+        // 16 bytes of padding: the kernels copy whole aligned 16-byte chunks
+        int* dcol = nullptr;
+        if ((st = h->alloc(&dcol, P.ucol.size() + 4))) return st;
+        CK(cudaMemset(dcol + P.ucol.size(), 0xff, 4 * sizeof(int)));
+        if (!P.ucol.empty())
+            CK(cudaMemcpy(dcol, P.ucol.data(), P.ucol.size() * sizeof(int), cudaMemcpyHostToDevice));
+        D.ucol = dcol;
+    }
     if ((st = h->upload(&D.gsrc, P.gsrc))) return st;
     if ((st = h->upload(&D.ranges, P.ranges))) return st;
     if ((st = h->upload(&D.rseg_ptr, P.rseg_ptr))) return st;
@@ -140,6 +149,7 @@ int upload_plan(ic_handle* h) {
     if ((st = h->upload(&D.rseg_se, P.rseg_se))) return st;
     if ((st = h->upload(&D.cptr, P.cptr))) return st;
     if ((st = h->upload(&D.csc, P.csc))) return st;
+    if ((st = h->upload(&D.cseg_end, P.cseg_end))) return st;
     if ((st = h->upload(&D.task, P.task))) return st;
     if ((st = h->upload(&D.tgt_ptr, P.tgt_ptr))) return st;
     if ((st = h->upload(&D.tgt, P.tgt))) return st;
@@ -150,7 +160,8 @@ int upload_plan(ic_handle* h) {
     if ((st = h->upload(&D.indeg0, P.indeg0))) return st;
     if ((st = h->upload(&D.seeds, P.seeds))) return st;
     double* uval = nullptr;
-    if ((st = h->alloc(&uval, size_t(P.nnz_u)))) return st;
+    if ((st = h->alloc(&uval, size_t(P.nnz_u) + 2))) return st;
+    CK(cudaMemset(uval, 0, (size_t(P.nnz_u) + 2) * sizeof(double)));
     D.uval = uval;
     if ((st = h->alloc(&D.indeg, P.task.size()))) return st;
     if ((st = h->alloc(&D.items_left, P.task.size()))) return st;
@@ -180,6 +191,8 @@ int upload_plan(ic_handle* h) {
         const int32_t* dacol = nullptr;
         if ((st = h->upload(&dacol, P.acol))) return st;
         S.acol = dacol;
+        if ((st = h->upload(&S.fwd_order, P.fwd_order))) return st;
+        if ((st = h->upload(&S.bwd_order, P.bwd_order))) return st;
     }
     if ((st = h->alloc(&S.y, size_t(P.n)))) return st;
     if ((st = h->alloc(&S.flag, size_t(P.n)))) return st;
@@ -492,6 +505,8 @@ int ic_stats(const ic_handle* h, ic_stats_t* out) {
     out->bytes = P.bytes;
     out->symbolic_s = h->symbolic_s;
     out->grid_ctas = h->grid_numeric;
+    out->solve_depth[0] = P.fwd_depth;
+    out->solve_depth[1] = P.bwd_depth;
     return IC_OK;
 }
 
@@ -605,6 +620,29 @@ int ic_get_timing(const ic_handle* hc, ic_timing_t* out) {
         if (st) return st;
     }
     *out = h->tm;
+    return IC_OK;
+}
+
+int ic_set_trace(ic_handle* h, int on) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    if (h->device < 0) return fail(IC_ERR_STATE, "host-only handle");
+    DeviceGuard g(h->device);
+    if (on && !h->dp.trace) {
+        unsigned long long* t = nullptr;
+        int st = h->alloc(&t, 4 * size_t(h->hp.total_items > 0 ? h->hp.total_items : 1));
+        if (st) return st;
+        CK(cudaMemset(t, 0, 4 * size_t(h->hp.total_items > 0 ? h->hp.total_items : 1) * 8));
+        h->trace_buf = t;
+    }
+    h->dp.trace = on ? h->trace_buf : nullptr;
+    return IC_OK;
+}
+
+int ic_get_trace(const ic_handle* h, uint64_t* out) {
+    if (!h || !out) return fail(IC_ERR_ARG, "NULL argument");
+    if (!h->trace_buf) return fail(IC_ERR_STATE, "tracing was never enabled");
+    DeviceGuard g(h->device);
+    CK(cudaMemcpy(out, h->trace_buf, 4 * size_t(h->hp.total_items) * 8, cudaMemcpyDeviceToHost));
     return IC_OK;
 }
 

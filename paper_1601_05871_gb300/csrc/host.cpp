@@ -404,9 +404,17 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
     P.csc.resize(P.cptr[n]);
     {
         std::vector<int32_t> fill(P.cptr.begin(), P.cptr.end() - 1);
+        std::vector<int32_t> send(P.nnz_u);  // end of the block segment holding each position
         for (int64_t p = 0; p < n; ++p)
-            for (int64_t e = P.urp[p] + 1; e < P.urp[p + 1]; ++e)
-                P.csc[fill[P.ucol[e]]++] = make_int2(int(p), int(e));
+            for (int32_t s = P.rseg_ptr[p]; s < P.rseg_ptr[p + 1]; ++s)
+                for (int32_t e = P.rseg_se[s].x; e < P.rseg_se[s].y; ++e) send[e] = P.rseg_se[s].y;
+        P.cseg_end.resize(P.cptr[n]);
+        for (int64_t p = 0; p < n; ++p)
+            for (int64_t e = P.urp[p] + 1; e < P.urp[p + 1]; ++e) {
+                const int32_t at = fill[P.ucol[e]]++;
+                P.csc[at] = make_int2(int(p), int(e));
+                P.cseg_end[at] = send[e];
+            }
     }
 
     // block pattern: block (bi, bj), bi <= bj, exists iff S has an entry in it
@@ -464,9 +472,29 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
         auto& oe = tend[t];
         if (T.x == T_CHOL || T.x == T_TRSM) {
             const int32_t blk = T.y, tb = (T.x == T_CHOL) ? T.y : T.w;
-            for (int64_t r = P.ranges[blk]; r < P.ranges[blk + 1]; ++r) {
+            // Rows of a diagonal block depend on earlier rows of the same block (the pivots
+            // of their diagonal-block column run that are targets of this task).  Targets
+            // are listed in wavefront order -- by dependence level, then row -- so rows
+            // claimed one after another are mostly independent and a row's inputs are
+            // always listed before it.
+            const int32_t rb = P.ranges[blk], nr = P.ranges[blk + 1] - rb;
+            std::vector<int32_t> level(nr, -1);
+            std::vector<std::pair<int32_t, int32_t>> ord;
+            for (int64_t r = rb; r < rb + nr; ++r) {
                 int2 s = seg(r, tb);
                 if (s.y <= s.x) continue;
+                int32_t lv = 0;
+                for (int32_t e = diag_run[r].x; e < diag_run[r].y; ++e) {
+                    const int32_t lp = level[P.csc[e].x - rb];
+                    if (lp >= 0) lv = std::max(lv, lp + 1);
+                }
+                level[r - rb] = lv;
+                ord.emplace_back(lv, int32_t(r));
+            }
+            std::sort(ord.begin(), ord.end());
+            for (const auto& lr : ord) {
+                const int64_t r = lr.second;
+                int2 s = seg(r, tb);
                 out.push_back(make_int4(int(r), diag_run[r].x, diag_run[r].y, s.x));
                 oe.push_back(s.y);
             }
@@ -526,6 +554,42 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
             best = std::max(best, depth[t]);
         }
         P.critical_path = best;
+    }
+
+    // claim orders of the triangular solves: rows sorted by their depth in the row
+    // dependence DAG (forward: row i needs the rows p of column i of U; backward: row i
+    // needs the columns c > i of row i), ties by row index.  A row's inputs always have
+    // a smaller depth, so they are claimed before it.
+    {
+        std::vector<int32_t> lf(n, 0), lb(n, 0);
+        int32_t mf = 0, mb = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            int32_t d = 0;
+            for (int32_t e = P.cptr[i]; e < P.cptr[i + 1]; ++e) d = std::max(d, lf[P.csc[e].x] + 1);
+            lf[i] = d;
+            mf = std::max(mf, d);
+        }
+        for (int64_t i = n - 1; i >= 0; --i) {
+            int32_t d = 0;
+            for (int64_t e = P.urp[i] + 1; e < P.urp[i + 1]; ++e) d = std::max(d, lb[P.ucol[e]] + 1);
+            lb[i] = d;
+            mb = std::max(mb, d);
+        }
+        auto order_by = [&](const std::vector<int32_t>& lev, int32_t maxd, bool descending_ties,
+                            std::vector<int32_t>& out) {
+            std::vector<int32_t> cnt(size_t(maxd) + 2, 0);
+            for (int64_t i = 0; i < n; ++i) ++cnt[lev[i] + 1];
+            for (int32_t d = 0; d <= maxd; ++d) cnt[d + 1] += cnt[d];
+            out.resize(n);
+            for (int64_t q = 0; q < n; ++q) {
+                const int64_t i = descending_ties ? n - 1 - q : q;
+                out[cnt[lev[i]]++] = int32_t(i);
+            }
+        };
+        order_by(lf, mf, false, P.fwd_order);
+        order_by(lb, mb, true, P.bwd_order);
+        P.fwd_depth = n ? int64_t(mf) + 1 : 0;
+        P.bwd_depth = n ? int64_t(mb) + 1 : 0;
     }
 
     // algorithmic flops: per pivot p, one sqrt, |S_p|-1 divides, and two flops for each

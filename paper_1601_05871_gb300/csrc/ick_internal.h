@@ -40,6 +40,7 @@ struct HostPlan {
     // column lists of U (strictly upper): for column r, pivot rows p < r ascending
     std::vector<int32_t> cptr;      // n + 1
     std::vector<int2> csc;          // (p, position of U_pr)
+    std::vector<int32_t> cseg_end;  // per column-list entry: end of row p's segment in block(r)
     // block pattern (upper), bptr: nb + 1
     std::vector<int64_t> bptr;
     std::vector<int32_t> bcol;
@@ -53,6 +54,8 @@ struct HostPlan {
     std::vector<int4> tgt;          // (r, csc_a, csc_b, seg_begin)
     std::vector<int32_t> tgt_end;   // seg_end
     std::vector<int2> seeds;        // (task, chunk) items ready at start
+    std::vector<int32_t> fwd_order, bwd_order;  // claim orders of the triangular solves
+    int64_t fwd_depth = 0, bwd_depth = 0;        // levels of the row dependence DAGs
     int64_t total_items = 0;
     int64_t critical_path = 0;
     int64_t max_level = 0;
@@ -73,6 +76,7 @@ struct DevPlan {
     const int2* rseg_se;
     const int* cptr;
     const int2* csc;
+    const int* cseg_end;
     const int4* task;
     const int* tgt_ptr;
     const int4* tgt;
@@ -91,6 +95,8 @@ struct DevPlan {
     int* counters;         // [0] queue head, [1] queue tail, [2] status bits, [3] abort
     long long* brk_row;    // smallest breakdown row
     int* diag;             // [0] items completed, [1] timeout site
+    unsigned long long* trace;  // NULL, or 4 words per queue slot: start ns, end ns,
+                                // task | chunk << 32, SM id
 };
 
 // Status bits written by the kernels into counters[2].
@@ -112,6 +118,8 @@ struct SolvePlan {
     double* y;       // permuted work vector
     int* flag;       // per-row completion stamps of the solves
     int* counter;    // [0] forward row claim, [1] backward row claim, [2] abort/timeout
+    const int* fwd_order;  // rows in forward claim order (by dependence depth)
+    const int* bwd_order;  // rows in backward claim order
 };
 
 // Kernel entry points (numeric.cu, solve.cu).

@@ -28,7 +28,25 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
+__device__ __forceinline__ unsigned smid() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// 16-byte asynchronous copy global -> shared that is cached in L2 only (.cg), so it
+// never returns a stale L1 line of data another SM has rewritten.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 template <bool EXACT>
 __device__ __forceinline__ double sub_product(double acc, double a, double b) {
@@ -39,7 +57,8 @@ __device__ __forceinline__ double sub_product(double acc, double a, double b) {
 enum Mode { M_CHOL = 0, M_TRSM = 1, M_UPDATE = 2 };
 
 struct Smem {
-    int task, chunk, next, pad;
+    int task, chunk, next, slot;
+    unsigned long long t0;
 };
 
 // Segment [b, e) of pivot row p that lies in block column `blk`, or an empty range.
@@ -71,99 +90,219 @@ __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int loc
     return true;
 }
 
+constexpr int kHash = 256;     // per-warp open-addressing table: target column -> slot
+constexpr int kRing = 4;       // staging slots per warp: kRing - 1 pivots in flight
+constexpr int kSegStage = 64;  // source elements of one pivot staged by copies
+
+// One staged pivot segment: values and columns copied as the enclosing 16-byte
+// aligned spans, plus the 16 bytes holding U_pr when it lies outside the segment.
+struct Slot {
+    double vals[kSegStage + 2];
+    double aval[2];
+    int cols[kSegStage + 4];
+};
+
+// Per-warp shared-memory work area (16-byte multiples first for the async copies).
+struct WarpBuf {
+    Slot ring[kRing];
+    double tval[kSegCap];  // target segment values (one chunk)
+    int tcol[kSegCap];     // target segment columns
+    int hkey[kHash];       // hash keys (column, or -1)
+    short hslot[kHash];    // slot in the target chunk of each key
+};
+
+__device__ __forceinline__ int hash_of(int c) { return int((unsigned(c) * 2654435761u) >> 24); }
+
+__device__ __forceinline__ int hash_find(const WarpBuf& W, int c) {
+    int h = hash_of(c);
+    for (;;) {
+        const int k = W.hkey[h];
+        if (k == c) return W.hslot[h];
+        if (k == -1) return -1;
+        h = (h + 1) & (kHash - 1);
+    }
+}
+
+template <bool EXACT>
+__device__ __forceinline__ void apply_one(WarpBuf& W, int c, int cmin, int cmax, double a, double v) {
+    if (c >= cmin && c <= cmax) {
+        const int idx = hash_find(W, c);
+        if (idx >= 0) W.tval[idx] = sub_product<EXACT>(W.tval[idx], a, v);
+    }
+}
+
+// Issue the copies of pivot q's source segment into ring slot q % kRing.  Returns 1
+// when the slot will hold the data (or the segment is empty), 0 when the pivot row is
+// not complete yet (Chol/Trsm): then the consumer waits and loads it directly.
+template <int MODE>
+__device__ __forceinline__ int issue_pivot(const DevPlan& P, const double* U, WarpBuf& W, int q,
+                                           int p, int pos, int sb, int len, bool start_at_r,
+                                           int rbase, volatile unsigned char* done) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int pq = __shfl_sync(full, p, q), posq = __shfl_sync(full, pos, q);
+    const int sbq = __shfl_sync(full, sb, q), lq = __shfl_sync(full, len, q);
+    if (lq == 0) return 1;
+    if (MODE != M_UPDATE) {
+        int f = 0;
+        if (lane == 0) f = done[pq - rbase];
+        if (!__shfl_sync(full, f, 0)) return 0;
+        __threadfence_block();
+    }
+    Slot& S = W.ring[q % kRing];
+    const int n = min(lq, kSegStage);
+    const int vb = sbq & ~1, nv = (((sbq + n + 1) & ~1) - vb) >> 1;
+    const int cb = sbq & ~3, nc = (((sbq + n + 3) & ~3) - cb) >> 2;
+    const int total = nv + nc + (start_at_r ? 0 : 1);
+    for (int t = lane; t < total; t += 32) {
+        if (t < nv) cp_async16(&S.vals[2 * t], U + vb + 2 * t);
+        else if (t < nv + nc) cp_async16(&S.cols[4 * (t - nv)], P.ucol + cb + 4 * (t - nv));
+        else cp_async16(&S.aval[0], U + (posq & ~1));
+    }
+    return 1;
+}
+
 // One target row: r, pivots csc[ca, cb), target segment [tb, te) of row r.
 // MODE: Chol (source = pivot row's block-k segment from column r on; wait on pivot
 // rows; finalise with sqrt and scaling), Trsm (source = pivot row's block-j segment;
 // wait on pivot rows that have one; finalise by dividing by U_rr), Update (Herk/Gemm:
 // all inputs final).  start_at_r: the source segment starts at the pivot's entry in
 // column r (target block column == block of r).
+//
+// Pivots are applied one at a time in ascending order, lane l taking source elements
+// l, l+32, ...; a target column is found through a per-warp hash table.  The source
+// segments of the next kRing-1 pivots are copied asynchronously into a ring of
+// shared-memory slots while the current one is applied.  For Chol and Trsm a copy is
+// issued only once the pivot row's completion flag is seen; a pivot that was not
+// complete at issue time is waited for and loaded directly when its turn comes.
 template <int MODE, bool EXACT>
 __device__ void process_target(const DevPlan& P, double* U, int r, int ca, int cb, int tb, int te,
                                int srcblk, bool start_at_r, int rbase,
-                               volatile unsigned char* done, int* tcol, double* tval,
+                               volatile unsigned char* done, WarpBuf& W,
                                unsigned long long deadline) {
     const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
     double piv = 1.0;
     if (MODE == M_TRSM) piv = __ldcg(U + __ldg(P.urp + r));
     for (int c0 = tb; c0 < te; c0 += kSegCap) {
         const int m = min(kSegCap, te - c0);
+        for (int x = lane; x < kHash; x += 32) W.hkey[x] = -1;
         for (int x = lane; x < m; x += 32) {
-            tcol[x] = __ldg(P.ucol + c0 + x);
-            tval[x] = __ldcg(U + c0 + x);
+            W.tcol[x] = __ldg(P.ucol + c0 + x);
+            W.tval[x] = __ldcg(U + c0 + x);
         }
         __syncwarp();
-        const int cmin = tcol[0], cmax = tcol[m - 1];
+        for (int x = lane; x < m; x += 32) {
+            const int c = W.tcol[x];
+            int h = hash_of(c);
+            while (atomicCAS(&W.hkey[h], -1, c) != -1) h = (h + 1) & (kHash - 1);
+            W.hslot[h] = short(x);
+        }
+        __syncwarp();
+        const int cmin = W.tcol[0], cmax = W.tcol[m - 1];
         for (int q0 = ca; q0 < cb; q0 += 32) {
             const int nq = min(32, cb - q0);
-            int p = 0, pos = 0, sb = 0, se = 0;
+            int p = 0, pos = 0, sb = 0, len = 0;
             if (lane < nq) {
                 const int2 pe = __ldg(P.csc + q0 + lane);
                 p = pe.x;
                 pos = pe.y;
-                const int2 s = row_segment(P, p, srcblk);
-                sb = start_at_r ? pos : s.x;
-                se = s.y;
+                if (start_at_r) {
+                    sb = pos;
+                    len = __ldg(P.cseg_end + q0 + lane) - pos;
+                } else {
+                    const int2 s = row_segment(P, p, srcblk);
+                    sb = s.x;
+                    len = s.y - s.x;
+                }
+            }
+            unsigned issued = 0;
+#pragma unroll
+            for (int s = 0; s < kRing - 1; ++s) {
+                if (s < nq)
+                    issued |= unsigned(issue_pivot<MODE>(P, U, W, s, p, pos, sb, len, start_at_r, rbase,
+                                                         done)) << s;
+                cp_async_commit();
             }
             for (int q = 0; q < nq; ++q) {
-                const int pq = __shfl_sync(0xffffffffu, p, q);
-                const int posq = __shfl_sync(0xffffffffu, pos, q);
-                const int sbq = __shfl_sync(0xffffffffu, sb, q);
-                const int seq = __shfl_sync(0xffffffffu, se, q);
-                if (seq <= sbq) continue;
-                if (MODE != M_UPDATE) {
-                    int ok = 1;
-                    if (lane == 0) ok = wait_row(P, done, pq - rbase, deadline);
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (!ok) return;
-                }
-                const double upr = __ldcg(U + posq);
-                for (int e = sbq + lane; e < seq; e += 32) {
-                    const int c = __ldg(P.ucol + e);
-                    if (c < cmin || c > cmax) continue;
-                    int lo = 0, hi = m - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (tcol[mid] < c) lo = mid + 1; else hi = mid;
+                const int nxt = q + kRing - 1;
+                if (nxt < nq)
+                    issued |= unsigned(issue_pivot<MODE>(P, U, W, nxt, p, pos, sb, len, start_at_r,
+                                                         rbase, done)) << nxt;
+                cp_async_commit();
+                cp_async_wait<kRing - 1>();
+                __syncwarp();
+                const int pq = __shfl_sync(full, p, q), posq = __shfl_sync(full, pos, q);
+                const int sbq = __shfl_sync(full, sb, q), lq = __shfl_sync(full, len, q);
+                if (lq > 0) {
+                    int first_direct = 0;
+                    double a;
+                    if ((issued >> q) & 1u) {
+                        const Slot& S = W.ring[q % kRing];
+                        const int n = min(lq, kSegStage);
+                        const int vo = sbq - (sbq & ~1), co = sbq - (sbq & ~3);
+                        a = start_at_r ? S.vals[vo] : S.aval[posq & 1];
+                        for (int x = lane; x < n; x += 32)
+                            apply_one<EXACT>(W, S.cols[co + x], cmin, cmax, a, S.vals[vo + x]);
+                        first_direct = n;
+                    } else {
+                        int ok = 1;
+                        if (lane == 0) ok = wait_row(P, done, pq - rbase, deadline);
+                        if (!__shfl_sync(full, ok, 0)) {
+                            cp_async_wait<0>();
+                            return;
+                        }
+                        a = __ldcg(U + posq);
                     }
-                    if (tcol[lo] == c) tval[lo] = sub_product<EXACT>(tval[lo], upr, __ldcg(U + e));
+                    for (int o = first_direct + lane; o < lq; o += 32)
+                        apply_one<EXACT>(W, __ldg(P.ucol + sbq + o), cmin, cmax, a, __ldcg(U + sbq + o));
                 }
                 __syncwarp();
             }
+            cp_async_wait<0>();
+            __syncwarp();
         }
         if (MODE == M_CHOL) {
             if (c0 == tb) {
                 if (lane == 0) {
-                    const double d = tval[0];
+                    const double d = W.tval[0];
                     if (!(d > 0.0) || !isfinite(d)) {
                         atomicOr(P.counters + 2, kStBreakdown);
                         atomicMin(P.brk_row, (long long)r);
                     }
                     piv = sqrt(d);
-                    tval[0] = piv;
+                    W.tval[0] = piv;
                 }
-                piv = __shfl_sync(0xffffffffu, piv, 0);
+                piv = __shfl_sync(full, piv, 0);
                 __syncwarp();
-                for (int x = 1 + lane; x < m; x += 32) tval[x] = tval[x] / piv;
+                for (int x = 1 + lane; x < m; x += 32) W.tval[x] = W.tval[x] / piv;
             } else {
-                for (int x = lane; x < m; x += 32) tval[x] = tval[x] / piv;
+                for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / piv;
             }
         } else if (MODE == M_TRSM) {
-            for (int x = lane; x < m; x += 32) tval[x] = tval[x] / piv;
+            for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / piv;
         }
         __syncwarp();
-        for (int x = lane; x < m; x += 32) __stcg(U + c0 + x, tval[x]);
+        for (int x = lane; x < m; x += 32) __stcg(U + c0 + x, W.tval[x]);
         __syncwarp();
     }
 }
 
+// Dynamic shared memory of one CTA: scheduler words, per-row flags, per-warp buffers.
+constexpr size_t kSmemHead = 32;
+constexpr size_t kWarpBytes = (sizeof(WarpBuf) + 15) / 16 * 16;
+constexpr size_t smem_bytes(int warps) { return kSmemHead + kMaxBlockRows + size_t(warps) * kWarpBytes; }
+static_assert((kSmemHead + kMaxBlockRows) % 16 == 0, "warp buffers must start 16-byte aligned");
+static_assert(sizeof(Slot) % 16 == 0, "staging slots must be 16-byte multiples");
+
 template <int WARPS, bool EXACT>
 __global__ void __launch_bounds__(WARPS * 32)
 numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
-    __shared__ Smem sm;
-    __shared__ unsigned char s_done[kMaxBlockRows];
-    __shared__ int s_tcol[WARPS][kSegCap];
-    __shared__ double s_tval[WARPS][kSegCap];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    unsigned char* s_done = smem_raw + kSmemHead;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpBuf& W = *reinterpret_cast<WarpBuf*>(smem_raw + kSmemHead + kMaxBlockRows + size_t(warp) * kWarpBytes);
     double* U = static_cast<double*>(P.uval);
     const unsigned long long deadline = gtimer() + timeout_ns;
     volatile unsigned char* done = s_done;
@@ -191,6 +330,8 @@ numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
             }
             sm.task = task;
             sm.chunk = chunk;
+            sm.slot = slot;
+            if (P.trace) sm.t0 = gtimer();
         }
         __syncthreads();
         const int task = sm.task, chunk = sm.chunk;
@@ -213,10 +354,10 @@ numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
                 const int gend = __ldg(P.tgt_end + t0 + idx);
                 if (T.x == T_CHOL)
                     process_target<M_CHOL, EXACT>(P, U, g.x, g.y, g.z, g.w, gend, blk, true, rbase,
-                                                  done, s_tcol[warp], s_tval[warp], deadline);
+                                                  done, W, deadline);
                 else
                     process_target<M_TRSM, EXACT>(P, U, g.x, g.y, g.z, g.w, gend, T.w, false, rbase,
-                                                  done, s_tcol[warp], s_tval[warp], deadline);
+                                                  done, W, deadline);
                 __threadfence_block();
                 __syncwarp();
                 if (lane == 0) done[g.x - rbase] = 1;
@@ -228,8 +369,12 @@ numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
             for (int idx = first + warp; idx < last; idx += WARPS) {
                 const int4 g = __ldg(P.tgt + t0 + idx);
                 const int gend = __ldg(P.tgt_end + t0 + idx);
-                process_target<M_UPDATE, EXACT>(P, U, g.x, g.y, g.z, g.w, gend, T.w, herk, 0, done,
-                                                s_tcol[warp], s_tval[warp], deadline);
+                if (herk)
+                    process_target<M_UPDATE, EXACT>(P, U, g.x, g.y, g.z, g.w, gend, T.w, true, 0, done,
+                                                    W, deadline);
+                else
+                    process_target<M_UPDATE, EXACT>(P, U, g.x, g.y, g.z, g.w, gend, T.w, false, 0, done,
+                                                    W, deadline);
             }
         }
         __threadfence();
@@ -241,6 +386,13 @@ numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
             if (lane == 0) {
                 last = atomicSub(P.items_left + task, 1) == 1;
                 atomicAdd(P.diag + 0, 1);
+                if (P.trace) {
+                    unsigned long long* rec = P.trace + 4ull * sm.slot;
+                    rec[0] = sm.t0;
+                    rec[1] = gtimer();
+                    rec[2] = (unsigned long long)(unsigned)task | ((unsigned long long)(unsigned)chunk << 32);
+                    rec[3] = smid();
+                }
             }
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
@@ -302,18 +454,25 @@ __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double
 template <int WARPS, bool EXACT>
 cudaError_t launch_t(const DevPlan& P, int grid, int epoch, unsigned long long timeout_ns,
                      cudaStream_t s) {
-    numeric_persistent<WARPS, EXACT><<<grid, WARPS * 32, 0, s>>>(P, epoch, timeout_ns);
+    numeric_persistent<WARPS, EXACT><<<grid, WARPS * 32, smem_bytes(WARPS), s>>>(P, epoch, timeout_ns);
     return cudaGetLastError();
+}
+
+template <int WARPS, bool EXACT>
+cudaError_t occupancy_t(int* blocks) {
+    cudaError_t e = cudaFuncSetAttribute(numeric_persistent<WARPS, EXACT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem_bytes(WARPS)));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, numeric_persistent<WARPS, EXACT>,
+                                                         WARPS * 32, smem_bytes(WARPS));
 }
 
 }  // namespace
 
 cudaError_t numeric_blocks_per_sm(int warps, bool exact, int* blocks) {
-    if (warps == 8)
-        return exact ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, numeric_persistent<8, true>, 256, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, numeric_persistent<8, false>, 256, 0);
-    return exact ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, numeric_persistent<16, true>, 512, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, numeric_persistent<16, false>, 512, 0);
+    if (warps == 8) return exact ? occupancy_t<8, true>(blocks) : occupancy_t<8, false>(blocks);
+    return exact ? occupancy_t<16, true>(blocks) : occupancy_t<16, false>(blocks);
 }
 
 cudaError_t launch_numeric_prepare(const DevPlan& P, const double* avals, double shift_alpha,

@@ -3,11 +3,13 @@
 //
 // ic_apply: z = P (U^T U)^{-1} P^T r.  The forward solve U^T y = P^T r gathers column i
 // of U (the column lists built by the symbolic phase); the backward solve U z = y
-// gathers row i of U.  Both are synchronisation-free: warps claim rows in dependency
-// order from an atomic counter (ascending for the forward solve, descending for the
-// backward one) and spin, with a bounded wait, on per-row completion stamps of the
-// rows they depend on.  Because claims are ordered, the lowest unfinished claimed row
-// always has its inputs and no warp waits on a row that no running warp owns.
+// gathers row i of U.  Both are synchronisation-free: warps claim rows from an atomic
+// counter in an order precomputed by the symbolic phase (rows sorted by their depth in
+// the solve's row dependence DAG) and spin, with a bounded wait, on per-row completion
+// stamps of the rows they depend on.  A row's inputs have smaller depth and are claimed
+// before it, so the earliest unfinished claimed row always has its inputs and no warp
+// waits on a row that no running warp owns; rows of equal depth (independent ND
+// subtrees, wavefronts inside a part) run concurrently.
 #include <cstdint>
 
 #include "ick_internal.h"
@@ -48,10 +50,11 @@ forward_solve(SolvePlan S, const double* __restrict__ r, int stamp, unsigned lon
     const int lane = threadIdx.x & 31;
     const unsigned long long deadline = gtimer() + timeout_ns;
     for (;;) {
-        int i = 0;
-        if (lane == 0) i = atomicAdd(S.counter + 0, 1);
-        i = __shfl_sync(0xffffffffu, i, 0);
-        if (i >= S.n) break;
+        int t = 0;
+        if (lane == 0) t = atomicAdd(S.counter + 0, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= S.n) break;
+        const int i = __ldg(S.fwd_order + t);
         const int a = __ldg(S.cptr + i), b = __ldg(S.cptr + i + 1);
         double acc = 0.0;
         bool ok = true;
@@ -79,8 +82,8 @@ backward_solve(SolvePlan S, double* __restrict__ z, int stamp, unsigned long lon
         int t = 0;
         if (lane == 0) t = atomicAdd(S.counter + 1, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
-        const int i = S.n - 1 - t;
-        if (i < 0) break;
+        if (t >= S.n) break;
+        const int i = __ldg(S.bwd_order + t);
         const long long a = __ldg(S.urp + i), b = __ldg(S.urp + i + 1);
         double acc = 0.0;
         bool ok = true;

@@ -43,7 +43,7 @@ class ic_stats_t(C.Structure):
                 ("nblocks", C.c_int64), ("ntasks", C.c_int64), ("ntasks_type", C.c_int64 * 4),
                 ("nitems", C.c_int64), ("critical_path", C.c_int64), ("max_level", C.c_int64),
                 ("flops", C.c_double), ("bytes", C.c_double), ("symbolic_s", C.c_double),
-                ("grid_ctas", C.c_int64)]
+                ("grid_ctas", C.c_int64), ("solve_depth", C.c_int64 * 2)]
 
 
 def load():
@@ -73,6 +73,8 @@ def load():
         "ic_reset_timing": (I, [P]),
         "ic_get_timing": (I, [P, P]),
         "ic_test_hold_task": (I, [P, I64, I]),
+        "ic_set_trace": (I, [P, I]),
+        "ic_get_trace": (I, [P, P]),
         "ic_destroy": (None, [P]),
         "ic_strerror": (C.c_char_p, [I]),
         "ic_last_error": (C.c_char_p, []),
@@ -222,6 +224,7 @@ def ic_stats(h):
     _check(load().ic_stats(h.ptr, C.byref(s)))
     d = {f: getattr(s, f) for f, _ in s._fields_}
     d["ntasks_type"] = list(s.ntasks_type)
+    d["solve_depth"] = list(s.solve_depth)
     return d
 
 
@@ -316,6 +319,18 @@ def ic_get_timing(h):
 
 def ic_test_hold_task(h, t, extra=1):
     _check(load().ic_test_hold_task(h.ptr, int(t), int(extra)))
+
+
+def ic_set_trace(h, on=True):
+    _check(load().ic_set_trace(h.ptr, int(bool(on))))
+
+
+def ic_get_trace(h):
+    """(nitems, 4) uint64: start ns, end ns, task | chunk << 32, SM id per queue slot."""
+    n = ic_stats(h)["nitems"]
+    out = np.zeros((n, 4), dtype=np.uint64)
+    _check(load().ic_get_trace(h.ptr, _p(out)))
+    return out
 
 
 def ic_destroy(h):
