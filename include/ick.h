@@ -146,6 +146,24 @@ int ic_numeric(ic_handle* h, const void* values, void* stream, int64_t* breakdow
  * Errors: IC_ERR_ARG, IC_ERR_STATE (no successful ic_numeric yet), IC_ERR_CUDA. */
 int ic_apply(ic_handle* h, const void* r, void* z, void* stream);
 
+/* The same preconditioner application as ic_apply, for callers that cannot allocate
+ * GPU memory where they apply it: code running while a stream is captured into a CUDA
+ * graph (cudaMalloc is not allowed during capture), code whose device memory is owned
+ * by another framework's allocator, or loops that must never reach the allocator.
+ * The paper has no counterpart; this is an interface convenience of this library.
+ * The call allocates nothing and calls no allocating routine: the solves' scratch (the
+ * permuted work vector, per-row completion stamps and claim counters) lives in one
+ * file-scope device array for at most 1,048,576 rows (about 12 MB), which every GPU
+ * that loads the library keeps until the process exits.  The first call on a device
+ * looks up that array's device address (once per device, with the device current),
+ * so make it before any stream capture begins.  All calls share the array and it keeps
+ * the last call's contents (counters are cleared at the start of each call): calls
+ * that overlap on the GPU -- on different streams or from different threads, for any
+ * handle -- race, and the caller must serialise them.  r and z: as for ic_apply.
+ * Errors: IC_ERR_ARG (NULL or aliased vectors, or n above 1,048,576 rows),
+ * IC_ERR_STATE (no successful ic_numeric yet), IC_ERR_CUDA. */
+int ic_apply_static(ic_handle* h, const void* r, void* z, void* stream);
+
 /* Preconditioned conjugate gradients on A x = b with M = L L^T (textbook PCG, x0 = 0,
  * stop when ||r||_2 / ||b||_2 <= tol).  A's pattern is the one given to ic_symbolic.
  *   A_vals  device, nnz(A) doubles in A's CSR order.

@@ -9,6 +9,7 @@ from .ick import (  # noqa: F401
     ic_symbolic,
     ic_numeric,
     ic_apply,
+    ic_apply_static,
     pcg_solve,
     ic_get_factor,
     ic_stats,

@@ -2,6 +2,7 @@
 // the symbolic plan, and the host orchestration of the numeric, apply and PCG kernels.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -381,6 +382,33 @@ int ic_apply(ic_handle* h, const void* r, void* z, void* stream) {
         CK(cudaEventRecord(h->ev[4], s));
         h->apply_pending = true;
     }
+    return IC_OK;
+}
+
+int ic_apply_static(ic_handle* h, const void* r, void* z, void* stream) {
+    if (!h || ((!r || !z) && h->hp.n > 0)) return fail(IC_ERR_ARG, "NULL argument");
+    if (r == z && h->hp.n > 0) return fail(IC_ERR_ARG, "r and z may not alias");
+    if (!h->factored) return fail(IC_ERR_STATE, "ic_apply_static before a successful ic_numeric");
+    if (h->hp.n > static_apply_max_rows())
+        return fail(IC_ERR_ARG, "ic_apply_static: n = " + std::to_string(h->hp.n) +
+                                    " exceeds the static scratch limit of " +
+                                    std::to_string(static_apply_max_rows()) + " rows; use ic_apply");
+    if (h->hp.n == 0) return IC_OK;
+    DeviceGuard g(h->device);
+    // process-wide call counter: completion stamps 2*epoch and 2*epoch+1 never repeat
+    // (the stamps are cleared and the count restarts long before int overflow)
+    static std::atomic<int> calls{0};
+    int epoch = ++calls;
+    bool clear = false;
+    if (epoch >= (1 << 29)) {
+        calls = 1;
+        epoch = 1;
+        clear = true;
+    }
+    const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
+    CK(launch_apply_static(h->sp, static_cast<const double*>(r), static_cast<double*>(z), epoch,
+                           tmo, h->grid_apply, static_cast<cudaStream_t>(stream), clear));
+    h->tm.launches += 2;
     return IC_OK;
 }
 

@@ -134,6 +134,11 @@ cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epo
 cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, double* y,
                         cudaStream_t s);
 cudaError_t apply_blocks_per_sm(int* blocks);
+// Allocation-free application (solve.cu): scratch in a file-scope device array.
+int static_apply_max_rows();
+cudaError_t launch_apply_static(const SolvePlan& S, const double* r, double* z, int epoch,
+                                unsigned long long timeout_ns, int grid, cudaStream_t s,
+                                bool clear_stamps);
 
 // PCG vector kernels (solve.cu): scalars live in a small device struct.  Reductions
 // are two-stage and deterministic: nparts block partials, then one block sums them in

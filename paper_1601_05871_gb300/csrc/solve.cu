@@ -228,6 +228,73 @@ cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epo
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------
+// Allocation-free variant of the preconditioner application (ic_apply_static).
+//
+// Some callers cannot call cudaMalloc where they apply the preconditioner: code that
+// runs while a stream is being captured into a CUDA graph (allocation is not
+// permitted during capture), code inside frameworks that own the whole device memory
+// budget through their own allocator, or latency-critical loops that must not touch
+// the allocator.  For them the solve's scratch -- the permuted work vector, the
+// per-row completion stamps and the two row-claim counters plus the abort word --
+// lives in one file-scope device array, sized for at most kStaticApplyRows rows.
+// Every GPU that loads the library keeps this array until the process exits; all
+// calls share it, so calls that overlap on the GPU (on different streams, or from
+// different threads) race and must be serialised by the caller.  The array keeps the
+// contents of the last call: the claim counters and the abort word are cleared at the
+// start of every call, and the completion stamps never need clearing because each
+// call uses stamps no earlier call has written (a process-wide call counter).
+constexpr int kStaticApplyRows = 1 << 20;
+constexpr size_t kStaticApplyBytes =
+    size_t(kStaticApplyRows) * sizeof(double) + size_t(kStaticApplyRows) * sizeof(int) + 16;
+
+static __device__ __align__(256) unsigned char g_apply_scratch[kStaticApplyBytes];
+
+int static_apply_max_rows() { return kStaticApplyRows; }
+
+// Device address of g_apply_scratch on the current device (the symbol's name is only
+// a host-side stand-in).  Looked up once per device, with that device current.
+cudaError_t static_apply_scratch(void** out) {
+    static void* addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_apply_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_apply_static(const SolvePlan& H, const double* r, double* z, int epoch,
+                                unsigned long long timeout_ns, int grid, cudaStream_t s,
+                                bool clear_stamps) {
+    if (H.n == 0) return cudaSuccess;
+    if (H.n > kStaticApplyRows) return cudaErrorInvalidValue;
+    void* base = nullptr;
+    cudaError_t e = static_apply_scratch(&base);
+    if (e != cudaSuccess) return e;
+    SolvePlan S = H;
+    S.y = static_cast<double*>(base);
+    S.flag = reinterpret_cast<int*>(static_cast<unsigned char*>(base) + size_t(kStaticApplyRows) * sizeof(double));
+    S.counter = reinterpret_cast<int*>(static_cast<unsigned char*>(base) +
+                                       size_t(kStaticApplyRows) * (sizeof(double) + sizeof(int)));
+    if (clear_stamps) {
+        e = cudaMemsetAsync(S.flag, 0, size_t(kStaticApplyRows) * sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(S.counter, 0, 3 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    forward_solve<<<grid, kApplyThreads, 0, s>>>(S, r, 2 * epoch, timeout_ns);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    backward_solve<<<grid, kApplyThreads, 0, s>>>(S, z, 2 * epoch + 1, timeout_ns);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, double* y,
                         cudaStream_t s) {
     if (S.n == 0) return cudaSuccess;

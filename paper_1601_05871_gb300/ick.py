@@ -61,6 +61,7 @@ def load():
         "ic_symbolic": (I, [P, I, P, P, I64, P, P]),
         "ic_numeric": (I, [P, P, P, P]),
         "ic_apply": (I, [P, P, P, P]),
+        "ic_apply_static": (I, [P, P, P, P]),
         "pcg_solve": (I, [P, P, P, P, D, I, P, P, P]),
         "ic_get_factor": (I, [P, P, P, P, P]),
         "ic_stats": (I, [P, P]),
@@ -206,6 +207,12 @@ def ic_numeric(h, values, stream=None):
 
 def ic_apply(h, r, z, stream=None):
     _check(load().ic_apply(h.ptr, _p(r), _p(z), _stream(stream)))
+
+
+def ic_apply_static(h, r, z, stream=None):
+    """ic_apply without any allocation: scratch in the library's static device array
+    (at most 1,048,576 rows; calls must not overlap on the GPU)."""
+    _check(load().ic_apply_static(h.ptr, _p(r), _p(z), _stream(stream)))
 
 
 def pcg_solve(h, A_vals, b, x, tol=1e-8, maxit=10000, stream=None, raise_noconv=True):
