@@ -70,7 +70,10 @@ typedef struct {
     int threads;       /* [0 = all] host threads for the symbolic phase                  */
     int host_only;     /* [0] 1: ic_symbolic builds the plan in host memory only (no GPU
                           needed); such a handle serves the ic_get_* and ic_stats calls   */
-    int reserved[5];
+    int solve_ctas_per_sm; /* [3] CTAs of 8 warps per SM for the triangular-solve
+                              kernels (fewer CTAs poll less; capped by occupancy)   */
+    int solve_lanes;   /* [32] lanes per row in the ic_apply / pcg_solve solves: 4|8|16|32 */
+    int reserved[3];
 } ic_opts;
 
 typedef struct {

@@ -115,6 +115,8 @@ ic_opts normalise(const ic_opts* o) {
     if (r.warps_per_cta == 0) r.warps_per_cta = 16;
     if (r.rows_per_item == 0) r.rows_per_item = 32;
     if (r.timeout_s == 0.0) r.timeout_s = 10.0;
+    if (r.solve_lanes == 0) r.solve_lanes = 32;
+    if (r.solve_ctas_per_sm == 0) r.solve_ctas_per_sm = 3;
     return r;
 }
 
@@ -182,6 +184,12 @@ int upload_plan(ic_handle* h) {
     S.cptr = D.cptr;
     S.csc = D.csc;
     S.uval = uval;
+    S.lanes_per_row = h->opts.solve_lanes;
+    if ((st = h->upload(&S.fwd_pad, P.fwd_pad))) return st;
+    if ((st = h->upload(&S.bwd_pad, P.bwd_pad))) return st;
+    S.nfwd_pad = int(P.fwd_pad.size());
+    S.nbwd_pad = int(P.bwd_pad.size());
+    if ((st = h->alloc(&S.rdiag, size_t(P.n)))) return st;
     {
         const int32_t* dperm = nullptr;
         if ((st = h->upload(&dperm, P.perm))) return st;
@@ -195,7 +203,7 @@ int upload_plan(ic_handle* h) {
         if ((st = h->upload(&S.fwd_order, P.fwd_order))) return st;
         if ((st = h->upload(&S.bwd_order, P.bwd_order))) return st;
     }
-    if ((st = h->alloc(&S.y, size_t(P.n)))) return st;
+    if ((st = h->alloc(&S.y, 2 * size_t(P.n)))) return st;  // forward and backward results
     if ((st = h->alloc(&S.flag, size_t(P.n)))) return st;
     CK(cudaMemset(S.flag, 0, size_t(P.n) * sizeof(int)));
     if ((st = h->alloc(&S.counter, 4))) return st;
@@ -217,6 +225,7 @@ int upload_plan(ic_handle* h) {
     if (bpsm < 1) return fail(IC_ERR_CUDA, "numeric kernel cannot be resident");
     h->grid_numeric = sms * bpsm;
     CK(apply_blocks_per_sm(&bpsm));
+    if (h->opts.solve_ctas_per_sm > 0 && h->opts.solve_ctas_per_sm < bpsm) bpsm = h->opts.solve_ctas_per_sm;
     h->grid_apply = sms * (bpsm < 1 ? 1 : bpsm);
     CK(cudaDeviceSynchronize());
     return IC_OK;
@@ -280,7 +289,9 @@ int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64
             delete h;
             return fail(IC_ERR_ARG, "dtype: only IC_F64 is available");
         }
-        if (h->opts.rows_per_item < 1 || h->opts.timeout_s < 0) {
+        if (h->opts.rows_per_item < 1 || h->opts.timeout_s < 0 ||
+            (h->opts.solve_lanes != 4 && h->opts.solve_lanes != 8 && h->opts.solve_lanes != 16 &&
+             h->opts.solve_lanes != 32)) {
             delete h;
             return fail(IC_ERR_ARG, "rows_per_item / timeout_s out of range");
         }
@@ -335,6 +346,8 @@ int ic_numeric(ic_handle* h, const void* values, void* stream, int64_t* breakdow
         ++h->tm.launches;
     }
     if (h->timing) CK(cudaEventRecord(h->ev[2], s));
+    CK(launch_solve_prepare(h->sp, s));
+    ++h->tm.launches;
     CK(cudaMemcpyAsync(h->h_counters, h->dp.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->h_counters + 4, h->dp.diag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->h_brk, h->dp.brk_row, sizeof(long long), cudaMemcpyDeviceToHost, s));

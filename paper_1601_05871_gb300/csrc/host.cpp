@@ -588,6 +588,22 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
         };
         order_by(lf, mf, false, P.fwd_order);
         order_by(lb, mb, true, P.bwd_order);
+        // padded copies: every level's run is filled up to a multiple of kClaimPad with
+        // -1, so an aligned claim of up to kClaimPad consecutive positions never mixes
+        // rows of two levels (rows claimed by one warp are then independent)
+        auto pad = [&](const std::vector<int32_t>& order, const std::vector<int32_t>& lev,
+                       std::vector<int32_t>& out) {
+            out.clear();
+            out.reserve(order.size() + order.size() / 2);
+            for (size_t q = 0; q < order.size(); ++q) {
+                out.push_back(order[q]);
+                const bool last = q + 1 == order.size() || lev[order[q + 1]] != lev[order[q]];
+                if (last)
+                    while (out.size() % kClaimPad) out.push_back(-1);
+            }
+        };
+        pad(P.fwd_order, lf, P.fwd_pad);
+        pad(P.bwd_order, lb, P.bwd_pad);
         P.fwd_depth = n ? int64_t(mf) + 1 : 0;
         P.bwd_depth = n ? int64_t(mb) + 1 : 0;
     }

@@ -17,6 +17,7 @@ enum TaskType : int { T_CHOL = 0, T_TRSM = 1, T_HERK = 2, T_GEMM = 3 };
 
 constexpr int kMaxBlockRows = 8192;  // per-row completion flags of one block live in shared memory
 constexpr int kSegCap = 128;         // target-segment entries staged per warp in shared memory
+constexpr int kClaimPad = 8;         // level runs of the padded solve orders are multiples of this
 
 // Everything the symbolic phase produces, in host memory.
 struct HostPlan {
@@ -55,6 +56,7 @@ struct HostPlan {
     std::vector<int32_t> tgt_end;   // seg_end
     std::vector<int2> seeds;        // (task, chunk) items ready at start
     std::vector<int32_t> fwd_order, bwd_order;  // claim orders of the triangular solves
+    std::vector<int32_t> fwd_pad, bwd_pad;      // the same, each level padded with -1
     int64_t fwd_depth = 0, bwd_depth = 0;        // levels of the row dependence DAGs
     int64_t total_items = 0;
     int64_t critical_path = 0;
@@ -120,6 +122,11 @@ struct SolvePlan {
     int* counter;    // [0] forward row claim, [1] backward row claim, [2] abort/timeout
     const int* fwd_order;  // rows in forward claim order (by dependence depth)
     const int* bwd_order;  // rows in backward claim order
+    const int* fwd_pad;    // padded claim orders (-1: empty slot) and their lengths
+    const int* bwd_pad;
+    int nfwd_pad, nbwd_pad;
+    double* rdiag;         // 1 / U_ii, computed after each numeric factorization
+    int lanes_per_row;     // 4, 8, 16 or 32 lanes per row in the ic_apply solves
 };
 
 // Kernel entry points (numeric.cu, solve.cu).
@@ -134,6 +141,7 @@ cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epo
 cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, double* y,
                         cudaStream_t s);
 cudaError_t apply_blocks_per_sm(int* blocks);
+cudaError_t launch_solve_prepare(const SolvePlan& S, cudaStream_t s);
 // Allocation-free application (solve.cu): scratch in a file-scope device array.
 int static_apply_max_rows();
 cudaError_t launch_apply_static(const SolvePlan& S, const double* r, double* z, int epoch,

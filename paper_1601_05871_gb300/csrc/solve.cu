@@ -104,6 +104,137 @@ backward_solve(SolvePlan S, double* __restrict__ z, int stamp, unsigned long lon
     }
 }
 
+// Solves of ic_apply (and pcg_solve).  Same claim orders and the same per-row sums as
+// the kernels above, but a row's value is its own completion flag: the work vectors
+// are filled with the bit pattern kUnset (all ones, a NaN that arithmetic does not
+// produce) before the launch, a row's value is published with one 8-byte store, and a
+// reader polls the value itself.  There is no separate flag store and no fence, so a
+// dependence costs one write and one read of L2 instead of two of each.
+constexpr long long kUnset = -1LL;
+
+__device__ __forceinline__ double publishable(double v) {
+    return __double_as_longlong(v) == kUnset ? __longlong_as_double(0x7fffffffffffffffLL) : v;
+}
+
+// Value of x[i] once it is set; false (and 0) on timeout or abort.
+__device__ __forceinline__ double await_value(const double* x, int i, int* abort_word,
+                                              unsigned long long deadline, bool& ok) {
+    const volatile long long* p = reinterpret_cast<const volatile long long*>(x + i);
+    long long b = *p;
+    unsigned spins = 0;
+    while (b == kUnset) {
+        if ((++spins & 255) == 0) {
+            if (*(volatile int*)abort_word || gtimer() > deadline) {
+                atomicExch(abort_word, 1);
+                ok = false;
+                return 0.0;
+            }
+        }
+        __nanosleep(16);
+        b = *p;
+    }
+    return __longlong_as_double(b);
+}
+
+// G lanes per row, 32/G rows per warp: on GB300 an FP64 warp instruction occupies the
+// SM's narrow FP64 pipe for the same time however many lanes are active, so packing
+// several rows into each FMA and reduction step cuts the FP64 instructions per row.
+// Rows of one warp are claimed together (32/G consecutive positions of the padded
+// claim order, whose level runs are multiples of 8), so they always belong to one
+// dependence level and never wait on each other: a warp-wide reconvergence before a
+// row is published can then never block the row's own consumer.  The diagonal is
+// applied as a precomputed reciprocal.
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+    const int lane = threadIdx.x & 31;
+    const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kApplyThreads)
+forward_solve_v(SolvePlan S, const double* __restrict__ r, double* yv, unsigned long long timeout_ns) {
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane / G, sl = lane % G;
+    const unsigned long long deadline = gtimer() + timeout_ns;
+    bool ok = true;
+    for (;;) {
+        int t0 = 0;
+        if (lane == 0) t0 = atomicAdd(S.counter + 0, R);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= S.nfwd_pad) break;
+        const int t = t0 + sub;
+        double acc = 0.0;
+        int i = -1;
+        double rhs = 0.0, rd = 0.0;  // loaded before the waits: off the dependence chain
+        if ((i = __ldg(S.fwd_pad + t)) >= 0) {
+            if (sl == 0) {
+                rhs = __ldg(r + __ldg(S.perm + i));
+                rd = __ldg(S.rdiag + i);
+            }
+            const int a = __ldg(S.cptr + i), b = __ldg(S.cptr + i + 1);
+            for (int e = a + sl; e < b; e += G) {
+                const int2 pe = __ldg(S.csc + e);
+                const double u = __ldg(S.uval + pe.y);
+                acc = fma(u, ok ? await_value(yv, pe.x, S.counter + 2, deadline, ok) : 0.0, acc);
+            }
+        }
+        acc = group_sum<G>(acc);
+        if (sl == 0 && i >= 0) {
+            const double v = (rhs - acc) * rd;
+            *reinterpret_cast<volatile double*>(yv + i) = publishable(v);
+        }
+        if (__any_sync(0xffffffffu, !ok)) break;
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kApplyThreads)
+backward_solve_v(SolvePlan S, const double* yv, double* zv, double* __restrict__ z,
+                 unsigned long long timeout_ns) {
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane / G, sl = lane % G;
+    const unsigned long long deadline = gtimer() + timeout_ns;
+    bool ok = true;
+    for (;;) {
+        int t0 = 0;
+        if (lane == 0) t0 = atomicAdd(S.counter + 1, R);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= S.nbwd_pad) break;
+        const int t = t0 + sub;
+        double acc = 0.0;
+        int i = -1;
+        double rhs = 0.0, rd = 0.0;
+        int dst = 0;
+        if ((i = __ldg(S.bwd_pad + t)) >= 0) {
+            if (sl == 0) {
+                rhs = __ldcg(yv + i);
+                rd = __ldg(S.rdiag + i);
+                dst = __ldg(S.perm + i);
+            }
+            const long long a = __ldg(S.urp + i), b = __ldg(S.urp + i + 1);
+            for (long long e = a + 1 + sl; e < b; e += G) {
+                const int c = __ldg(S.ucol + e);
+                const double u = __ldg(S.uval + e);
+                acc = fma(u, ok ? await_value(zv, c, S.counter + 2, deadline, ok) : 0.0, acc);
+            }
+        }
+        acc = group_sum<G>(acc);
+        if (sl == 0 && i >= 0) {
+            const double v = (rhs - acc) * rd;
+            z[dst] = v;
+            *reinterpret_cast<volatile double*>(zv + i) = publishable(v);
+        }
+        if (__any_sync(0xffffffffu, !ok)) break;
+    }
+}
+
+__global__ void rdiag_kernel(SolvePlan S) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x)
+        S.rdiag[i] = 1.0 / S.uval[S.urp[i]];
+}
+
 // y = A x with G threads per row (G in {4, 8, 16, 32}).
 template <int G>
 __global__ void __launch_bounds__(256)
@@ -220,11 +351,41 @@ cudaError_t apply_blocks_per_sm(int* blocks) {
 cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epoch,
                          unsigned long long timeout_ns, int grid, cudaStream_t s) {
     if (S.n == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(S.counter, 0, 2 * sizeof(int), s);
+    (void)epoch;
+    // S.y holds 2n doubles: the forward result, then the backward result
+    cudaError_t e = cudaMemsetAsync(S.y, 0xff, 2 * size_t(S.n) * sizeof(double), s);
     if (e != cudaSuccess) return e;
-    forward_solve<<<grid, kApplyThreads, 0, s>>>(S, r, 2 * epoch, timeout_ns);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    backward_solve<<<grid, kApplyThreads, 0, s>>>(S, z, 2 * epoch + 1, timeout_ns);
+    e = cudaMemsetAsync(S.counter, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    switch (S.lanes_per_row) {
+        case 4:
+            forward_solve_v<4><<<grid, kApplyThreads, 0, s>>>(S, r, S.y, timeout_ns);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            backward_solve_v<4><<<grid, kApplyThreads, 0, s>>>(S, S.y, S.y + S.n, z, timeout_ns);
+            break;
+        case 16:
+            forward_solve_v<16><<<grid, kApplyThreads, 0, s>>>(S, r, S.y, timeout_ns);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            backward_solve_v<16><<<grid, kApplyThreads, 0, s>>>(S, S.y, S.y + S.n, z, timeout_ns);
+            break;
+        case 32:
+            forward_solve_v<32><<<grid, kApplyThreads, 0, s>>>(S, r, S.y, timeout_ns);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            backward_solve_v<32><<<grid, kApplyThreads, 0, s>>>(S, S.y, S.y + S.n, z, timeout_ns);
+            break;
+        default:
+            forward_solve_v<8><<<grid, kApplyThreads, 0, s>>>(S, r, S.y, timeout_ns);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            backward_solve_v<8><<<grid, kApplyThreads, 0, s>>>(S, S.y, S.y + S.n, z, timeout_ns);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_prepare(const SolvePlan& S, cudaStream_t s) {
+    if (S.n == 0) return cudaSuccess;
+    int g = (S.n + 255) / 256;
+    rdiag_kernel<<<g > 4096 ? 4096 : g, 256, 0, s>>>(S);
     return cudaGetLastError();
 }
 
@@ -300,7 +461,8 @@ cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, d
     if (S.n == 0) return cudaSuccess;
     // threads per row from the average row length
     const double avg = double(S.nnz_a) / double(S.n);
-    const int G = avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32;
+    // few lanes per row: fewer FP64 reduction instructions per row (narrow FP64 pipe)
+    const int G = avg <= 20 ? 4 : avg <= 48 ? 8 : avg <= 96 ? 16 : 32;
     long long blocks = ((long long)S.n * G + 255) / 256;
     const int grid = int(blocks > 65536 ? 65536 : blocks);
     switch (G) {

@@ -35,7 +35,7 @@ class ic_opts(C.Structure):
     _fields_ = [("block_rows", C.c_int), ("dtype", C.c_int), ("warps_per_cta", C.c_int),
                 ("rows_per_item", C.c_int), ("timeout_s", C.c_double), ("shift_alpha", C.c_double),
                 ("exact", C.c_int), ("threads", C.c_int), ("host_only", C.c_int),
-                ("reserved", C.c_int * 5)]
+                ("solve_ctas_per_sm", C.c_int), ("solve_lanes", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class ic_stats_t(C.Structure):
@@ -175,14 +175,14 @@ class Handle:
 
 def ic_symbolic(rowptr, colind, k, perm=None, ranges=None, *, block_rows=0, dtype=IC_F64,
                 warps_per_cta=0, rows_per_item=0, timeout_s=0.0, shift_alpha=0.0, exact=0,
-                threads=0, host_only=0):
+                threads=0, host_only=0, solve_ctas_per_sm=0, solve_lanes=0):
     L = load()
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     n = len(rowptr) - 1
     pat = ic_csr_pattern(n, _p(rowptr), _p(colind))
     o = ic_opts(block_rows, dtype, warps_per_cta, rows_per_item, timeout_s, shift_alpha, exact, threads,
-                host_only)
+                host_only, solve_ctas_per_sm, solve_lanes)
     perm_a = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
     ranges_a = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
     nr = 0 if ranges_a is None else len(ranges_a) - 1
