@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--numeric-only", action="store_true",
                     help="time only the numeric factorization (for profiling runs)")
+    ap.add_argument("--no-f32", action="store_true", help="skip the mixed-precision arm")
     return ap.parse_args()
 
 
@@ -325,11 +326,62 @@ def main():
                        "d2h_bytes_per_step": int(xh.nbytes), "ms_per_step": t_e2e * 1e3,
                        "note": "factor flops / end-to-end step time (copies + factor + PCG)"}
 
+    # mixed precision arm: FP32 factor values and solves, FP64 pivots and PCG, same
+    # workload, timed the same way; the plain FP64 arm above is its comparison
+    h32 = None
+    if not a.numeric_only and not a.no_f32:
+        h32 = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
+                              warps_per_cta=a.warps, dtype=ick.IC_F32)
+        ick.ic_set_timing(h32, True)
+        x32 = torch.empty_like(x)
+
+        def step32():
+            ick.ic_numeric(h32, av, stream)
+            t = ick.ic_get_timing(h32)
+            it, rel = ick.pcg_solve(h32, av, b, x32, a.tol, 5000, stream)
+            return t["prepare_ms"] + t["numeric_ms"], it, rel
+
+        for _ in range(a.warmup):
+            step32()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f32_fact, f32_it, f32_rel = [], 0, 0.0
+        e0.record(stream)
+        for _ in range(a.steps):
+            f, f32_it, f32_rel = step32()
+            f32_fact.append(f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t32 = e0.elapsed_time(e1) / a.steps
+        f32_true = float(np.linalg.norm(prob.scipy() @ x32.cpu().numpy() - b_host) / np.linalg.norm(b_host))
+        mf32 = sum(f32_fact) / len(f32_fact)
+        line["mixed_f32"] = {"factor_ms": mf32, "factor_gflops": st["flops"] / (mf32 * 1e-3) / 1e9,
+                             "pcg_iters": f32_it, "relres": f32_rel, "true_relres": f32_true,
+                             "time_to_solution_ms": t32,
+                             "speedup_vs_f64_time_to_solution": ms_per_step / t32}
+
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        fl, t = run_oracle_sample(a.side, a.k)
+        import oracle
+        o = oracle.OracleIC.from_problem(prob, perm, a.k)
+        t0 = time.perf_counter()
+        assert o.numeric(prob.vals) == 0
+        t = time.perf_counter() - t0
+        fl = o.flops
         line["cpu_baseline"] = {"value": fl / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                                 "sample": f"one oracle numeric IC({a.k}) of the full {a.side}^3 "
                                           f"workload ({t:.1f} s)"}
+        # error of each GPU factor against the FP64 oracle on the full workload
+        ref = o.values()
+        amax = float(np.abs(prob.vals).max())
+        orp, oci, _ = o.pattern()
+        parity = {}
+        for name, hh in (("f64", h), ("f32", h32)):
+            if hh is None:
+                continue
+            rp, ci, lv, _ = ick.ic_get_factor(hh)
+            parity[name] = {"pattern_equal": bool(np.array_equal(rp, orp) and np.array_equal(ci, oci)),
+                            "max_abs_err_over_max_A": float(np.abs(lv - ref).max() / amax)}
+        line["parity_vs_oracle"] = parity
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:

@@ -162,10 +162,21 @@ int upload_plan(ic_handle* h) {
     if ((st = h->upload(&D.succ, P.succ))) return st;
     if ((st = h->upload(&D.indeg0, P.indeg0))) return st;
     if ((st = h->upload(&D.seeds, P.seeds))) return st;
+    // factor values (FP64, or FP32 plus FP64 pivots), padded by 16 bytes
+    const bool f32 = h->opts.dtype == IC_F32;
     double* uval = nullptr;
-    if ((st = h->alloc(&uval, size_t(P.nnz_u) + 2))) return st;
-    CK(cudaMemset(uval, 0, (size_t(P.nnz_u) + 2) * sizeof(double)));
-    D.uval = uval;
+    float* uval32 = nullptr;
+    if (f32) {
+        if ((st = h->alloc(&uval32, size_t(P.nnz_u) + 4))) return st;
+        CK(cudaMemset(uval32, 0, (size_t(P.nnz_u) + 4) * sizeof(float)));
+        D.uval = uval32;
+        if ((st = h->alloc(&D.udiag, size_t(P.n)))) return st;
+        if ((st = h->upload(&D.diag_src, P.udiag_src))) return st;
+    } else {
+        if ((st = h->alloc(&uval, size_t(P.nnz_u) + 2))) return st;
+        CK(cudaMemset(uval, 0, (size_t(P.nnz_u) + 2) * sizeof(double)));
+        D.uval = uval;
+    }
     if ((st = h->alloc(&D.indeg, P.task.size()))) return st;
     if ((st = h->alloc(&D.items_left, P.task.size()))) return st;
     if ((st = h->alloc(&D.queue, size_t(P.total_items)))) return st;
@@ -184,6 +195,10 @@ int upload_plan(ic_handle* h) {
     S.cptr = D.cptr;
     S.csc = D.csc;
     S.uval = uval;
+    S.uval32 = uval32;
+    S.udiag = D.udiag;
+    S.dtype = h->opts.dtype;
+    if (f32 && (st = h->alloc(&S.rdiag32, size_t(P.n)))) return st;
     S.lanes_per_row = h->opts.solve_lanes;
     if ((st = h->upload(&S.fwd_pad, P.fwd_pad))) return st;
     if ((st = h->upload(&S.bwd_pad, P.bwd_pad))) return st;
@@ -221,7 +236,7 @@ int upload_plan(ic_handle* h) {
     int dev = 0, sms = 0, bpsm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CK(numeric_blocks_per_sm(h->opts.warps_per_cta, h->opts.exact != 0, &bpsm));
+    CK(numeric_blocks_per_sm(h->opts.warps_per_cta, h->opts.exact != 0, h->opts.dtype, &bpsm));
     if (bpsm < 1) return fail(IC_ERR_CUDA, "numeric kernel cannot be resident");
     h->grid_numeric = sms * bpsm;
     CK(apply_blocks_per_sm(&bpsm));
@@ -285,9 +300,10 @@ int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64
             delete h;
             return fail(IC_ERR_ARG, "warps_per_cta must be 8 or 16");
         }
-        if (h->opts.dtype != IC_F64) {
+        if ((h->opts.dtype != IC_F64 && h->opts.dtype != IC_F32) ||
+            (h->opts.dtype == IC_F32 && h->opts.exact)) {
             delete h;
-            return fail(IC_ERR_ARG, "dtype: only IC_F64 is available");
+            return fail(IC_ERR_ARG, "dtype must be IC_F64 or IC_F32 (exact=1 needs IC_F64)");
         }
         if (h->opts.rows_per_item < 1 || h->opts.timeout_s < 0 ||
             (h->opts.solve_lanes != 4 && h->opts.solve_lanes != 8 && h->opts.solve_lanes != 16 &&
@@ -337,11 +353,13 @@ int ic_numeric(ic_handle* h, const void* values, void* stream, int64_t* breakdow
     const int epoch = ++h->epoch;
     const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
     if (h->timing) CK(cudaEventRecord(h->ev[0], s));
-    CK(launch_numeric_prepare(h->dp, static_cast<const double*>(values), h->opts.shift_alpha, epoch, s));
+    CK(launch_numeric_prepare(h->dp, static_cast<const double*>(values), h->opts.shift_alpha, epoch,
+                              h->opts.dtype, s));
     ++h->tm.launches;
     if (h->timing) CK(cudaEventRecord(h->ev[1], s));
     if (h->dp.total_items > 0) {
-        CK(launch_numeric(h->dp, epoch, h->opts.warps_per_cta, h->opts.exact != 0, h->grid_numeric,
+        CK(launch_numeric(h->dp, epoch, h->opts.warps_per_cta, h->opts.exact != 0, h->opts.dtype,
+                          h->grid_numeric,
                           tmo, s));
         ++h->tm.launches;
     }
@@ -402,6 +420,7 @@ int ic_apply_static(ic_handle* h, const void* r, void* z, void* stream) {
     if (!h || ((!r || !z) && h->hp.n > 0)) return fail(IC_ERR_ARG, "NULL argument");
     if (r == z && h->hp.n > 0) return fail(IC_ERR_ARG, "r and z may not alias");
     if (!h->factored) return fail(IC_ERR_STATE, "ic_apply_static before a successful ic_numeric");
+    if (h->opts.dtype != IC_F64) return fail(IC_ERR_ARG, "ic_apply_static: IC_F64 factors only");
     if (h->hp.n > static_apply_max_rows())
         return fail(IC_ERR_ARG, "ic_apply_static: n = " + std::to_string(h->hp.n) +
                                     " exceeds the static scratch limit of " +
@@ -507,7 +526,18 @@ int ic_get_factor(ic_handle* h, int64_t* rowptr, int32_t* colind, double* vals, 
         if (!h->factored) return fail(IC_ERR_STATE, "no successful ic_numeric");
         DeviceGuard g(h->device);
         u.resize(P.nnz_u);
-        CK(cudaMemcpy(u.data(), h->dp.uval, u.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        if (h->opts.dtype == IC_F32) {
+            // FP32 off-diagonal values, FP64 pivots
+            std::vector<float> u32(P.nnz_u);
+            std::vector<double> d(n);
+            if (P.nnz_u)
+                CK(cudaMemcpy(u32.data(), h->dp.uval, u32.size() * sizeof(float), cudaMemcpyDeviceToHost));
+            if (n) CK(cudaMemcpy(d.data(), h->dp.udiag, d.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int64_t e = 0; e < P.nnz_u; ++e) u[e] = double(u32[e]);
+            for (int64_t i = 0; i < n; ++i) u[P.urp[i]] = d[i];
+        } else if (P.nnz_u) {
+            CK(cudaMemcpy(u.data(), h->dp.uval, u.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        }
     }
     // L row i = U column i: pivots p < i in ascending order, then the diagonal
     int64_t pos = 0;

@@ -99,6 +99,8 @@ struct DevPlan {
     int* diag;             // [0] items completed, [1] timeout site
     unsigned long long* trace;  // NULL, or 4 words per queue slot: start ns, end ns,
                                 // task | chunk << 32, SM id
+    double* udiag;         // IC_F32: FP64 diagonal pivots (U_ii) of the factor
+    const int* diag_src;   // IC_F32: index of A's diagonal value of each row
 };
 
 // Status bits written by the kernels into counters[2].
@@ -127,14 +129,18 @@ struct SolvePlan {
     int nfwd_pad, nbwd_pad;
     double* rdiag;         // 1 / U_ii, computed after each numeric factorization
     int lanes_per_row;     // 4, 8, 16 or 32 lanes per row in the ic_apply solves
+    int dtype;             // IC_F64 or IC_F32 (factor values and solves in FP32)
+    const float* uval32;   // IC_F32 factor values
+    const double* udiag;   // IC_F32 FP64 pivots
+    float* rdiag32;        // IC_F32 reciprocal pivots
 };
 
 // Kernel entry points (numeric.cu, solve.cu).
 cudaError_t launch_numeric_prepare(const DevPlan& P, const double* avals, double shift_alpha,
-                                   int epoch, cudaStream_t s);
-cudaError_t launch_numeric(const DevPlan& P, int epoch, int warps, bool exact, int grid,
+                                   int epoch, int dtype, cudaStream_t s);
+cudaError_t launch_numeric(const DevPlan& P, int epoch, int warps, bool exact, int dtype, int grid,
                            unsigned long long timeout_ns, cudaStream_t s);
-cudaError_t numeric_blocks_per_sm(int warps, bool exact, int* blocks);
+cudaError_t numeric_blocks_per_sm(int warps, bool exact, int dtype, int* blocks);
 
 cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epoch,
                          unsigned long long timeout_ns, int grid, cudaStream_t s);

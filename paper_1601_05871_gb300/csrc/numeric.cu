@@ -15,7 +15,14 @@
 // pattern S and are discarded.  Chol and Trsm rows depend on earlier rows of the
 // same diagonal block; those waits use per-row completion flags in shared memory.
 // Every wait is bounded by a %globaltimer deadline and ends in a status bit.
+//
+// Precision: T = double is the FP64 factorization.  T = float keeps the off-diagonal
+// factor values in FP32 while every diagonal pivot is accumulated, square-rooted and
+// tested for breakdown in FP64 (array udiag): in Chol and Herk each pivot row's source
+// segment starts at column r, so its contribution to U_rr is exactly U_pr^2, which the
+// owning warp subtracts in FP64.
 #include <cstdint>
+#include <type_traits>
 
 #include "ick_internal.h"
 
@@ -48,10 +55,17 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+
 template <bool EXACT>
 __device__ __forceinline__ double sub_product(double acc, double a, double b) {
     if (EXACT) return __dsub_rn(acc, __dmul_rn(a, b));
     return fma(-a, b, acc);
+}
+template <bool EXACT>
+__device__ __forceinline__ float sub_product(float acc, float a, float b) {
+    return fmaf(-a, b, acc);
 }
 
 enum Mode { M_CHOL = 0, M_TRSM = 1, M_UPDATE = 2 };
@@ -75,6 +89,11 @@ __device__ __forceinline__ void set_timeout(const DevPlan& P, int site) {
     atomicExch(P.diag + 1, site);
 }
 
+__device__ __forceinline__ void note_breakdown(const DevPlan& P, int r) {
+    atomicOr(P.counters + 2, kStBreakdown);
+    atomicMin(P.brk_row, (long long)r);
+}
+
 // Wait until done[local] is set by another warp of this CTA; false on timeout/abort.
 __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int local,
                          unsigned long long deadline) {
@@ -96,16 +115,20 @@ constexpr int kSegStage = 64;  // source elements of one pivot staged by copies
 
 // One staged pivot segment: values and columns copied as the enclosing 16-byte
 // aligned spans, plus the 16 bytes holding U_pr when it lies outside the segment.
+template <typename T>
 struct Slot {
-    double vals[kSegStage + 2];
-    double aval[2];
+    T vals[kSegStage + 16 / sizeof(T)];
+    T aval[16 / sizeof(T)];
     int cols[kSegStage + 4];
 };
 
 // Per-warp shared-memory work area (16-byte multiples first for the async copies).
+template <typename T>
 struct WarpBuf {
-    Slot ring[kRing];
-    double tval[kSegCap];  // target segment values (one chunk)
+    Slot<T> ring[kRing];
+    double dacc;           // FP64 diagonal accumulator (T = float)
+    double pad;
+    T tval[kSegCap];       // target segment values (one chunk)
     int tcol[kSegCap];     // target segment columns
     int hkey[kHash];       // hash keys (column, or -1)
     short hslot[kHash];    // slot in the target chunk of each key
@@ -113,7 +136,8 @@ struct WarpBuf {
 
 __device__ __forceinline__ int hash_of(int c) { return int((unsigned(c) * 2654435761u) >> 24); }
 
-__device__ __forceinline__ int hash_find(const WarpBuf& W, int c) {
+template <typename T>
+__device__ __forceinline__ int hash_find(const WarpBuf<T>& W, int c) {
     int h = hash_of(c);
     for (;;) {
         const int k = W.hkey[h];
@@ -123,8 +147,8 @@ __device__ __forceinline__ int hash_find(const WarpBuf& W, int c) {
     }
 }
 
-template <bool EXACT>
-__device__ __forceinline__ void apply_one(WarpBuf& W, int c, int cmin, int cmax, double a, double v) {
+template <bool EXACT, typename T>
+__device__ __forceinline__ void apply_one(WarpBuf<T>& W, int c, int cmin, int cmax, T a, T v) {
     if (c >= cmin && c <= cmax) {
         const int idx = hash_find(W, c);
         if (idx >= 0) W.tval[idx] = sub_product<EXACT>(W.tval[idx], a, v);
@@ -134,10 +158,11 @@ __device__ __forceinline__ void apply_one(WarpBuf& W, int c, int cmin, int cmax,
 // Issue the copies of pivot q's source segment into ring slot q % kRing.  Returns 1
 // when the slot will hold the data (or the segment is empty), 0 when the pivot row is
 // not complete yet (Chol/Trsm): then the consumer waits and loads it directly.
-template <int MODE>
-__device__ __forceinline__ int issue_pivot(const DevPlan& P, const double* U, WarpBuf& W, int q,
+template <int MODE, typename T>
+__device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf<T>& W, int q,
                                            int p, int pos, int sb, int len, bool start_at_r,
                                            int rbase, volatile unsigned char* done) {
+    constexpr int EPC = 16 / sizeof(T);  // elements per 16-byte chunk
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const int pq = __shfl_sync(full, p, q), posq = __shfl_sync(full, pos, q);
@@ -149,15 +174,15 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const double* U, Wa
         if (!__shfl_sync(full, f, 0)) return 0;
         __threadfence_block();
     }
-    Slot& S = W.ring[q % kRing];
+    Slot<T>& S = W.ring[q % kRing];
     const int n = min(lq, kSegStage);
-    const int vb = sbq & ~1, nv = (((sbq + n + 1) & ~1) - vb) >> 1;
+    const int vb = sbq & ~(EPC - 1), nv = (((sbq + n + EPC - 1) & ~(EPC - 1)) - vb) / EPC;
     const int cb = sbq & ~3, nc = (((sbq + n + 3) & ~3) - cb) >> 2;
     const int total = nv + nc + (start_at_r ? 0 : 1);
     for (int t = lane; t < total; t += 32) {
-        if (t < nv) cp_async16(&S.vals[2 * t], U + vb + 2 * t);
+        if (t < nv) cp_async16(&S.vals[EPC * t], U + vb + EPC * t);
         else if (t < nv + nc) cp_async16(&S.cols[4 * (t - nv)], P.ucol + cb + 4 * (t - nv));
-        else cp_async16(&S.aval[0], U + (posq & ~1));
+        else cp_async16(&S.aval[0], U + (posq & ~(EPC - 1)));
     }
     return 1;
 }
@@ -175,22 +200,32 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const double* U, Wa
 // shared-memory slots while the current one is applied.  For Chol and Trsm a copy is
 // issued only once the pivot row's completion flag is seen; a pivot that was not
 // complete at issue time is waited for and loaded directly when its turn comes.
-template <int MODE, bool EXACT>
-__device__ void process_target(const DevPlan& P, double* U, int r, int ca, int cb, int tb, int te,
+template <int MODE, bool EXACT, typename T>
+__device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, int tb, int te,
                                int srcblk, bool start_at_r, int rbase,
-                               volatile unsigned char* done, WarpBuf& W,
+                               volatile unsigned char* done, WarpBuf<T>& W,
                                unsigned long long deadline) {
+    constexpr bool MIXED = std::is_same<T, float>::value;
+    constexpr int EPC = 16 / sizeof(T);
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    double piv = 1.0;
-    if (MODE == M_TRSM) piv = __ldcg(U + __ldg(P.urp + r));
+    // Trsm: FP32 multiplies by the rounded reciprocal of the FP64 pivot; FP64 divides
+    // by the pivot itself (the operation of the definition)
+    T scale = T(1);
+    if (MODE == M_TRSM) {
+        if (MIXED) scale = T(1.0 / __ldcg(P.udiag + r));
+        else scale = ld_cg(U + __ldg(P.urp + r));
+    }
     for (int c0 = tb; c0 < te; c0 += kSegCap) {
         const int m = min(kSegCap, te - c0);
+        // the FP64 diagonal of a Chol/Herk target row (T = float): first chunk only
+        const bool dchunk = MIXED && start_at_r && c0 == tb;
         for (int x = lane; x < kHash; x += 32) W.hkey[x] = -1;
         for (int x = lane; x < m; x += 32) {
             W.tcol[x] = __ldg(P.ucol + c0 + x);
-            W.tval[x] = __ldcg(U + c0 + x);
+            W.tval[x] = ld_cg(U + c0 + x);
         }
+        if (dchunk && lane == 0) W.dacc = __ldcg(P.udiag + r);
         __syncwarp();
         for (int x = lane; x < m; x += 32) {
             const int c = W.tcol[x];
@@ -236,12 +271,12 @@ __device__ void process_target(const DevPlan& P, double* U, int r, int ca, int c
                 const int sbq = __shfl_sync(full, sb, q), lq = __shfl_sync(full, len, q);
                 if (lq > 0) {
                     int first_direct = 0;
-                    double a;
+                    T a;
                     if ((issued >> q) & 1u) {
-                        const Slot& S = W.ring[q % kRing];
+                        const Slot<T>& S = W.ring[q % kRing];
                         const int n = min(lq, kSegStage);
-                        const int vo = sbq - (sbq & ~1), co = sbq - (sbq & ~3);
-                        a = start_at_r ? S.vals[vo] : S.aval[posq & 1];
+                        const int vo = sbq - (sbq & ~(EPC - 1)), co = sbq - (sbq & ~3);
+                        a = start_at_r ? S.vals[vo] : S.aval[posq & (EPC - 1)];
                         for (int x = lane; x < n; x += 32)
                             apply_one<EXACT>(W, S.cols[co + x], cmin, cmax, a, S.vals[vo + x]);
                         first_direct = n;
@@ -252,10 +287,11 @@ __device__ void process_target(const DevPlan& P, double* U, int r, int ca, int c
                             cp_async_wait<0>();
                             return;
                         }
-                        a = __ldcg(U + posq);
+                        a = ld_cg(U + posq);
                     }
                     for (int o = first_direct + lane; o < lq; o += 32)
-                        apply_one<EXACT>(W, __ldg(P.ucol + sbq + o), cmin, cmax, a, __ldcg(U + sbq + o));
+                        apply_one<EXACT>(W, __ldg(P.ucol + sbq + o), cmin, cmax, a, ld_cg(U + sbq + o));
+                    if (dchunk && lane == 0) W.dacc = fma(-double(a), double(a), W.dacc);
                 }
                 __syncwarp();
             }
@@ -265,22 +301,30 @@ __device__ void process_target(const DevPlan& P, double* U, int r, int ca, int c
         if (MODE == M_CHOL) {
             if (c0 == tb) {
                 if (lane == 0) {
-                    const double d = W.tval[0];
-                    if (!(d > 0.0) || !isfinite(d)) {
-                        atomicOr(P.counters + 2, kStBreakdown);
-                        atomicMin(P.brk_row, (long long)r);
-                    }
-                    piv = sqrt(d);
-                    W.tval[0] = piv;
+                    const double d = MIXED ? W.dacc : double(W.tval[0]);
+                    if (!(d > 0.0) || !isfinite(d)) note_breakdown(P, r);
+                    const double piv = sqrt(d);
+                    if (MIXED) __stcg(P.udiag + r, piv);
+                    W.tval[0] = T(piv);
+                    W.dacc = MIXED ? 1.0 / piv : piv;
                 }
-                piv = __shfl_sync(full, piv, 0);
                 __syncwarp();
-                for (int x = 1 + lane; x < m; x += 32) W.tval[x] = W.tval[x] / piv;
+                if (MIXED) {
+                    scale = T(W.dacc);
+                    for (int x = 1 + lane; x < m; x += 32) W.tval[x] = W.tval[x] * scale;
+                } else {
+                    scale = T(W.dacc);  // the pivot itself: FP64 divides as in the definition
+                    for (int x = 1 + lane; x < m; x += 32) W.tval[x] = W.tval[x] / scale;
+                }
             } else {
-                for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / piv;
+                if (MIXED) for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] * scale;
+                else for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / scale;
             }
         } else if (MODE == M_TRSM) {
-            for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / piv;
+            if (MIXED) for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] * scale;
+            else for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / scale;
+        } else if (dchunk && lane == 0) {
+            __stcg(P.udiag + r, W.dacc);  // Herk: the updated FP64 diagonal
         }
         __syncwarp();
         for (int x = lane; x < m; x += 32) __stcg(U + c0 + x, W.tval[x]);
@@ -290,20 +334,26 @@ __device__ void process_target(const DevPlan& P, double* U, int r, int ca, int c
 
 // Dynamic shared memory of one CTA: scheduler words, per-row flags, per-warp buffers.
 constexpr size_t kSmemHead = 32;
-constexpr size_t kWarpBytes = (sizeof(WarpBuf) + 15) / 16 * 16;
-constexpr size_t smem_bytes(int warps) { return kSmemHead + kMaxBlockRows + size_t(warps) * kWarpBytes; }
+template <typename T>
+__host__ __device__ constexpr size_t warp_bytes() { return (sizeof(WarpBuf<T>) + 15) / 16 * 16; }
+template <typename T>
+__host__ __device__ constexpr size_t smem_bytes(int warps) {
+    return kSmemHead + kMaxBlockRows + size_t(warps) * warp_bytes<T>();
+}
 static_assert((kSmemHead + kMaxBlockRows) % 16 == 0, "warp buffers must start 16-byte aligned");
-static_assert(sizeof(Slot) % 16 == 0, "staging slots must be 16-byte multiples");
+static_assert(sizeof(Slot<double>) % 16 == 0 && sizeof(Slot<float>) % 16 == 0,
+              "staging slots must be 16-byte multiples");
 
-template <int WARPS, bool EXACT>
+template <int WARPS, bool EXACT, typename T>
 __global__ void __launch_bounds__(WARPS * 32)
 numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     unsigned char* s_done = smem_raw + kSmemHead;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpBuf& W = *reinterpret_cast<WarpBuf*>(smem_raw + kSmemHead + kMaxBlockRows + size_t(warp) * kWarpBytes);
-    double* U = static_cast<double*>(P.uval);
+    WarpBuf<T>& W = *reinterpret_cast<WarpBuf<T>*>(smem_raw + kSmemHead + kMaxBlockRows +
+                                                   size_t(warp) * warp_bytes<T>());
+    T* U = static_cast<T*>(P.uval);
     const unsigned long long deadline = gtimer() + timeout_ns;
     volatile unsigned char* done = s_done;
 
@@ -336,11 +386,11 @@ numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
         __syncthreads();
         const int task = sm.task, chunk = sm.chunk;
         if (task < 0) break;
-        const int4 T = __ldg(P.task + task);
+        const int4 Tk = __ldg(P.task + task);
         const int t0 = __ldg(P.tgt_ptr + task), nt = __ldg(P.tgt_ptr + task + 1) - t0;
 
-        if (T.x == T_CHOL || T.x == T_TRSM) {
-            const int blk = T.y;
+        if (Tk.x == T_CHOL || Tk.x == T_TRSM) {
+            const int blk = Tk.y;
             const int rbase = __ldg(P.ranges + blk), nrows = __ldg(P.ranges + blk + 1) - rbase;
             for (int i = threadIdx.x; i < nrows; i += WARPS * 32) s_done[i] = 0;
             if (threadIdx.x == 0) sm.next = 0;
@@ -352,12 +402,12 @@ numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
                 if (idx >= nt) break;
                 const int4 g = __ldg(P.tgt + t0 + idx);
                 const int gend = __ldg(P.tgt_end + t0 + idx);
-                if (T.x == T_CHOL)
-                    process_target<M_CHOL, EXACT>(P, U, g.x, g.y, g.z, g.w, gend, blk, true, rbase,
-                                                  done, W, deadline);
+                if (Tk.x == T_CHOL)
+                    process_target<M_CHOL, EXACT, T>(P, U, g.x, g.y, g.z, g.w, gend, blk, true, rbase,
+                                                     done, W, deadline);
                 else
-                    process_target<M_TRSM, EXACT>(P, U, g.x, g.y, g.z, g.w, gend, T.w, false, rbase,
-                                                  done, W, deadline);
+                    process_target<M_TRSM, EXACT, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, false, rbase,
+                                                     done, W, deadline);
                 __threadfence_block();
                 __syncwarp();
                 if (lane == 0) done[g.x - rbase] = 1;
@@ -365,16 +415,16 @@ numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
         } else {
             const int first = chunk * P.rows_per_item;
             const int last = min(nt, first + P.rows_per_item);
-            const bool herk = (T.x == T_HERK);
+            const bool herk = (Tk.x == T_HERK);
             for (int idx = first + warp; idx < last; idx += WARPS) {
                 const int4 g = __ldg(P.tgt + t0 + idx);
                 const int gend = __ldg(P.tgt_end + t0 + idx);
                 if (herk)
-                    process_target<M_UPDATE, EXACT>(P, U, g.x, g.y, g.z, g.w, gend, T.w, true, 0, done,
-                                                    W, deadline);
+                    process_target<M_UPDATE, EXACT, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, true, 0, done,
+                                                       W, deadline);
                 else
-                    process_target<M_UPDATE, EXACT>(P, U, g.x, g.y, g.z, g.w, gend, T.w, false, 0, done,
-                                                    W, deadline);
+                    process_target<M_UPDATE, EXACT, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, false, 0, done,
+                                                       W, deadline);
             }
         }
         __threadfence();
@@ -415,12 +465,15 @@ numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
 
 // Scatter of B's values onto the pattern S (zero on fill, optional diagonal shift)
 // and reset of the scheduler state.  gsrc >= 0: index into A's values; -1: fill;
-// <= -2: the diagonal, whose index is -2 - gsrc.
+// <= -2: the diagonal, whose index is -2 - gsrc.  With T = float the off-diagonal
+// values are rounded to FP32 and the diagonals go to the FP64 array udiag.
+template <typename T>
 __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double alpha, int nnz_u,
                                 int epoch) {
+    constexpr bool MIXED = std::is_same<T, float>::value;
     const int stride = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    double* U = static_cast<double*>(P.uval);
+    T* U = static_cast<T*>(P.uval);
     for (int pos = tid; pos < nnz_u; pos += stride) {
         const int s = __ldg(P.gsrc + pos);
         double v = 0.0;
@@ -430,8 +483,14 @@ __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double
             v = __ldg(av + (-2 - s));
             if (alpha != 0.0) v = __dadd_rn(v, __dmul_rn(alpha, v));
         }
-        U[pos] = v;
+        U[pos] = T(v);
     }
+    if (MIXED)
+        for (int i = tid; i < P.n; i += stride) {
+            double v = __ldg(av + __ldg(P.diag_src + i));
+            if (alpha != 0.0) v = __dadd_rn(v, __dmul_rn(alpha, v));
+            P.udiag[i] = v;
+        }
     for (int t = tid; t < P.ntasks; t += stride) {
         P.indeg[t] = __ldg(P.indeg0 + t);
         P.items_left[t] = __ldg(P.nitems + t);
@@ -451,46 +510,54 @@ __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double
     }
 }
 
-template <int WARPS, bool EXACT>
+template <int WARPS, bool EXACT, typename T>
 cudaError_t launch_t(const DevPlan& P, int grid, int epoch, unsigned long long timeout_ns,
                      cudaStream_t s) {
-    numeric_persistent<WARPS, EXACT><<<grid, WARPS * 32, smem_bytes(WARPS), s>>>(P, epoch, timeout_ns);
+    numeric_persistent<WARPS, EXACT, T><<<grid, WARPS * 32, smem_bytes<T>(WARPS), s>>>(P, epoch, timeout_ns);
     return cudaGetLastError();
 }
 
-template <int WARPS, bool EXACT>
+template <int WARPS, bool EXACT, typename T>
 cudaError_t occupancy_t(int* blocks) {
-    cudaError_t e = cudaFuncSetAttribute(numeric_persistent<WARPS, EXACT>,
+    cudaError_t e = cudaFuncSetAttribute(numeric_persistent<WARPS, EXACT, T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem_bytes(WARPS)));
+                                         int(smem_bytes<T>(WARPS)));
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, numeric_persistent<WARPS, EXACT>,
-                                                         WARPS * 32, smem_bytes(WARPS));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, numeric_persistent<WARPS, EXACT, T>,
+                                                         WARPS * 32, smem_bytes<T>(WARPS));
 }
 
 }  // namespace
 
-cudaError_t numeric_blocks_per_sm(int warps, bool exact, int* blocks) {
-    if (warps == 8) return exact ? occupancy_t<8, true>(blocks) : occupancy_t<8, false>(blocks);
-    return exact ? occupancy_t<16, true>(blocks) : occupancy_t<16, false>(blocks);
+cudaError_t numeric_blocks_per_sm(int warps, bool exact, int dtype, int* blocks) {
+    if (dtype == IC_F32)
+        return warps == 8 ? occupancy_t<8, false, float>(blocks) : occupancy_t<16, false, float>(blocks);
+    if (warps == 8) return exact ? occupancy_t<8, true, double>(blocks) : occupancy_t<8, false, double>(blocks);
+    return exact ? occupancy_t<16, true, double>(blocks) : occupancy_t<16, false, double>(blocks);
 }
 
 cudaError_t launch_numeric_prepare(const DevPlan& P, const double* avals, double shift_alpha,
-                                   int epoch, cudaStream_t s) {
+                                   int epoch, int dtype, cudaStream_t s) {
     const int work = P.nnz_u > P.ntasks ? P.nnz_u : P.ntasks;
     int pgrid = (work + 255) / 256;
     pgrid = pgrid < 1 ? 1 : (pgrid > 8192 ? 8192 : pgrid);
-    numeric_prepare<<<pgrid, 256, 0, s>>>(P, avals, shift_alpha, P.nnz_u, epoch);
+    if (dtype == IC_F32)
+        numeric_prepare<float><<<pgrid, 256, 0, s>>>(P, avals, shift_alpha, P.nnz_u, epoch);
+    else
+        numeric_prepare<double><<<pgrid, 256, 0, s>>>(P, avals, shift_alpha, P.nnz_u, epoch);
     return cudaGetLastError();
 }
 
-cudaError_t launch_numeric(const DevPlan& P, int epoch, int warps, bool exact, int grid,
+cudaError_t launch_numeric(const DevPlan& P, int epoch, int warps, bool exact, int dtype, int grid,
                            unsigned long long timeout_ns, cudaStream_t s) {
+    if (dtype == IC_F32)
+        return warps == 8 ? launch_t<8, false, float>(P, grid, epoch, timeout_ns, s)
+                          : launch_t<16, false, float>(P, grid, epoch, timeout_ns, s);
     if (warps == 8)
-        return exact ? launch_t<8, true>(P, grid, epoch, timeout_ns, s)
-                     : launch_t<8, false>(P, grid, epoch, timeout_ns, s);
-    return exact ? launch_t<16, true>(P, grid, epoch, timeout_ns, s)
-                 : launch_t<16, false>(P, grid, epoch, timeout_ns, s);
+        return exact ? launch_t<8, true, double>(P, grid, epoch, timeout_ns, s)
+                     : launch_t<8, false, double>(P, grid, epoch, timeout_ns, s);
+    return exact ? launch_t<16, true, double>(P, grid, epoch, timeout_ns, s)
+                 : launch_t<16, false, double>(P, grid, epoch, timeout_ns, s);
 }
 
 }  // namespace ick

@@ -144,17 +144,46 @@ __device__ __forceinline__ double await_value(const double* x, int i, int* abort
 // dependence level and never wait on each other: a warp-wide reconvergence before a
 // row is published can then never block the row's own consumer.  The diagonal is
 // applied as a precomputed reciprocal.
-template <int G>
-__device__ __forceinline__ double group_sum(double v) {
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
     const int lane = threadIdx.x & 31;
     const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
     return v;
 }
 
-template <int G>
+// FP32 counterparts of the value-as-flag helpers (all-ones is a NaN pattern for both).
+__device__ __forceinline__ float publishable(float v) {
+    return __float_as_int(v) == -1 ? __int_as_float(0x7fffffff) : v;
+}
+__device__ __forceinline__ float await_value(const float* x, int i, int* abort_word,
+                                             unsigned long long deadline, bool& ok) {
+    const volatile int* p = reinterpret_cast<const volatile int*>(x + i);
+    int b = *p;
+    unsigned spins = 0;
+    while (b == -1) {
+        if ((++spins & 255) == 0) {
+            if (*(volatile int*)abort_word || gtimer() > deadline) {
+                atomicExch(abort_word, 1);
+                ok = false;
+                return 0.f;
+            }
+        }
+        __nanosleep(16);
+        b = *p;
+    }
+    return __int_as_float(b);
+}
+
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+
+// T = double: FP64 factor and solves.  T = float: FP32 factor values, work vectors and
+// sums; the right-hand side arrives in FP64 and the result leaves in FP64.
+template <int G, typename T>
 __global__ void __launch_bounds__(kApplyThreads)
-forward_solve_v(SolvePlan S, const double* __restrict__ r, double* yv, unsigned long long timeout_ns) {
+forward_solve_v(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all,
+                const double* __restrict__ r, T* yv, unsigned long long timeout_ns) {
     constexpr int R = 32 / G;
     const int lane = threadIdx.x & 31, sub = lane / G, sl = lane % G;
     const unsigned long long deadline = gtimer() + timeout_ns;
@@ -165,34 +194,34 @@ forward_solve_v(SolvePlan S, const double* __restrict__ r, double* yv, unsigned 
         t0 = __shfl_sync(0xffffffffu, t0, 0);
         if (t0 >= S.nfwd_pad) break;
         const int t = t0 + sub;
-        double acc = 0.0;
+        T acc = T(0);
         int i = -1;
-        double rhs = 0.0, rd = 0.0;  // loaded before the waits: off the dependence chain
+        T rhs = T(0), rd = T(0);  // loaded before the waits: off the dependence chain
         if ((i = __ldg(S.fwd_pad + t)) >= 0) {
             if (sl == 0) {
-                rhs = __ldg(r + __ldg(S.perm + i));
-                rd = __ldg(S.rdiag + i);
+                rhs = T(__ldg(r + __ldg(S.perm + i)));
+                rd = __ldg(rd_all + i);
             }
             const int a = __ldg(S.cptr + i), b = __ldg(S.cptr + i + 1);
             for (int e = a + sl; e < b; e += G) {
                 const int2 pe = __ldg(S.csc + e);
-                const double u = __ldg(S.uval + pe.y);
-                acc = fma(u, ok ? await_value(yv, pe.x, S.counter + 2, deadline, ok) : 0.0, acc);
+                const T u = __ldg(uv + pe.y);
+                acc = fma(u, ok ? await_value(yv, pe.x, S.counter + 2, deadline, ok) : T(0), acc);
             }
         }
         acc = group_sum<G>(acc);
         if (sl == 0 && i >= 0) {
-            const double v = (rhs - acc) * rd;
-            *reinterpret_cast<volatile double*>(yv + i) = publishable(v);
+            const T v = (rhs - acc) * rd;
+            *reinterpret_cast<volatile T*>(yv + i) = publishable(v);
         }
         if (__any_sync(0xffffffffu, !ok)) break;
     }
 }
 
-template <int G>
+template <int G, typename T>
 __global__ void __launch_bounds__(kApplyThreads)
-backward_solve_v(SolvePlan S, const double* yv, double* zv, double* __restrict__ z,
-                 unsigned long long timeout_ns) {
+backward_solve_v(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all, const T* yv,
+                 T* zv, double* __restrict__ z, unsigned long long timeout_ns) {
     constexpr int R = 32 / G;
     const int lane = threadIdx.x & 31, sub = lane / G, sl = lane % G;
     const unsigned long long deadline = gtimer() + timeout_ns;
@@ -203,36 +232,62 @@ backward_solve_v(SolvePlan S, const double* yv, double* zv, double* __restrict__
         t0 = __shfl_sync(0xffffffffu, t0, 0);
         if (t0 >= S.nbwd_pad) break;
         const int t = t0 + sub;
-        double acc = 0.0;
+        T acc = T(0);
         int i = -1;
-        double rhs = 0.0, rd = 0.0;
+        T rhs = T(0), rd = T(0);
         int dst = 0;
         if ((i = __ldg(S.bwd_pad + t)) >= 0) {
             if (sl == 0) {
-                rhs = __ldcg(yv + i);
-                rd = __ldg(S.rdiag + i);
+                rhs = ld_cg(yv + i);
+                rd = __ldg(rd_all + i);
                 dst = __ldg(S.perm + i);
             }
             const long long a = __ldg(S.urp + i), b = __ldg(S.urp + i + 1);
             for (long long e = a + 1 + sl; e < b; e += G) {
                 const int c = __ldg(S.ucol + e);
-                const double u = __ldg(S.uval + e);
-                acc = fma(u, ok ? await_value(zv, c, S.counter + 2, deadline, ok) : 0.0, acc);
+                const T u = __ldg(uv + e);
+                acc = fma(u, ok ? await_value(zv, c, S.counter + 2, deadline, ok) : T(0), acc);
             }
         }
         acc = group_sum<G>(acc);
         if (sl == 0 && i >= 0) {
-            const double v = (rhs - acc) * rd;
-            z[dst] = v;
-            *reinterpret_cast<volatile double*>(zv + i) = publishable(v);
+            const T v = (rhs - acc) * rd;
+            z[dst] = double(v);
+            *reinterpret_cast<volatile T*>(zv + i) = publishable(v);
         }
         if (__any_sync(0xffffffffu, !ok)) break;
     }
 }
 
 __global__ void rdiag_kernel(SolvePlan S) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x)
-        S.rdiag[i] = 1.0 / S.uval[S.urp[i]];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
+        if (S.dtype == IC_F32) S.rdiag32[i] = float(1.0 / S.udiag[i]);
+        else S.rdiag[i] = 1.0 / S.uval[S.urp[i]];
+    }
+}
+
+template <typename T>
+cudaError_t launch_solves(const SolvePlan& S, const T* uv, const T* rd, const double* r, double* z,
+                          T* y, int grid, unsigned long long timeout_ns, cudaStream_t s) {
+    switch (S.lanes_per_row) {
+        case 4:
+            forward_solve_v<4, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, r, y, timeout_ns);
+            backward_solve_v<4, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, y, y + S.n, z, timeout_ns);
+            break;
+        case 8:
+            forward_solve_v<8, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, r, y, timeout_ns);
+            backward_solve_v<8, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, y, y + S.n, z, timeout_ns);
+            break;
+        case 16:
+            forward_solve_v<16, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, r, y, timeout_ns);
+            backward_solve_v<16, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, y, y + S.n, z, timeout_ns);
+            break;
+        default:
+            forward_solve_v<32, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, r, y, timeout_ns);
+            backward_solve_v<32, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, y, y + S.n, z, timeout_ns);
+            break;
+    }
+    return cudaGetLastError();
 }
 
 // y = A x with G threads per row (G in {4, 8, 16, 32}).
@@ -352,34 +407,16 @@ cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epo
                          unsigned long long timeout_ns, int grid, cudaStream_t s) {
     if (S.n == 0) return cudaSuccess;
     (void)epoch;
-    // S.y holds 2n doubles: the forward result, then the backward result
-    cudaError_t e = cudaMemsetAsync(S.y, 0xff, 2 * size_t(S.n) * sizeof(double), s);
+    // S.y holds 2n doubles: the forward then the backward result (2n floats for IC_F32)
+    const size_t bytes = 2 * size_t(S.n) * (S.dtype == IC_F32 ? sizeof(float) : sizeof(double));
+    cudaError_t e = cudaMemsetAsync(S.y, 0xff, bytes, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(S.counter, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    switch (S.lanes_per_row) {
-        case 4:
-            forward_solve_v<4><<<grid, kApplyThreads, 0, s>>>(S, r, S.y, timeout_ns);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            backward_solve_v<4><<<grid, kApplyThreads, 0, s>>>(S, S.y, S.y + S.n, z, timeout_ns);
-            break;
-        case 16:
-            forward_solve_v<16><<<grid, kApplyThreads, 0, s>>>(S, r, S.y, timeout_ns);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            backward_solve_v<16><<<grid, kApplyThreads, 0, s>>>(S, S.y, S.y + S.n, z, timeout_ns);
-            break;
-        case 32:
-            forward_solve_v<32><<<grid, kApplyThreads, 0, s>>>(S, r, S.y, timeout_ns);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            backward_solve_v<32><<<grid, kApplyThreads, 0, s>>>(S, S.y, S.y + S.n, z, timeout_ns);
-            break;
-        default:
-            forward_solve_v<8><<<grid, kApplyThreads, 0, s>>>(S, r, S.y, timeout_ns);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            backward_solve_v<8><<<grid, kApplyThreads, 0, s>>>(S, S.y, S.y + S.n, z, timeout_ns);
-            break;
-    }
-    return cudaGetLastError();
+    if (S.dtype == IC_F32)
+        return launch_solves<float>(S, S.uval32, S.rdiag32, r, z, reinterpret_cast<float*>(S.y), grid,
+                                    timeout_ns, s);
+    return launch_solves<double>(S, S.uval, S.rdiag, r, z, S.y, grid, timeout_ns, s);
 }
 
 cudaError_t launch_solve_prepare(const SolvePlan& S, cudaStream_t s) {
