@@ -242,6 +242,57 @@ int ic_get_timing(const ic_handle* h, ic_timing_t* out);
  * bounded; nothing traps).  extra = 0 restores the plan.  Errors: IC_ERR_ARG, IC_ERR_CUDA. */
 int ic_test_hold_task(ic_handle* h, int64_t t, int extra);
 
+/* Batched symbolic factorization: count independent SPD matrices (different sizes
+ * allowed) become one block-diagonal system whose task DAG is the union of the
+ * systems' independent DAGs, so one ic_numeric launch factors all of them.  System s
+ * occupies rows [row_off[s], row_off[s+1]) of the union in the original ordering;
+ * its values are the concatenation of every system's CSR values in order.
+ *   A        host, count patterns.
+ *   perms    host, NULL or count entries (each NULL = identity) of the systems' orders.
+ *   ranges, nranges  host, NULL or count entries: each system's ranges (NULL entry: the
+ *            whole system as one range, split by block_rows).
+ * Errors: as ic_symbolic. */
+int ic_symbolic_batch(int64_t count, const ic_csr_pattern* A, int k, const int32_t* const* perms,
+                      const int64_t* const* ranges, const int64_t* nranges, const ic_opts* opts,
+                      ic_handle** out);
+
+/* Number of systems of the handle (1 for ic_symbolic) and, when row_off is not NULL,
+ * their count+1 row offsets.  Errors: IC_ERR_ARG. */
+int ic_batch_info(const ic_handle* h, int64_t* count, int64_t* row_off);
+
+/* Independent PCG on every system of the handle (textbook PCG per system, x0 = 0, each
+ * system stops when its own ||r||/||b|| <= tol; a converged system's iterate no longer
+ * changes while the others continue).  One iteration over all systems is captured
+ * into a CUDA graph and replayed; convergence is read from the device every 4
+ * iterations.  b and x: device, the union's rows.  iters, relres: host, count entries
+ * or NULL.  Errors: IC_ERR_ARG, IC_ERR_STATE, IC_ERR_NOCONV (some system reached maxit),
+ * IC_ERR_TIMEOUT, IC_ERR_CUDA. */
+int pcg_solve_batch(ic_handle* h, const void* A_vals, const double* b, double* x, double tol, int maxit,
+                    int* iters, double* relres, void* stream);
+
+/* ic_numeric without the final synchronisation: enqueues the value scatter, the task
+ * kernel and the copies of the status words on stream, so it can be captured into a
+ * CUDA graph.  After the stream (or graph) has completed, ic_numeric_status returns
+ * what ic_numeric would have (IC_OK, IC_ERR_BREAKDOWN with *breakdown_row,
+ * IC_ERR_TIMEOUT).  Until then the factor is treated as valid by ic_apply.
+ * Errors: IC_ERR_ARG, IC_ERR_STATE, IC_ERR_CUDA. */
+int ic_numeric_async(ic_handle* h, const void* values, void* stream);
+int ic_numeric_status(ic_handle* h, int64_t* breakdown_row);
+
+/* Autotuner for the task granularity trade-offs of Section 4 (block size and the work
+ * per task) and the solve launch shape.  For the given matrix or batch (count = 1 for
+ * one matrix; arguments as ic_symbolic_batch), it times ic_numeric (median of reps)
+ * over block_rows in {1024, 2048, 4096, 8192}, then warps_per_cta in {8, 16}, then
+ * rows_per_item in {16, 32, 64} (coordinate search, each best kept), and ic_apply over
+ * solve_lanes in {16, 32} x solve_ctas_per_sm in {2, 3, 4} on the chosen plan.
+ * values: device, the (concatenated) values.  base: other options (NULL: defaults).
+ * best: receives the chosen options; times (host, 2 doubles or NULL): numeric ms and
+ * apply ms of the choice.  The stream is synchronised.
+ * Errors: as ic_symbolic and ic_numeric. */
+int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* const* perms,
+                const int64_t* const* ranges, const int64_t* nranges, const void* values,
+                const ic_opts* base, int reps, ic_opts* best, double* times, void* stream);
+
 /* Task trace of the numeric kernel.  ic_set_trace(h, 1) allocates 4 uint64 words per
  * work item; every later ic_numeric records, per queue slot, the %globaltimer start
  * and end (ns) of the item, task | chunk << 32, and the SM that ran it.

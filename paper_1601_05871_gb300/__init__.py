@@ -30,3 +30,11 @@ from .ick import (  # noqa: F401
     IC_F32,
     TASK_NAMES,
 )
+from .ick import (  # noqa: F401,E402
+    ic_symbolic_batch,
+    ic_batch_info,
+    pcg_solve_batch,
+    ic_numeric_async,
+    ic_numeric_status,
+    ic_autotune,
+)

@@ -2,6 +2,7 @@
 // the symbolic plan, and the host orchestration of the numeric, apply and PCG kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -72,6 +73,16 @@ struct ic_handle {
     bool apply_pending = false;  // ev[3]..ev[4] bracket an apply not yet added to tm
     ic_timing_t tm{};
     unsigned long long* trace_buf = nullptr;  // ic_set_trace
+    // systems of a batch (one system for ic_symbolic): row offsets, per-row system id,
+    // per-system PCG scalars
+    std::vector<int64_t> row_off;
+    long long* d_row_off = nullptr;
+    int* d_sys = nullptr;
+    BatchScalars bs{};
+    int* h_nactive = nullptr;      // pinned
+    bool numeric_pending = false;  // ic_numeric_async issued, status not read yet
+    cudaStream_t cap_stream = nullptr;  // graph capture / replay stream of pcg_solve_batch
+    cudaEvent_t cap_ev[2] = {nullptr, nullptr};
 
     ~ic_handle() {
         for (cudaEvent_t e : ev)
@@ -80,6 +91,10 @@ struct ic_handle {
         if (h_counters) cudaFreeHost(h_counters);
         if (h_brk) cudaFreeHost(h_brk);
         if (h_sc) cudaFreeHost(h_sc);
+        if (h_nactive) cudaFreeHost(h_nactive);
+        for (cudaEvent_t e : cap_ev)
+            if (e) cudaEventDestroy(e);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 
     template <class T>
@@ -185,6 +200,8 @@ int upload_plan(ic_handle* h) {
     if ((st = h->alloc(&D.counters, 8))) return st;
     if ((st = h->alloc(&D.brk_row, 1))) return st;
     if ((st = h->alloc(&D.diag, 8))) return st;
+    if ((st = h->alloc(&D.epoch_dev, 1))) return st;
+    CK(cudaMemset(D.epoch_dev, 0, sizeof(int)));
 
     // solve / PCG buffers
     SolvePlan& S = h->sp;
@@ -257,6 +274,40 @@ int fold_apply_time(ic_handle* h) {
     return IC_OK;
 }
 
+// Record the systems of the handle (count+1 row offsets into the original ordering)
+// and allocate the per-row system ids and per-system PCG scalars.
+int attach_batch(ic_handle* h, const int64_t* off, int64_t count) {
+    h->row_off.assign(off, off + count + 1);
+    const int64_t n = h->hp.n;
+    std::vector<int32_t> sys(n);
+    for (int64_t s = 0; s < count; ++s)
+        for (int64_t i = off[s]; i < off[s + 1]; ++i) sys[i] = int32_t(s);
+    int st = 0;
+    const int* dsys = nullptr;
+    if ((st = h->upload(&dsys, sys))) return st;
+    h->d_sys = const_cast<int*>(dsys);
+    const int64_t* droff = nullptr;
+    if ((st = h->upload(&droff, h->row_off))) return st;
+    h->d_row_off = reinterpret_cast<long long*>(const_cast<int64_t*>(droff));
+    BatchScalars& B = h->bs;
+    double* dbuf = nullptr;
+    if ((st = h->alloc(&dbuf, 6 * size_t(count)))) return st;
+    B.tmp = dbuf;
+    B.rz = dbuf + count;
+    B.bnorm = dbuf + 2 * count;
+    B.alpha = dbuf + 3 * count;
+    B.beta = dbuf + 4 * count;
+    B.relres = dbuf + 5 * count;
+    int* ibuf = nullptr;
+    if ((st = h->alloc(&ibuf, 2 * size_t(count) + 2))) return st;
+    B.active = ibuf;
+    B.iters = ibuf + count;
+    B.nactive = ibuf + 2 * count;
+    B.iter = ibuf + 2 * count + 1;
+    CK(cudaMallocHost(&h->h_nactive, sizeof(int)));
+    return IC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -287,8 +338,11 @@ int ic_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* ke
     }
 }
 
-int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
-                int64_t nranges, const ic_opts* opts, ic_handle** out) {
+// Shared by ic_symbolic (one system) and ic_symbolic_batch (row_off: count+1 offsets
+// of the systems inside the block-diagonal union).
+static int symbolic_impl(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
+                         int64_t nranges, const ic_opts* opts, const int64_t* row_off, int64_t count,
+                         ic_handle** out) {
     if (!out) return fail(IC_ERR_ARG, "NULL out");
     *out = nullptr;
     const auto t0 = std::chrono::steady_clock::now();
@@ -319,6 +373,7 @@ int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64
             return fail(st, err);
         }
         if (h->opts.host_only) {
+            h->row_off.assign(row_off, row_off + count + 1);
             h->symbolic_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
             *out = h;
             return IC_OK;
@@ -329,6 +384,7 @@ int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64
             return cuda_fail(e, "cudaGetDevice");
         }
         st = upload_plan(h);
+        if (!st) st = attach_batch(h, row_off, count);
         if (st) {
             delete h;
             return st;
@@ -342,41 +398,97 @@ int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64
     return IC_OK;
 }
 
-int ic_numeric(ic_handle* h, const void* values, void* stream, int64_t* breakdown_row) {
-    if (breakdown_row) *breakdown_row = -1;
-    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
+                int64_t nranges, const ic_opts* opts, ic_handle** out) {
+    if (!A) return fail(IC_ERR_ARG, "NULL pattern");
+    const int64_t off[2] = {0, A->n};
+    return symbolic_impl(A, k, perm, ranges, nranges, opts, off, 1, out);
+}
+
+int ic_symbolic_batch(int64_t count, const ic_csr_pattern* A, int k, const int32_t* const* perms,
+                      const int64_t* const* ranges, const int64_t* nranges, const ic_opts* opts,
+                      ic_handle** out) {
+    if (!out) return fail(IC_ERR_ARG, "NULL out");
+    *out = nullptr;
+    if (count < 1 || !A) return fail(IC_ERR_ARG, "count must be >= 1 and A non-NULL");
+    try {
+        // block-diagonal union: rows and columns of system s shifted by row_off[s]; each
+        // system's ordering and ranges are kept and shifted the same way
+        std::vector<int64_t> off(count + 1, 0), noff(count + 1, 0);
+        for (int64_t s = 0; s < count; ++s) {
+            if (A[s].n < 0 || (A[s].n > 0 && (!A[s].rowptr || !A[s].colind)))
+                return fail(IC_ERR_ARG, "system " + std::to_string(s) + ": bad pattern");
+            off[s + 1] = off[s] + A[s].n;
+            noff[s + 1] = noff[s] + (A[s].n ? A[s].rowptr[A[s].n] : 0);
+        }
+        const int64_t n = off[count];
+        if (n > INT32_MAX - 1 || noff[count] > INT32_MAX) return fail(IC_ERR_ARG, "batch too large");
+        std::vector<int64_t> rp(n + 1, 0);
+        std::vector<int32_t> ci(noff[count]);
+        std::vector<int32_t> pm(n);
+        std::vector<int64_t> rg(1, 0);
+        for (int64_t s = 0; s < count; ++s) {
+            const ic_csr_pattern& a = A[s];
+            for (int64_t i = 0; i < a.n; ++i) {
+                rp[off[s] + i + 1] = noff[s] + a.rowptr[i + 1];
+                for (int64_t e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e)
+                    ci[noff[s] + e] = int32_t(a.colind[e] + off[s]);
+                const int32_t pi = (perms && perms[s]) ? perms[s][i] : int32_t(i);
+                if (pi < 0 || pi >= a.n) return fail(IC_ERR_ARG, "system " + std::to_string(s) + ": bad perm");
+                pm[off[s] + i] = int32_t(pi + off[s]);
+            }
+            if (ranges && ranges[s] && nranges) {
+                for (int64_t b = 1; b <= nranges[s]; ++b) rg.push_back(ranges[s][b] + off[s]);
+                if (nranges[s] < 1 || ranges[s][0] != 0 || ranges[s][nranges[s]] != a.n)
+                    return fail(IC_ERR_ARG, "system " + std::to_string(s) + ": ranges must run from 0 to n");
+            } else if (a.n > 0) {
+                rg.push_back(off[s + 1]);  // the whole system as one range (split by block_rows)
+            }
+        }
+        ic_csr_pattern U{n, rp.data(), ci.data()};
+        return symbolic_impl(&U, k, pm.data(), rg.data(), int64_t(rg.size()) - 1, opts, off.data(), count, out);
+    } catch (const std::bad_alloc&) {
+        return fail(IC_ERR_NOMEM, "host allocation failed");
+    }
+}
+
+int ic_batch_info(const ic_handle* h, int64_t* count, int64_t* row_off) {
+    if (!h || !count) return fail(IC_ERR_ARG, "NULL argument");
+    *count = int64_t(h->row_off.size()) - 1;
+    if (row_off) std::memcpy(row_off, h->row_off.data(), h->row_off.size() * sizeof(int64_t));
+    return IC_OK;
+}
+
+// Enqueue the numeric phase and the copies of its status words to pinned host memory.
+// With timing on, events bracket the scatter and the task kernel.
+static int numeric_enqueue(ic_handle* h, const void* values, cudaStream_t s, bool timing) {
     if (!values && h->hp.nnz_a > 0) return fail(IC_ERR_ARG, "NULL values");
     if (h->opts.host_only) return fail(IC_ERR_STATE, "handle was created with host_only");
-    DeviceGuard g(h->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    h->factored = false;
     const int epoch = ++h->epoch;
     const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
-    if (h->timing) CK(cudaEventRecord(h->ev[0], s));
+    if (timing) CK(cudaEventRecord(h->ev[0], s));
     CK(launch_numeric_prepare(h->dp, static_cast<const double*>(values), h->opts.shift_alpha, epoch,
                               h->opts.dtype, s));
     ++h->tm.launches;
-    if (h->timing) CK(cudaEventRecord(h->ev[1], s));
+    if (timing) CK(cudaEventRecord(h->ev[1], s));
     if (h->dp.total_items > 0) {
         CK(launch_numeric(h->dp, epoch, h->opts.warps_per_cta, h->opts.exact != 0, h->opts.dtype,
-                          h->grid_numeric,
-                          tmo, s));
+                          h->grid_numeric, tmo, s));
         ++h->tm.launches;
     }
-    if (h->timing) CK(cudaEventRecord(h->ev[2], s));
+    if (timing) CK(cudaEventRecord(h->ev[2], s));
     CK(launch_solve_prepare(h->sp, s));
     ++h->tm.launches;
     CK(cudaMemcpyAsync(h->h_counters, h->dp.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->h_counters + 4, h->dp.diag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->h_brk, h->dp.brk_row, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (h->timing) {
-        float a = 0.f, b = 0.f;
-        CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
-        CK(cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
-        h->tm.prepare_ms = a;
-        h->tm.numeric_ms = b;
-    }
+    return IC_OK;
+}
+
+// Interpret the status words copied by the last enqueued numeric phase.
+static int numeric_status(ic_handle* h, int64_t* breakdown_row) {
+    h->numeric_pending = false;
+    h->factored = false;
     const int bits = h->h_counters[2];
     if (bits & kStTimeout)
         return fail(IC_ERR_TIMEOUT, "numeric: device wait timed out at site " + std::to_string(h->h_counters[5]));
@@ -389,6 +501,41 @@ int ic_numeric(ic_handle* h, const void* values, void* stream, int64_t* breakdow
     }
     h->factored = true;
     return IC_OK;
+}
+
+int ic_numeric(ic_handle* h, const void* values, void* stream, int64_t* breakdown_row) {
+    if (breakdown_row) *breakdown_row = -1;
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    DeviceGuard g(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->factored = false;
+    int st = numeric_enqueue(h, values, s, h->timing);
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));
+    if (h->timing) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+        CK(cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
+        h->tm.prepare_ms = a;
+        h->tm.numeric_ms = b;
+    }
+    return numeric_status(h, breakdown_row);
+}
+
+int ic_numeric_async(ic_handle* h, const void* values, void* stream) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    DeviceGuard g(h->device);
+    int st = numeric_enqueue(h, values, static_cast<cudaStream_t>(stream), false);
+    if (st) return st;
+    h->numeric_pending = true;
+    h->factored = true;  // provisional until ic_numeric_status reads the status words
+    return IC_OK;
+}
+
+int ic_numeric_status(ic_handle* h, int64_t* breakdown_row) {
+    if (breakdown_row) *breakdown_row = -1;
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    return numeric_status(h, breakdown_row);
 }
 
 int ic_apply(ic_handle* h, const void* r, void* z, void* stream) {
@@ -514,6 +661,102 @@ int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, doub
     if (iters) *iters = it;
     if (relres) *relres = rel;
     if (!(rel <= tol)) return fail(IC_ERR_NOCONV, "PCG reached maxit");
+    return IC_OK;
+}
+
+// One iteration of batched PCG (captured once per solve, replayed as a graph).
+static cudaError_t batch_iteration(ic_handle* h, const double* av, double* x, double tol,
+                                   unsigned long long tmo, cudaStream_t s) {
+    BatchScalars& B = h->bs;
+    const int n = int(h->hp.n), count = int(h->row_off.size()) - 1;
+    cudaError_t e;
+    if ((e = batch_bump(B, s)) != cudaSuccess) return e;
+    if ((e = launch_spmv(h->sp, av, h->p, h->q, s)) != cudaSuccess) return e;
+    if ((e = batch_dot(h->d_row_off, count, h->p, h->q, B.tmp, s)) != cudaSuccess) return e;
+    if ((e = batch_scalars(B, count, 0, tol, s)) != cudaSuccess) return e;
+    if ((e = batch_xr(n, h->d_sys, B.alpha, x, h->r, h->p, h->q, s)) != cudaSuccess) return e;
+    if ((e = batch_dot(h->d_row_off, count, h->r, h->r, B.tmp, s)) != cudaSuccess) return e;
+    if ((e = batch_scalars(B, count, 1, tol, s)) != cudaSuccess) return e;
+    if ((e = launch_apply(h->sp, h->r, h->z, 0, tmo, h->grid_apply, s)) != cudaSuccess) return e;
+    if ((e = batch_dot(h->d_row_off, count, h->r, h->z, B.tmp, s)) != cudaSuccess) return e;
+    if ((e = batch_scalars(B, count, 2, tol, s)) != cudaSuccess) return e;
+    return batch_p(n, h->d_sys, B.beta, B.active, h->p, h->z, s);
+}
+
+int pcg_solve_batch(ic_handle* h, const void* A_vals, const double* b, double* x, double tol, int maxit,
+                    int* iters, double* relres, void* stream) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    const int n = int(h->hp.n), count = int(h->row_off.size()) - 1;
+    if (iters)
+        for (int s = 0; s < count; ++s) iters[s] = 0;
+    if (relres)
+        for (int s = 0; s < count; ++s) relres[s] = 0.0;
+    if (n > 0 && (!A_vals || !b || !x)) return fail(IC_ERR_ARG, "NULL argument");
+    if (!(tol >= 0.0) || maxit < 0) return fail(IC_ERR_ARG, "tol/maxit out of range");
+    if (!h->factored) return fail(IC_ERR_STATE, "pcg_solve_batch before a successful ic_numeric");
+    if (n == 0 || count < 1) return IC_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t us = static_cast<cudaStream_t>(stream);
+    if (!h->cap_stream) {
+        CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->cap_ev[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->cap_ev[1], cudaEventDisableTiming));
+    }
+    cudaStream_t s = h->cap_stream;  // capturable even when the caller uses the legacy stream
+    CK(cudaEventRecord(h->cap_ev[0], us));
+    CK(cudaStreamWaitEvent(s, h->cap_ev[0], 0));
+    const double* av = static_cast<const double*>(A_vals);
+    BatchScalars& B = h->bs;
+    const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
+    CK(cudaMemsetAsync(h->sp.counter + 2, 0, sizeof(int), s));
+    CK(pcg_init(n, b, x, h->r, s));
+    CK(batch_dot(h->d_row_off, count, b, b, B.tmp, s));
+    CK(batch_scalars(B, count, 4, tol, s));
+    CK(launch_apply(h->sp, h->r, h->z, 0, tmo, h->grid_apply, s));
+    CK(cudaMemcpyAsync(h->p, h->z, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(batch_dot(h->d_row_off, count, h->r, h->z, B.tmp, s));
+    CK(batch_scalars(B, count, 3, tol, s));
+    h->tm.launches += 8;
+    // capture one iteration and replay it; convergence is read every few iterations
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t ce = batch_iteration(h, av, x, tol, tmo, s);
+    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ce != cudaSuccess ? ce : ee, "pcg_solve_batch: graph capture");
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+    int it = 0;
+    cudaError_t le = cudaSuccess;
+    while (it < maxit) {
+        const int burst = std::min(4, maxit - it);
+        for (int j = 0; j < burst && le == cudaSuccess; ++j) le = cudaGraphLaunch(exec, s);
+        if (le == cudaSuccess) le = cudaMemcpyAsync(h->h_nactive, B.nactive, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (le == cudaSuccess) le = cudaStreamSynchronize(s);
+        if (le != cudaSuccess) break;
+        it += burst;
+        if (*h->h_nactive == 0) break;
+    }
+    cudaGraphExecDestroy(exec);
+    if (le != cudaSuccess) return cuda_fail(le, "pcg_solve_batch: graph launch");
+    h->tm.launches += int64_t(it) * 13;
+    std::vector<int> its(count);
+    std::vector<double> rel(count);
+    CK(cudaMemcpy(its.data(), B.iters, count * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rel.data(), B.relres, count * sizeof(double), cudaMemcpyDeviceToHost));
+    int abort_word = 0;
+    CK(cudaMemcpy(&abort_word, h->sp.counter + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaEventRecord(h->cap_ev[1], s));
+    CK(cudaStreamWaitEvent(us, h->cap_ev[1], 0));
+    if (iters) std::memcpy(iters, its.data(), count * sizeof(int));
+    if (relres) std::memcpy(relres, rel.data(), count * sizeof(double));
+    if (abort_word) return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
+    for (int s2 = 0; s2 < count; ++s2)
+        if (!(rel[s2] <= tol)) return fail(IC_ERR_NOCONV, "system " + std::to_string(s2) + " reached maxit");
     return IC_OK;
 }
 
@@ -737,6 +980,110 @@ int ic_test_hold_task(ic_handle* h, int64_t t, int extra) {
         CK(cudaMemcpy(const_cast<int2*>(h->dp.seeds), seeds.data(), seeds.size() * sizeof(int2),
                       cudaMemcpyHostToDevice));
     h->dp.nseeds = nseed;
+    return IC_OK;
+}
+
+int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* const* perms,
+                const int64_t* const* ranges, const int64_t* nranges, const void* values,
+                const ic_opts* base, int reps, ic_opts* best, double* times, void* stream) {
+    if (!best || !values || reps < 1) return fail(IC_ERR_ARG, "NULL best/values or reps < 1");
+    ic_opts cur = normalise(base);
+    cur.host_only = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // median numeric time of a candidate (rebuilds the plan), or < 0 on error
+    auto time_numeric = [&](const ic_opts& o, ic_handle** keep) -> double {
+        ic_handle* h = nullptr;
+        if (ic_symbolic_batch(count, A, k, perms, ranges, nranges, &o, &h)) return -1.0;
+        if (ic_set_timing(h, 1)) { ic_destroy(h); return -1.0; }
+        std::vector<double> t;
+        for (int r = 0; r <= reps; ++r) {
+            if (ic_numeric(h, values, s, nullptr)) { ic_destroy(h); return -1.0; }
+            if (r > 0) t.push_back(h->tm.prepare_ms + h->tm.numeric_ms);  // first run warms up
+        }
+        std::sort(t.begin(), t.end());
+        if (keep) *keep = h; else ic_destroy(h);
+        return t[t.size() / 2];
+    };
+    double best_num = -1.0;
+    {
+        const int cand[] = {1024, 2048, 4096, 8192};
+        ic_opts pick = cur;
+        for (int br : cand) {
+            ic_opts o = cur;
+            o.block_rows = br;
+            const double t = time_numeric(o, nullptr);
+            if (t >= 0 && (best_num < 0 || t < best_num)) { best_num = t; pick = o; }
+        }
+        if (best_num < 0) return fail(IC_ERR_ARG, "autotune: no candidate factored (" + std::string(ic_last_error()) + ")");
+        cur = pick;
+    }
+    for (int w : {8, 16}) {
+        if (w == cur.warps_per_cta) continue;
+        ic_opts o = cur;
+        o.warps_per_cta = w;
+        const double t = time_numeric(o, nullptr);
+        if (t >= 0 && t < best_num) { best_num = t; cur = o; }
+    }
+    for (int rpi : {16, 32, 64}) {
+        if (rpi == cur.rows_per_item) continue;
+        ic_opts o = cur;
+        o.rows_per_item = rpi;
+        const double t = time_numeric(o, nullptr);
+        if (t >= 0 && t < best_num) { best_num = t; cur = o; }
+    }
+    // solve launch shape on the chosen plan: lanes per row and CTAs per SM
+    ic_handle* h = nullptr;
+    if (time_numeric(cur, &h) < 0) return fail(IC_ERR_ARG, "autotune: chosen plan failed");
+    double best_apply = -1.0;
+    {
+        DeviceGuard g(h->device);
+        int sms = 0, dev = 0, bpsm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(apply_blocks_per_sm(&bpsm));
+        double* r = nullptr;
+        double* z = nullptr;
+        CK(cudaMalloc(&r, 2 * size_t(h->hp.n > 0 ? h->hp.n : 1) * sizeof(double)));
+        z = r + h->hp.n;
+        CK(cudaMemsetAsync(r, 0, 2 * size_t(h->hp.n) * sizeof(double), s));
+        std::vector<double> ones(h->hp.n, 1.0);
+        CK(cudaMemcpyAsync(r, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int lanes : {16, 32})
+            for (int cps : {2, 3, 4}) {
+                h->sp.lanes_per_row = lanes;
+                h->grid_apply = sms * std::min(cps, bpsm < 1 ? 1 : bpsm);
+                std::vector<float> t;
+                for (int q = 0; q <= reps; ++q) {
+                    CK(cudaEventRecord(e0, s));
+                    CK(launch_apply(h->sp, r, z, 0, (unsigned long long)(h->opts.timeout_s * 1e9),
+                                    h->grid_apply, s));
+                    CK(cudaEventRecord(e1, s));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    if (q > 0) t.push_back(ms);
+                }
+                std::sort(t.begin(), t.end());
+                const double med = t[t.size() / 2];
+                if (best_apply < 0 || med < best_apply) {
+                    best_apply = med;
+                    cur.solve_lanes = lanes;
+                    cur.solve_ctas_per_sm = cps;
+                }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(r);
+    }
+    ic_destroy(h);
+    *best = cur;
+    if (times) {
+        times[0] = best_num;
+        times[1] = best_apply;
+    }
     return IC_OK;
 }
 

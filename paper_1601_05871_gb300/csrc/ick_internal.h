@@ -101,6 +101,7 @@ struct DevPlan {
                                 // task | chunk << 32, SM id
     double* udiag;         // IC_F32: FP64 diagonal pivots (U_ii) of the factor
     const int* diag_src;   // IC_F32: index of A's diagonal value of each row
+    int* epoch_dev;        // queue epoch, advanced on the device before each numeric phase
 };
 
 // Status bits written by the kernels into counters[2].
@@ -170,6 +171,20 @@ cudaError_t pcg_step_x_r(int n, double* x, double* r, const double* p, const dou
                          PcgScalars* sc, double* partial, int nparts, cudaStream_t s);
 cudaError_t pcg_step_p(int n, double* p, const double* z, PcgScalars* sc, cudaStream_t s);
 cudaError_t pcg_init(int n, const double* b, double* x, double* r, cudaStream_t s);
+
+// Batched PCG (batch.cu): per-system scalars of systems stored block-diagonally.
+struct BatchScalars {
+    double *tmp, *rz, *bnorm, *alpha, *beta, *relres;
+    int *active, *iters, *nactive, *iter;
+};
+cudaError_t batch_dot(const long long* row_off, int count, const double* a, const double* b,
+                      double* out, cudaStream_t s);
+cudaError_t batch_scalars(const BatchScalars& B, int count, int op, double tol, cudaStream_t s);
+cudaError_t batch_bump(const BatchScalars& B, cudaStream_t s);
+cudaError_t batch_xr(int n, const int* sys, const double* alpha, double* x, double* r, const double* p,
+                     const double* q, cudaStream_t s);
+cudaError_t batch_p(int n, const int* sys, const double* beta, const int* active, double* p,
+                    const double* z, cudaStream_t s);
 
 // Host symbolic phase (host.cpp).
 int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,

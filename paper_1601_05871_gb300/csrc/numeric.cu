@@ -346,7 +346,10 @@ static_assert(sizeof(Slot<double>) % 16 == 0 && sizeof(Slot<float>) % 16 == 0,
 
 template <int WARPS, bool EXACT, typename T>
 __global__ void __launch_bounds__(WARPS * 32)
-numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
+numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
+    // the queue's epoch lives on the device (advanced before every numeric phase), so a
+    // replayed CUDA graph never mistakes the previous run's slots for filled ones
+    const int epoch = *reinterpret_cast<const volatile int*>(P.epoch_dev);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     unsigned char* s_done = smem_raw + kSmemHead;
@@ -469,7 +472,8 @@ numeric_persistent(DevPlan P, int epoch, unsigned long long timeout_ns) {
 // values are rounded to FP32 and the diagonals go to the FP64 array udiag.
 template <typename T>
 __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double alpha, int nnz_u,
-                                int epoch) {
+                                int) {
+    const int epoch = *reinterpret_cast<const volatile int*>(P.epoch_dev);
     constexpr bool MIXED = std::is_same<T, float>::value;
     const int stride = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -510,6 +514,10 @@ __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double
     }
 }
 
+// Starts a new queue epoch (stamps never repeat between numeric phases, whether issued
+// directly or replayed from a graph; stamps wrap after 2^31 phases).
+__global__ void advance_epoch(int* e) { *e = (*e == 0x7fffffff) ? 1 : *e + 1; }
+
 template <int WARPS, bool EXACT, typename T>
 cudaError_t launch_t(const DevPlan& P, int grid, int epoch, unsigned long long timeout_ns,
                      cudaStream_t s) {
@@ -541,6 +549,9 @@ cudaError_t launch_numeric_prepare(const DevPlan& P, const double* avals, double
     const int work = P.nnz_u > P.ntasks ? P.nnz_u : P.ntasks;
     int pgrid = (work + 255) / 256;
     pgrid = pgrid < 1 ? 1 : (pgrid > 8192 ? 8192 : pgrid);
+    advance_epoch<<<1, 1, 0, s>>>(P.epoch_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     if (dtype == IC_F32)
         numeric_prepare<float><<<pgrid, 256, 0, s>>>(P, avals, shift_alpha, P.nnz_u, epoch);
     else

@@ -74,6 +74,12 @@ def load():
         "ic_reset_timing": (I, [P]),
         "ic_get_timing": (I, [P, P]),
         "ic_test_hold_task": (I, [P, I64, I]),
+        "ic_symbolic_batch": (I, [I64, P, I, P, P, P, P, P]),
+        "ic_batch_info": (I, [P, P, P]),
+        "pcg_solve_batch": (I, [P, P, P, P, D, I, P, P, P]),
+        "ic_numeric_async": (I, [P, P, P]),
+        "ic_numeric_status": (I, [P, P]),
+        "ic_autotune": (I, [I64, P, I, P, P, P, P, P, I, P, P, P]),
         "ic_set_trace": (I, [P, I]),
         "ic_get_trace": (I, [P, P]),
         "ic_destroy": (None, [P]),
@@ -338,6 +344,108 @@ def ic_get_trace(h):
     out = np.zeros((n, 4), dtype=np.uint64)
     _check(load().ic_get_trace(h.ptr, _p(out)))
     return out
+
+
+def _opts(block_rows=0, dtype=IC_F64, warps_per_cta=0, rows_per_item=0, timeout_s=0.0, shift_alpha=0.0,
+          exact=0, threads=0, host_only=0, solve_ctas_per_sm=0, solve_lanes=0):
+    return ic_opts(block_rows, dtype, warps_per_cta, rows_per_item, timeout_s, shift_alpha, exact, threads,
+                   host_only, solve_ctas_per_sm, solve_lanes)
+
+
+def _batch_args(patterns, perms, ranges):
+    """ctypes arrays for a batch: patterns is a list of (rowptr, colind)."""
+    count = len(patterns)
+    keep = []
+    pats = (ic_csr_pattern * count)()
+    for s, (rp, ci) in enumerate(patterns):
+        rp = np.ascontiguousarray(rp, dtype=np.int64)
+        ci = np.ascontiguousarray(ci, dtype=np.int32)
+        keep += [rp, ci]
+        pats[s] = ic_csr_pattern(len(rp) - 1, _p(rp), _p(ci))
+    pp = None
+    if perms is not None:
+        pp = (C.c_void_p * count)()
+        for s, pm in enumerate(perms):
+            if pm is not None:
+                pm = np.ascontiguousarray(pm, dtype=np.int32)
+                keep.append(pm)
+                pp[s] = pm.ctypes.data
+    rr, nr = None, None
+    if ranges is not None:
+        rr = (C.c_void_p * count)()
+        nr = np.zeros(count, dtype=np.int64)
+        keep.append(nr)
+        for s, rg in enumerate(ranges):
+            if rg is not None:
+                rg = np.ascontiguousarray(rg, dtype=np.int64)
+                keep.append(rg)
+                rr[s] = rg.ctypes.data
+                nr[s] = len(rg) - 1
+    return count, pats, pp, rr, nr, keep
+
+
+def ic_symbolic_batch(patterns, k, perms=None, ranges=None, **opts):
+    """One handle over independent systems; patterns: list of (rowptr, colind)."""
+    L = load()
+    count, pats, pp, rr, nr, keep = _batch_args(patterns, perms, ranges)
+    o = _opts(**opts)
+    out = C.c_void_p()
+    _check(L.ic_symbolic_batch(count, pats, int(k), pp, rr, _p(nr), C.byref(o), C.byref(out)))
+    n = sum(len(p[0]) - 1 for p in patterns)
+    nnz = sum(int(np.asarray(p[0])[-1]) for p in patterns)
+    del keep
+    return Handle(out.value, n, nnz)
+
+
+def ic_batch_info(h):
+    """Row offsets (count+1) of the handle's systems."""
+    L = load()
+    cnt = np.zeros(1, dtype=np.int64)
+    _check(L.ic_batch_info(h.ptr, _p(cnt), None))
+    off = np.empty(int(cnt[0]) + 1, dtype=np.int64)
+    _check(L.ic_batch_info(h.ptr, _p(cnt), _p(off)))
+    return off
+
+
+def pcg_solve_batch(h, A_vals, b, x, tol=1e-8, maxit=10000, stream=None, raise_noconv=True):
+    """Independent PCG per system; returns (iters, relres) arrays."""
+    count = len(ic_batch_info(h)) - 1
+    it = np.zeros(count, dtype=np.int32)
+    rel = np.zeros(count, dtype=np.float64)
+    st = load().pcg_solve_batch(h.ptr, _p(A_vals), _p(b), _p(x), float(tol), int(maxit), _p(it), _p(rel),
+                                _stream(stream))
+    if st != IC_ERR_NOCONV or raise_noconv:
+        _check(st)
+    return it, rel
+
+
+def ic_numeric_async(h, values, stream=None):
+    _check(load().ic_numeric_async(h.ptr, _p(values), _stream(stream)))
+
+
+def ic_numeric_status(h):
+    brk = np.zeros(1, dtype=np.int64)
+    st = load().ic_numeric_status(h.ptr, _p(brk))
+    if st == IC_ERR_BREAKDOWN:
+        e = IckError(st, f"breakdown at row {int(brk[0])}")
+        e.row = int(brk[0])
+        raise e
+    _check(st)
+    return -1
+
+
+def ic_autotune(patterns, k, values, perms=None, ranges=None, reps=3, stream=None, **base):
+    """Returns (opts dict, (numeric_ms, apply_ms)) chosen by timing on the device."""
+    L = load()
+    count, pats, pp, rr, nr, keep = _batch_args(patterns, perms, ranges)
+    b = _opts(**base)
+    best = ic_opts()
+    times = np.zeros(2, dtype=np.float64)
+    _check(L.ic_autotune(count, pats, int(k), pp, rr, _p(nr), _p(values), C.byref(b), int(reps),
+                         C.byref(best), _p(times), _stream(stream)))
+    del keep
+    d = {f: getattr(best, f) for f, _ in best._fields_ if f != "reserved"}
+    return d, (float(times[0]), float(times[1]))
 
 
 def ic_destroy(h):

@@ -319,3 +319,59 @@ def test_plan_in_random_orders_matches_oracle_bitwise(orc, case):
         rows = np.repeat(np.arange(n), np.diff(lrp))
         upos = urp[lci] + np.array([np.searchsorted(ucol[urp[c]:urp[c + 1]], r) for r, c in zip(rows, lci)])
         assert np.array_equal(U[upos], lref), (case, trial)
+
+
+# ------------------------------------------------------------------ batches (block-diagonal unions)
+
+def _batch(orc, count=6, seed=3000):
+    probs = synth.diffusion_batch(count, 3, 7, seed=seed)
+    perms = [orc.nd_grid(*p.grid, 1, 40)[0] for p in probs]
+    return probs, perms
+
+
+def test_batch_plan_is_union_of_independent_plans(orc):
+    probs, perms = _batch(orc)
+    h = ick.ic_symbolic_batch([(p.rowptr, p.colind) for p in probs], 1, perms, host_only=1, block_rows=64)
+    off = ick.ic_batch_info(h)
+    assert list(np.diff(off)) == [p.n for p in probs]
+    rp, ci, _, lv = ick.ic_get_factor(h, values=False)
+    for s, (p, pm) in enumerate(zip(probs, perms)):
+        o = orc.OracleIC.from_problem(p, pm, 1)
+        orp, oci, olv = o.pattern()
+        a, b = off[s], off[s + 1]
+        assert np.array_equal(rp[a:b + 1] - rp[a], orp)
+        assert np.array_equal(ci[rp[a]:rp[b]] - a, oci) and np.array_equal(lv[rp[a]:rp[b]], olv)
+    # no task depends on a task of another system
+    rng, bptr, bcol = ick.ic_get_blocks(h)
+    sys_of_block = np.searchsorted(off, rng[:-1], side="right") - 1
+    d = ick.ic_get_tasks(h)
+    pp, pr = d["pred_ptr"], d["pred"]
+    for t in range(len(d["type"])):
+        for q in pr[pp[t]:pp[t + 1]]:
+            assert sys_of_block[d["k"][t]] == sys_of_block[d["k"][q]]
+
+
+def test_batch_plan_executes_bitwise_per_system(orc):
+    probs, perms = _batch(orc, count=4, seed=3100)
+    rows, cols, vals = [], [], []
+    off = 0
+    for p in probs:
+        r = np.repeat(np.arange(p.n), np.diff(p.rowptr)) + off
+        rows.append(r); cols.append(p.colind + off); vals.append(p.vals)
+        off += p.n
+    union = synth.matrices._from_coo("union", off, np.concatenate(rows), np.concatenate(cols),
+                                     np.concatenate(vals), 0)
+    uperm = np.concatenate([pm + o for pm, o in zip(perms, np.cumsum([0] + [p.n for p in probs])[:-1])])
+    h = ick.ic_symbolic_batch([(p.rowptr, p.colind) for p in probs], 1, perms, host_only=1, block_rows=48)
+    d = ick.ic_get_tasks(h)
+    urp, ucol, U = _execute_plan(union, uperm, h, _random_topo(d, np.random.default_rng(5)))
+    offs = ick.ic_batch_info(h)
+    for s, (p, pm) in enumerate(zip(probs, perms)):
+        o = orc.OracleIC.from_problem(p, pm, 1)
+        assert o.numeric(p.vals) == 0
+        lrp, lci, _ = o.pattern()
+        a = offs[s]
+        rws = np.repeat(np.arange(p.n), np.diff(lrp))
+        upos = urp[lci + a] + np.array([np.searchsorted(ucol[urp[c + a]:urp[c + a + 1]], r + a)
+                                        for r, c in zip(rws, lci)])
+        assert np.array_equal(U[upos], o.values()), s
