@@ -34,6 +34,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "IC(k) factor GFLOP/s & HBM GB/s; PCG time-to-1e-8 vs plain FP64 on GB300"
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (see the alu roofline in the design notes)
+# DRAM bytes (read + write) per launch of a solve kernel, keyed by (side, k, kernel):
+# ncu captures at 48^3 and 64^3 give 14.80 / 15.20 bytes per factor entry (forward /
+# backward) at both sizes, scaled here to the 96^3 factor (57,510,348 entries);
+# profiles/ holds the captures' summary
+SOLVE_TRAFFIC = {(96, 2, "forward_dag"): 14.80 * 57510348, (96, 2, "backward_dag"): 15.20 * 57510348}
 
 
 def parse():
@@ -52,12 +57,15 @@ def parse():
     ap.add_argument("--numeric-only", action="store_true",
                     help="time only the numeric factorization (for profiling runs)")
     ap.add_argument("--no-f32", action="store_true", help="skip the mixed-precision arm")
+    ap.add_argument("--solve-mode", type=int, default=0, choices=[0, 1],
+                    help="triangular solves: 0 block-DAG, 1 row-level")
     return ap.parse_args()
 
 
 def workload_name(a):
     return (f"27-point Laplacian {a.side}^3 (n={a.side ** 3}), geometric ND, 2D blocks <= "
-            f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}")
+            f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}, "
+            f"{'block-DAG' if a.solve_mode == 0 else 'row-level'} triangular solves")
 
 
 class ClockSampler:
@@ -194,7 +202,7 @@ def main():
     prob = synth.laplace3d_27pt(a.side)
     perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.block_rows)
     h = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
-                        warps_per_cta=a.warps)
+                        warps_per_cta=a.warps, solve_mode=a.solve_mode)
     st = ick.ic_stats(h)
     ick.ic_set_timing(h, True)
     stream = torch.cuda.current_stream()
@@ -264,20 +272,28 @@ def main():
     except Exception:
         peak_src = "fallback"
     n, nnz_l = st["n"], st["nnz_l"]
-    solve_bytes = nnz_l * 12 + n * 8 * 4  # both solves: L values + indices, r, y, z, perm
-    roof_numeric = {"kernel": "ic_numeric (value scatter + persistent task-DAG kernel)",
+    # one solve launch reads every factor entry once (8-byte value + 4-byte index) and
+    # four row vectors (row pointer, right-hand side, reciprocal diagonal, result)
+    solve_bytes = nnz_l * 12 + n * 8 * 4
+    roof_numeric = {"kernel": "numeric_persistent (+ numeric_prepare scatter)",
                     "bound": "alu", "achieved": st["flops"] / (mean_fact * 1e-3) / 1e9,
                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "peak_source": "nominal FP64",
                     "hbm_achieved_gbs": st["bytes"] / (mean_fact * 1e-3) / 1e9,
                     "hbm_peak_gbs": peak_hbm, "traffic": None}
     roof_numeric["frac"] = roof_numeric["achieved"] / roof_numeric["peak"]
-    per_apply = tim["apply_ms"] / max(1, tim["apply_calls"])
-    roof_solve = {"kernel": "forward_solve + backward_solve (one ic_apply)", "bound": "hbm",
-                  "achieved": solve_bytes / (per_apply * 1e-3) / 1e9 if per_apply > 0 else 0.0,
-                  "peak": peak_hbm, "unit": "GB/s", "peak_source": peak_src, "traffic": None}
-    roof_solve["frac"] = roof_solve["achieved"] / roof_solve["peak"]
-    dominant = roof_solve if apply_ms_step > mean_kern else roof_numeric
-
+    calls = max(1, tim["apply_calls"])
+    roofs = {"numeric": (mean_fact, roof_numeric)}
+    names = ("forward_dag", "backward_dag") if a.solve_mode == 0 else ("forward_solve_v", "backward_solve_v")
+    for name, key in zip(names, ("fwd_ms", "bwd_ms")):
+        per = tim[key] / calls
+        r = {"kernel": name, "bound": "hbm",
+             "achieved": solve_bytes / (per * 1e-3) / 1e9 if per > 0 else 0.0,
+             "peak": peak_hbm, "unit": "GB/s", "peak_source": peak_src,
+             "launch_ms": per, "algorithmic_bytes": solve_bytes,
+             "traffic": SOLVE_TRAFFIC.get((a.side, a.k, name))}
+        r["frac"] = r["achieved"] / r["peak"]
+        roofs[name] = (tim[key] / a.steps, r)
+    dominant = max(roofs.values(), key=lambda v: v[0])[1]
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -292,7 +308,9 @@ def main():
             "pcg": {"iters": iters[-1], "relres": rels[-1], "true_relres": true_rel,
                     "tol": a.tol, "apply_ms_per_step": apply_ms_step,
                     "time_to_solution_ms": ms_per_step},
-            "roofline": dominant, "roofline_numeric": roof_numeric, "roofline_solve": roof_solve,
+            "roofline": dominant, "roofline_numeric": roof_numeric,
+            "roofline_solves": [roofs[names[0]][1], roofs[names[1]][1]],
+            "ms_per_step_by_kernel": {k: v[0] for k, v in roofs.items()},
             "gpu_launches": int(tim["launches"]), "clocks": clocks}
 
     if not a.no_e2e:
@@ -331,7 +349,7 @@ def main():
     h32 = None
     if not a.numeric_only and not a.no_f32:
         h32 = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
-                              warps_per_cta=a.warps, dtype=ick.IC_F32)
+                              warps_per_cta=a.warps, dtype=ick.IC_F32, solve_mode=a.solve_mode)
         ick.ic_set_timing(h32, True)
         x32 = torch.empty_like(x)
 

@@ -70,10 +70,14 @@ typedef struct {
     int threads;       /* [0 = all] host threads for the symbolic phase                  */
     int host_only;     /* [0] 1: ic_symbolic builds the plan in host memory only (no GPU
                           needed); such a handle serves the ic_get_* and ic_stats calls   */
-    int solve_ctas_per_sm; /* [3] CTAs of 8 warps per SM for the triangular-solve
-                              kernels (fewer CTAs poll less; capped by occupancy)   */
-    int solve_lanes;   /* [32] lanes per row in the ic_apply / pcg_solve solves: 4|8|16|32 */
-    int reserved[3];
+    int solve_ctas_per_sm; /* [2 block-DAG, 3 row-level] CTAs per SM for the triangular-
+                              solve kernels (capped by occupancy)                    */
+    int solve_lanes;   /* [8 block-DAG, 32 row-level] lanes per row in the ic_apply /
+                          pcg_solve solves: 4|8|16|32                                 */
+    int solve_mode;    /* [0] triangular solves of ic_apply / pcg_solve: 0 block-DAG (block
+                        * rows as tasks, one CTA per block row's local chain), 1 row-level
+                        * (every row a unit, claimed in dependence-level order)           */
+    int reserved[2];
 } ic_opts;
 
 typedef struct {
@@ -221,6 +225,36 @@ int ic_get_upper(const ic_handle* h, int64_t* urp, int32_t* ucol, int64_t* cptr,
  * from ic_stats.  Errors: IC_ERR_ARG. */
 int ic_get_blocks(const ic_handle* h, int64_t* ranges, int64_t* bptr, int32_t* bcol);
 
+/* The block-DAG triangular solves of ic_apply (solve_mode 0), for inspection and
+ * tests.  A block row (range) k is solved by task L(k) (one CTA, rows in the range's
+ * local dependence-level order) after tasks E(k, c), which sum the entries that
+ * reach outside the range, each for a chunk of its rows.  backward = 0: L y = r;
+ * 1: L^T z = y.  Every pointer may be NULL (that output is skipped).
+ *   ntasks      receives the number of tasks.
+ *   tasks       4 per task in claim order: type (0 = E, 1 = L), range, first row,
+ *               end row.
+ *   counters    2 * nranges: per range, the ranges it waits for, then its E tasks.
+ *   succ_ptr, succ  nranges + 1 offsets and the ranges each L(k) releases (use
+ *               ic_stats' nblocks - nranges as the size bound of succ).
+ *   split       n: forward, the column-list index (into ic_get_upper's cp) where
+ *               the entries inside the row's range begin; backward, the number of
+ *               entries after the diagonal of the row that lie inside its range.
+ *   order_ptr, order  nranges + 1 offsets and the rows of each range in claim order,
+ *               every level padded with -1 to a multiple of 8 (size order_ptr[nranges]).
+ *   need        order_ptr[nranges]: per order position, the number of the range's rows
+ *               in lower levels; the row there runs once that many rows are complete.
+ * Errors: IC_ERR_ARG. */
+int ic_get_solve_tasks(const ic_handle* h, int backward, int64_t* ntasks, int32_t* tasks, int32_t* counters,
+                       int32_t* succ_ptr, int32_t* succ, int32_t* split, int32_t* order_ptr, int32_t* order,
+                       int32_t* need);
+
+/* The internal entries of each row as the L tasks apply them (same direction
+ * convention; any pointer may be NULL).  ptr (n + 1): row i's entries are
+ * [ptr[i], ptr[i+1]); j (ptr[n]): the source row minus the range's first row; pos
+ * (ptr[n]): the position of the value in ic_get_upper's row-major storage.
+ * Errors: IC_ERR_ARG. */
+int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t* j, int32_t* pos);
+
 /* Kernel timing of the handle's calls, from CUDA events recorded on the launching
  * stream while timing is on (ic_set_timing(h, 1); it adds no synchronisation beyond
  * what the calls already do).  launches counts the library's own kernel launches
@@ -231,6 +265,8 @@ typedef struct {
     double apply_ms;       /* triangular-solve kernels, summed since the last reset        */
     int64_t apply_calls;   /* ic_apply calls (direct or inside pcg_solve) since the reset  */
     int64_t launches;      /* kernels launched by the library since the reset              */
+    double fwd_ms;         /* forward-solve kernel alone, summed since the last reset      */
+    double bwd_ms;         /* backward-solve kernel alone, summed since the last reset     */
 } ic_timing_t;
 int ic_set_timing(ic_handle* h, int on);
 int ic_reset_timing(ic_handle* h);
@@ -284,7 +320,8 @@ int ic_numeric_status(ic_handle* h, int64_t* breakdown_row);
  * one matrix; arguments as ic_symbolic_batch), it times ic_numeric (median of reps)
  * over block_rows in {1024, 2048, 4096, 8192}, then warps_per_cta in {8, 16}, then
  * rows_per_item in {16, 32, 64} (coordinate search, each best kept), and ic_apply over
- * solve_lanes in {16, 32} x solve_ctas_per_sm in {2, 3, 4} on the chosen plan.
+ * solve_lanes in {8, 16, 32} (8 only for the block-DAG solves) x solve_ctas_per_sm in
+ * {2, 3, 4, 6} (within occupancy) on the chosen plan.
  * values: device, the (concatenated) values.  base: other options (NULL: defaults).
  * best: receives the chosen options; times (host, 2 doubles or NULL): numeric ms and
  * apply ms of the choice.  The stream is synchronised.
@@ -300,6 +337,13 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
  * Errors: IC_ERR_ARG, IC_ERR_STATE (host-only handle or tracing off), IC_ERR_CUDA. */
 int ic_set_trace(ic_handle* h, int on);
 int ic_get_trace(const ic_handle* h, uint64_t* out);
+
+/* Task trace of the block-DAG solves (solve_mode 0), recorded while ic_set_trace is
+ * on: per task of ic_get_solve_tasks' claim order, 4 uint64 words: %globaltimer (ns)
+ * at the claim, when its wait ended, and when it finished; task index | SM id << 32.
+ * ic_get_solve_trace copies ntasks * 4 words of the last ic_apply's forward
+ * (backward = 0) or backward (1) solve.  Errors: IC_ERR_ARG, IC_ERR_STATE, IC_ERR_CUDA. */
+int ic_get_solve_trace(const ic_handle* h, int backward, uint64_t* out);
 
 void ic_destroy(ic_handle* h);
 

@@ -18,6 +18,9 @@ from .ick import (  # noqa: F401
     ic_get_task_targets,
     ic_get_upper,
     ic_get_blocks,
+    ic_get_solve_tasks,
+    ic_get_solve_trace,
+    ic_get_solve_entries,
     ic_set_timing,
     ic_reset_timing,
     ic_get_timing,

@@ -69,10 +69,11 @@ struct ic_handle {
     PcgScalars* sc = nullptr;
     // timing (ic_set_timing)
     bool timing = false;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    bool apply_pending = false;  // ev[3]..ev[4] bracket an apply not yet added to tm
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool apply_pending = false;  // ev[3] (forward) ev[5] (backward) ev[4] (end) of an apply not yet in tm
     ic_timing_t tm{};
     unsigned long long* trace_buf = nullptr;  // ic_set_trace
+    unsigned long long* solve_trace_buf = nullptr;
     // systems of a batch (one system for ic_symbolic): row offsets, per-row system id,
     // per-system PCG scalars
     std::vector<int64_t> row_off;
@@ -130,8 +131,8 @@ ic_opts normalise(const ic_opts* o) {
     if (r.warps_per_cta == 0) r.warps_per_cta = 16;
     if (r.rows_per_item == 0) r.rows_per_item = 32;
     if (r.timeout_s == 0.0) r.timeout_s = 10.0;
-    if (r.solve_lanes == 0) r.solve_lanes = 32;
-    if (r.solve_ctas_per_sm == 0) r.solve_ctas_per_sm = 3;
+    if (r.solve_lanes == 0) r.solve_lanes = r.solve_mode == 0 ? 8 : 32;
+    if (r.solve_ctas_per_sm == 0) r.solve_ctas_per_sm = r.solve_mode == 0 ? 2 : 3;
     return r;
 }
 
@@ -235,6 +236,57 @@ int upload_plan(ic_handle* h) {
         if ((st = h->upload(&S.fwd_order, P.fwd_order))) return st;
         if ((st = h->upload(&S.bwd_order, P.bwd_order))) return st;
     }
+    S.solve_mode = h->opts.solve_mode;
+    S.nranges = int(P.ranges.size()) - 1;
+    S.max_range_rows = P.max_range_rows;
+    S.nftask = int(P.ftask.size());
+    S.nbtask = int(P.btask.size());
+    S.noff = int(P.nnz_u - P.n);
+    if ((st = h->upload(&S.sf_split, P.sf_split))) return st;
+    if ((st = h->upload(&S.sb_nint, P.sb_nint))) return st;
+    if ((st = h->upload(&S.lf_ptr, P.lf_ptr))) return st;
+    if ((st = h->upload(&S.lf_ord, P.lf_ord))) return st;
+    if ((st = h->upload(&S.lb_ptr, P.lb_ptr))) return st;
+    if ((st = h->upload(&S.lb_ord, P.lb_ord))) return st;
+    if ((st = h->upload(&S.lf_need, P.lf_need))) return st;
+    if ((st = h->upload(&S.lb_need, P.lb_need))) return st;
+    if ((st = h->upload(&S.xf_ptr, P.xf.ptr))) return st;
+    if ((st = h->upload(&S.xf_j, P.xf.j))) return st;
+    if ((st = h->upload(&S.xf_pos, P.xf.pos))) return st;
+    if ((st = h->upload(&S.xb_ptr, P.xb.ptr))) return st;
+    if ((st = h->upload(&S.xb_j, P.xb.j))) return st;
+    if ((st = h->upload(&S.xb_pos, P.xb.pos))) return st;
+    S.nxf = int(P.xf.j.size());
+    S.nxb = int(P.xb.j.size());
+    S.uvt = S.xf_val = S.xb_val = nullptr;
+    if (S.solve_mode == 0) {
+        const size_t cnt[3] = {size_t(P.nnz_u - P.n) + 4, P.xf.j.size() + 4, P.xb.j.size() + 4};
+        void** dst[3] = {&S.uvt, &S.xf_val, &S.xb_val};
+        for (int q = 0; q < 3; ++q) {
+            if (f32) {
+                float* t = nullptr;
+                if ((st = h->alloc(&t, cnt[q]))) return st;
+                *dst[q] = t;
+            } else {
+                double* t = nullptr;
+                if ((st = h->alloc(&t, cnt[q]))) return st;
+                *dst[q] = t;
+            }
+        }
+    }
+    if ((st = h->upload(&S.ftask, P.ftask))) return st;
+    if ((st = h->upload(&S.btask, P.btask))) return st;
+    if ((st = h->upload(&S.fsucc_ptr, P.fsucc_ptr))) return st;
+    if ((st = h->upload(&S.fsucc, P.fsucc))) return st;
+    if ((st = h->upload(&S.bsucc_ptr, P.bsucc_ptr))) return st;
+    if ((st = h->upload(&S.bsucc, P.bsucc))) return st;
+    if ((st = h->upload(&S.dag_cnt0, P.dag_cnt0))) return st;
+    if ((st = h->alloc(&S.dag_cnt, P.dag_cnt0.size()))) return st;
+    {
+        double* w = nullptr;
+        if ((st = h->alloc(&w, size_t(P.n)))) return st;
+        S.dag_w = w;
+    }
     if ((st = h->alloc(&S.y, 2 * size_t(P.n)))) return st;  // forward and backward results
     if ((st = h->alloc(&S.flag, size_t(P.n)))) return st;
     CK(cudaMemset(S.flag, 0, size_t(P.n) * sizeof(int)));
@@ -256,9 +308,13 @@ int upload_plan(ic_handle* h) {
     CK(numeric_blocks_per_sm(h->opts.warps_per_cta, h->opts.exact != 0, h->opts.dtype, &bpsm));
     if (bpsm < 1) return fail(IC_ERR_CUDA, "numeric kernel cannot be resident");
     h->grid_numeric = sms * bpsm;
-    CK(apply_blocks_per_sm(&bpsm));
+    if (S.solve_mode == 0)
+        CK(dag_blocks_per_sm(S.lanes_per_row, S.dtype, P.max_range_rows, &bpsm));
+    else
+        CK(apply_blocks_per_sm(&bpsm));
+    if (bpsm < 1) return fail(IC_ERR_CUDA, "solve kernels cannot be resident");
     if (h->opts.solve_ctas_per_sm > 0 && h->opts.solve_ctas_per_sm < bpsm) bpsm = h->opts.solve_ctas_per_sm;
-    h->grid_apply = sms * (bpsm < 1 ? 1 : bpsm);
+    h->grid_apply = sms * bpsm;
     CK(cudaDeviceSynchronize());
     return IC_OK;
 }
@@ -267,9 +323,12 @@ int upload_plan(ic_handle* h) {
 int fold_apply_time(ic_handle* h) {
     if (!h->apply_pending) return IC_OK;
     CK(cudaEventSynchronize(h->ev[4]));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev[3], h->ev[4]));
-    h->tm.apply_ms += ms;
+    float f = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&f, h->ev[3], h->ev[5]));
+    CK(cudaEventElapsedTime(&b, h->ev[5], h->ev[4]));
+    h->tm.fwd_ms += f;
+    h->tm.bwd_ms += b;
+    h->tm.apply_ms += f + b;
     h->apply_pending = false;
     return IC_OK;
 }
@@ -361,9 +420,9 @@ static int symbolic_impl(const ic_csr_pattern* A, int k, const int32_t* perm, co
         }
         if (h->opts.rows_per_item < 1 || h->opts.timeout_s < 0 ||
             (h->opts.solve_lanes != 4 && h->opts.solve_lanes != 8 && h->opts.solve_lanes != 16 &&
-             h->opts.solve_lanes != 32)) {
+             h->opts.solve_lanes != 32) || (h->opts.solve_mode != 0 && h->opts.solve_mode != 1)) {
             delete h;
-            return fail(IC_ERR_ARG, "rows_per_item / timeout_s out of range");
+            return fail(IC_ERR_ARG, "rows_per_item / timeout_s / solve_lanes / solve_mode out of range");
         }
         std::string err;
         int st = build_plan(A, k, perm, ranges, nranges, h->opts.block_rows, h->opts.rows_per_item,
@@ -478,7 +537,7 @@ static int numeric_enqueue(ic_handle* h, const void* values, cudaStream_t s, boo
     }
     if (timing) CK(cudaEventRecord(h->ev[2], s));
     CK(launch_solve_prepare(h->sp, s));
-    ++h->tm.launches;
+    h->tm.launches += 1 + dag_prepare_launches(h->sp);
     CK(cudaMemcpyAsync(h->h_counters, h->dp.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->h_counters + 4, h->dp.diag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->h_brk, h->dp.brk_row, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -550,10 +609,9 @@ int ic_apply(ic_handle* h, const void* r, void* z, void* stream) {
     if (h->timing) {
         int st = fold_apply_time(h);
         if (st) return st;
-        CK(cudaEventRecord(h->ev[3], s));
     }
     CK(launch_apply(h->sp, static_cast<const double*>(r), static_cast<double*>(z), epoch, tmo,
-                    h->grid_apply, s));
+                    h->grid_apply, s, h->timing ? h->ev[3] : nullptr, h->timing ? h->ev[5] : nullptr));
     h->tm.launches += 2;
     ++h->tm.apply_calls;
     if (h->timing) {
@@ -905,6 +963,50 @@ int ic_get_blocks(const ic_handle* h, int64_t* ranges, int64_t* bptr, int32_t* b
     return IC_OK;
 }
 
+int ic_get_solve_tasks(const ic_handle* h, int backward, int64_t* ntasks, int32_t* tasks, int32_t* counters,
+                       int32_t* succ_ptr, int32_t* succ, int32_t* split, int32_t* order_ptr, int32_t* order,
+                       int32_t* need) {
+    if (!h || (backward != 0 && backward != 1)) return fail(IC_ERR_ARG, "NULL handle or bad direction");
+    const HostPlan& P = h->hp;
+    const std::vector<int4>& T = backward ? P.btask : P.ftask;
+    const size_t nb = P.ranges.size() - 1;
+    if (ntasks) *ntasks = int64_t(T.size());
+    if (tasks)
+        for (size_t t = 0; t < T.size(); ++t) {
+            tasks[4 * t] = T[t].x;
+            tasks[4 * t + 1] = T[t].y;
+            tasks[4 * t + 2] = T[t].z;
+            tasks[4 * t + 3] = T[t].w;
+        }
+    if (counters && nb) std::memcpy(counters, P.dag_cnt0.data() + (backward ? 2 * nb : 0), 2 * nb * sizeof(int32_t));
+    const std::vector<int32_t>& sp = backward ? P.bsucc_ptr : P.fsucc_ptr;
+    const std::vector<int32_t>& sc = backward ? P.bsucc : P.fsucc;
+    if (succ_ptr) std::memcpy(succ_ptr, sp.data(), sp.size() * sizeof(int32_t));
+    if (succ && !sc.empty()) std::memcpy(succ, sc.data(), sc.size() * sizeof(int32_t));
+    const std::vector<int32_t>& spl = backward ? P.sb_nint : P.sf_split;
+    if (split && !spl.empty()) std::memcpy(split, spl.data(), spl.size() * sizeof(int32_t));
+    const std::vector<int32_t>& op = backward ? P.lb_ptr : P.lf_ptr;
+    const std::vector<int32_t>& od = backward ? P.lb_ord : P.lf_ord;
+    if (order_ptr) std::memcpy(order_ptr, op.data(), op.size() * sizeof(int32_t));
+    if (order && !od.empty()) std::memcpy(order, od.data(), od.size() * sizeof(int32_t));
+    const std::vector<int32_t>& nd = backward ? P.lb_need : P.lf_need;
+    if (need && !nd.empty()) std::memcpy(need, nd.data(), nd.size() * sizeof(int32_t));
+    return IC_OK;
+}
+
+int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t* j, int32_t* pos) {
+    if (!h || (backward != 0 && backward != 1)) return fail(IC_ERR_ARG, "NULL handle or bad direction");
+    const HostPlan& P = h->hp;
+    const SolveLayout& L = backward ? P.xb : P.xf;
+    auto put = [](int32_t* out, const std::vector<int32_t>& v) {
+        if (out && !v.empty()) std::memcpy(out, v.data(), v.size() * sizeof(int32_t));
+    };
+    put(ptr, L.ptr);
+    put(j, L.j);
+    put(pos, L.pos);
+    return IC_OK;
+}
+
 int ic_set_timing(ic_handle* h, int on) {
     if (!h) return fail(IC_ERR_ARG, "NULL handle");
     if (h->device < 0) return fail(IC_ERR_STATE, "host-only handle");
@@ -947,8 +1049,24 @@ int ic_set_trace(ic_handle* h, int on) {
         if (st) return st;
         CK(cudaMemset(t, 0, 4 * size_t(h->hp.total_items > 0 ? h->hp.total_items : 1) * 8));
         h->trace_buf = t;
+        const size_t nt = h->hp.ftask.size() + h->hp.btask.size();
+        st = h->alloc(&t, 4 * (nt > 0 ? nt : 1));
+        if (st) return st;
+        CK(cudaMemset(t, 0, 4 * (nt > 0 ? nt : 1) * 8));
+        h->solve_trace_buf = t;
     }
     h->dp.trace = on ? h->trace_buf : nullptr;
+    h->sp.trace = on ? h->solve_trace_buf : nullptr;
+    return IC_OK;
+}
+
+int ic_get_solve_trace(const ic_handle* h, int backward, uint64_t* out) {
+    if (!h || !out || (backward != 0 && backward != 1)) return fail(IC_ERR_ARG, "bad argument");
+    if (!h->solve_trace_buf) return fail(IC_ERR_STATE, "tracing was never enabled");
+    DeviceGuard g(h->device);
+    const size_t off = backward ? h->hp.ftask.size() : 0;
+    const size_t cnt = backward ? h->hp.btask.size() : h->hp.ftask.size();
+    CK(cudaMemcpy(out, h->solve_trace_buf + 4 * off, 4 * cnt * 8, cudaMemcpyDeviceToHost));
     return IC_OK;
 }
 
@@ -1040,7 +1158,7 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
         int sms = 0, dev = 0, bpsm = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        CK(apply_blocks_per_sm(&bpsm));
+        const bool dag = h->sp.solve_mode == 0;
         double* r = nullptr;
         double* z = nullptr;
         CK(cudaMalloc(&r, 2 * size_t(h->hp.n > 0 ? h->hp.n : 1) * sizeof(double)));
@@ -1051,10 +1169,14 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        for (int lanes : {16, 32})
-            for (int cps : {2, 3, 4}) {
+        for (int lanes : {8, 16, 32}) {
+            if (!dag && lanes == 8) continue;
+            if (dag) CK(dag_blocks_per_sm(lanes, h->sp.dtype, h->sp.max_range_rows, &bpsm));
+            else CK(apply_blocks_per_sm(&bpsm));
+            for (int cps : {2, 3, 4, 6}) {
+                if (cps > bpsm) continue;
                 h->sp.lanes_per_row = lanes;
-                h->grid_apply = sms * std::min(cps, bpsm < 1 ? 1 : bpsm);
+                h->grid_apply = sms * cps;
                 std::vector<float> t;
                 for (int q = 0; q <= reps; ++q) {
                     CK(cudaEventRecord(e0, s));
@@ -1074,6 +1196,7 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
                     cur.solve_ctas_per_sm = cps;
                 }
             }
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaFree(r);

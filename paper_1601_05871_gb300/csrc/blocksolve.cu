@@ -1,0 +1,447 @@
+// Block-DAG triangular solves of ic_apply: L y = r (forward) and L^T z = y (backward)
+// with L = U^T the incomplete factor.
+//
+// The 2D block structure of Section 3.2 organises the solve like the factorization's
+// task DAG (Section 3.3): a range of rows (a block row) is one unit.  Task E(k, c)
+// sums, for a chunk of range k's rows, the entries whose other index lies in another
+// range (all finished when E starts); task L(k) is one CTA that solves the range's
+// rows with the remaining, internal entries, the rows taken in local dependence-level
+// order and the range's results kept in shared memory, so a dependence inside a range
+// costs a shared-memory round trip rather than an L2 one.  Nested-dissection leaves
+// are independent in the forward solve and run concurrently; separators follow.
+//
+// Scheduling: one persistent grid claims tasks in a fixed topological order (atomic
+// counter), waits (bounded) until the task's range counter reaches zero, runs it and
+// releases its successors.  Every task a CTA waits for was claimed earlier by a
+// resident CTA, so the claims cannot deadlock.  All waits give up at the deadline or
+// when another CTA has set the abort word, and the host reports IC_ERR_TIMEOUT.
+#include <cstdint>
+
+#include "ick_internal.h"
+
+namespace ick {
+namespace {
+
+constexpr int kDagThreads = 512;
+
+__device__ __forceinline__ unsigned long long gclock() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool aborted(const int* abort_word) {
+    return *reinterpret_cast<const volatile int*>(abort_word) != 0;
+}
+
+// Thread 0: wait until *c is zero; false on abort or timeout.
+__device__ bool await_zero(const int* c, int* abort_word, unsigned long long deadline) {
+    const volatile int* p = c;
+    unsigned spins = 0;
+    while (*p != 0) {
+        if ((++spins & 63) == 0 && (aborted(abort_word) || gclock() > deadline)) {
+            atomicExch(abort_word, 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+// Lane 0: wait until the range's count of completed rows reaches need (one shared
+// word, read by one lane per waiting warp); false on abort or timeout.
+__device__ bool await_count(const int* done, int need, int* abort_word, unsigned long long deadline) {
+    const volatile int* p = done;
+    unsigned spins = 0;
+    int d;
+    while ((d = *p) < need) {
+        if ((++spins & 255) == 0 && (aborted(abort_word) || gclock() > deadline)) {
+            atomicExch(abort_word, 1);
+            return false;
+        }
+        (void)d;
+    }
+    __threadfence_block();
+    return true;
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T sum_group(T v) {
+    const int lane = threadIdx.x & 31;
+    const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+
+// A row's first 64 internal entries are loaded into registers (64 / G per lane)
+// before its wait, so the loads overlap the wait and leave the dependence chain.
+template <int G>
+struct Held {
+    static constexpr int M = 64 / G;
+};
+
+// Marks the warp's rows complete: every lane's stores precede the count update.
+__device__ __forceinline__ void complete_rows(int* done, unsigned rows_mask) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0 && rows_mask) {
+        __threadfence_block();
+        atomicAdd(done, __popc(rows_mask));
+    }
+}
+
+// ------------------------------------------------------------------ forward tasks
+
+// E(k, c): w_i = sum of U_pi y_p over the column-list entries of row i with p outside
+// the row's range (a prefix of the list, pivots ascending), for rows [lo, hi).  The
+// values come from the column-ordered copy, contiguous with the column lists.
+template <int G, typename T>
+__device__ void fwd_external(const SolvePlan& S, const T* __restrict__ uvt, const T* y, T* w, int lo, int hi) {
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane / G, sl = lane % G;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = lo + warp * R; base < hi; base += nw * R) {
+        const int i = base + sub;
+        T acc = T(0);
+        int a = 0, b = 0;
+        if (i < hi) {
+            a = __ldg(S.cptr + i);
+            b = __ldg(S.sf_split + i);
+            for (int q = a + sl; q < b; q += G) acc = fma(__ldg(uvt + q), ldcg(y + __ldg(&S.csc[q].x)), acc);
+        }
+        acc = sum_group<G>(acc);
+        if (sl == 0 && a < b) w[i] = acc;
+    }
+}
+
+// L(k) of either direction: the range's rows in its padded local order, G lanes per
+// row and 32/G rows per warp (one level per claim).  A row runs once every row of the
+// lower levels is complete (done >= need); its internal operands come from shared
+// memory and its other operands are loaded before the wait.
+//   forward:  y_i = (r_perm(i) - w_i - sum) / U_ii, stored to y
+//   backward: z_i = (y_i - w_i - sum) / U_ii, stored to zv and to z at perm(i)
+template <int G, typename T, bool BW>
+__device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const T* __restrict__ rd_all,
+                            const double* __restrict__ r, const T* y, T* out, double* __restrict__ z, const T* w,
+                            int k, int s, T* sh, int* claim, int* done, unsigned long long deadline) {
+    constexpr int R = 32 / G, M = Held<G>::M;
+    const int lane = threadIdx.x & 31, sl = lane % G;
+    const int* ord = BW ? S.lb_ord : S.lf_ord;
+    const int* need_a = BW ? S.lb_need : S.lf_need;
+    const int* xptr = BW ? S.xb_ptr : S.xf_ptr;
+    const int* xj = BW ? S.xb_j : S.xf_j;
+    const int base = __ldg((BW ? S.lb_ptr : S.lf_ptr) + k);
+    const int len = __ldg((BW ? S.lb_ptr : S.lf_ptr) + k + 1) - base;
+    for (;;) {
+        int t0 = 0;
+        if (lane == 0) t0 = atomicAdd(claim, R);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        if (t0 >= len) break;
+        const int i = __ldg(ord + base + t0 + lane / G);
+        const int need = __ldg(need_a + base + t0);
+        T t = T(0), rd = T(0);
+        int a = 0, c = 0, dst = 0;
+        if (i >= 0) {
+            a = __ldg(xptr + i);
+            c = __ldg(xptr + i + 1);
+            if (sl == 0) {
+                rd = __ldg(rd_all + i);
+                bool ext;
+                if (BW) {
+                    t = ldcg(y + i);
+                    dst = __ldg(S.perm + i);
+                    ext = __ldg(S.sb_nint + i) < int(__ldg(S.urp + i + 1) - __ldg(S.urp + i)) - 1;
+                } else {
+                    t = T(__ldg(r + __ldg(S.perm + i)));
+                    ext = __ldg(S.cptr + i) < __ldg(S.sf_split + i);
+                }
+                if (ext) t -= ldcg(w + i);
+            }
+        }
+        int j[M];
+        T u[M];
+        int cnt = 0;
+#pragma unroll
+        for (int x = 0; x < M; ++x) {
+            const int q = a + sl + x * G;
+            j[x] = 0;
+            u[x] = T(0);
+            if (q < c) {
+                j[x] = __ldg(xj + q);
+                u[x] = __ldg(xv + q);
+                cnt = x + 1;
+            }
+        }
+        const unsigned rows = __ballot_sync(0xffffffffu, sl == 0 && i >= 0);
+        const int most = __reduce_max_sync(0xffffffffu, cnt);
+        int ok = 1;
+        if (lane == 0) ok = await_count(done, need, S.counter + 2, deadline);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        T acc = T(0);
+#pragma unroll
+        for (int x = 0; x < M; ++x) {
+            if (x >= most) break;
+            if (x < cnt) acc = fma(u[x], sh[j[x]], acc);
+        }
+        for (int q = a + sl + M * G; q < c; q += G) acc = fma(__ldg(xv + q), sh[__ldg(xj + q)], acc);
+        acc = sum_group<G>(acc);
+        T v = T(0);
+        if (sl == 0 && i >= 0) {
+            v = (t - acc) * rd;
+            sh[i - s] = v;
+        }
+        // the count is raised before the global stores, so its fence waits only for
+        // the shared-memory results; later tasks read the global copies after the
+        // task's closing fence
+        complete_rows(done, rows);
+        if (sl == 0 && i >= 0) {
+            out[i] = v;
+            if (BW) z[dst] = double(v);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- backward tasks
+
+// E'(k, c): w_i = sum of U_im z_m over the entries of row i with m beyond the row's
+// range (a suffix of the row, columns ascending), for rows [lo, hi).
+template <int G, typename T>
+__device__ void bwd_external(const SolvePlan& S, const T* __restrict__ uv, const T* zv, T* w, int lo, int hi) {
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane / G, sl = lane % G;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = lo + warp * R; base < hi; base += nw * R) {
+        const int i = base + sub;
+        T acc = T(0);
+        long long a = 0, b = 0;
+        if (i < hi) {
+            a = __ldg(S.urp + i) + 1 + __ldg(S.sb_nint + i);
+            b = __ldg(S.urp + i + 1);
+            for (long long q = a + sl; q < b; q += G) acc = fma(__ldg(uv + q), ldcg(zv + __ldg(S.ucol + q)), acc);
+        }
+        acc = sum_group<G>(acc);
+        if (sl == 0 && a < b) w[i] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ the two grids
+
+// Claims the next task of `tasks`; thread 0 waits for its range counter.  Returns the
+// task index, or -1 when the list is exhausted or the solve was aborted.
+__device__ __forceinline__ unsigned smid() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+__device__ int claim_task(int* claim_ctr, const int4* tasks, int ntasks, const int* pend, const int* epend,
+                          int* abort_word, unsigned long long deadline, int* s_task, int* s_claim,
+                          int* s_done, unsigned long long* trace) {
+    if (threadIdx.x == 0) {
+        int t = -1;
+        if (!aborted(abort_word)) {
+            t = atomicAdd(claim_ctr, 1);
+            if (t >= ntasks) {
+                t = -1;
+            } else {
+                const unsigned long long t0 = gclock();
+                const int4 tk = tasks[t];
+                if (!await_zero(tk.x == 0 ? pend + tk.y : epend + tk.y, abort_word, deadline)) t = -1;
+                if (trace && t >= 0) {
+                    trace[4 * t] = t0;
+                    trace[4 * t + 1] = gclock();
+                    trace[4 * t + 3] = (unsigned long long)t | ((unsigned long long)smid() << 32);
+                }
+            }
+        }
+        *s_task = t;
+        *s_claim = 0;
+        *s_done = 0;
+    }
+    __syncthreads();
+    return *s_task;
+}
+
+template <int G, typename T>
+__global__ void __launch_bounds__(kDagThreads)
+forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all, const double* __restrict__ r,
+            T* y, T* w, unsigned long long timeout_ns) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* sh = reinterpret_cast<T*>(smem);
+    __shared__ int s_task, s_claim, s_done;
+    const unsigned long long deadline = gclock() + timeout_ns;
+    int* pend = S.dag_cnt;
+    int* epend = S.dag_cnt + S.nranges;
+    for (;;) {
+        const int t = claim_task(S.counter + 0, S.ftask, S.nftask, pend, epend, S.counter + 2, deadline,
+                                 &s_task, &s_claim, &s_done, S.trace);
+        if (t < 0) break;
+        const int4 tk = S.ftask[t];
+        if (tk.x == 0)
+            fwd_external<G, T>(S, uvt, y, w, tk.z, tk.w);
+        else
+            solve_local<G, T, false>(S, static_cast<const T*>(S.xf_val), rd_all, r, nullptr, y, nullptr, w, tk.y,
+                                     tk.z, sh, &s_claim, &s_done, deadline);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (S.trace) S.trace[4 * t + 2] = gclock();
+            if (tk.x == 0) {
+                atomicSub(epend + tk.y, 1);
+            } else {
+                const int a = __ldg(S.fsucc_ptr + tk.y), b = __ldg(S.fsucc_ptr + tk.y + 1);
+                for (int q = a; q < b; ++q) atomicSub(pend + __ldg(S.fsucc + q), 1);
+            }
+        }
+    }
+}
+
+template <int G, typename T>
+__global__ void __launch_bounds__(kDagThreads)
+backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all, const T* y, T* zv,
+             double* __restrict__ z, T* w, unsigned long long timeout_ns) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* sh = reinterpret_cast<T*>(smem);
+    __shared__ int s_task, s_claim, s_done;
+    const unsigned long long deadline = gclock() + timeout_ns;
+    int* pend = S.dag_cnt + 2 * S.nranges;
+    int* epend = S.dag_cnt + 3 * S.nranges;
+    for (;;) {
+        unsigned long long* tr = S.trace ? S.trace + 4 * size_t(S.nftask) : nullptr;
+        const int t = claim_task(S.counter + 1, S.btask, S.nbtask, pend, epend, S.counter + 2, deadline,
+                                 &s_task, &s_claim, &s_done, tr);
+        if (t < 0) break;
+        const int4 tk = S.btask[t];
+        if (tk.x == 0)
+            bwd_external<G, T>(S, uv, zv, w, tk.z, tk.w);
+        else
+            solve_local<G, T, true>(S, static_cast<const T*>(S.xb_val), rd_all, nullptr, y, zv, z, w, tk.y, tk.z,
+                                    sh, &s_claim, &s_done, deadline);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (tr) tr[4 * t + 2] = gclock();
+            if (tk.x == 0) {
+                atomicSub(epend + tk.y, 1);
+            } else {
+                const int a = __ldg(S.bsucc_ptr + tk.y), b = __ldg(S.bsucc_ptr + tk.y + 1);
+                for (int q = a; q < b; ++q) atomicSub(pend + __ldg(S.bsucc + q), 1);
+            }
+        }
+    }
+}
+
+// The shared-memory cap is a per-function setting shared by all handles, so it is
+// always the largest range (kMaxBlockRows rows); the occupancy uses the actual size.
+template <int G, typename T>
+cudaError_t set_smem_and_occupancy(size_t smem, int* blocks) {
+    const int cap = int(kMaxBlockRows * sizeof(T));
+    cudaError_t e = cudaFuncSetAttribute(forward_dag<G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(backward_dag<G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    if (e != cudaSuccess) return e;
+    int a = 0, b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, forward_dag<G, T>, kDagThreads, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, backward_dag<G, T>, kDagThreads, smem);
+    *blocks = a < b ? a : b;
+    return e;
+}
+
+template <int G, typename T>
+void launch_dag(const SolvePlan& S, const T* uv, const T* rd, const double* r, double* z, T* y, T* w, int grid,
+                size_t smem, unsigned long long timeout_ns, cudaStream_t s, cudaEvent_t t1) {
+    forward_dag<G, T><<<grid, kDagThreads, smem, s>>>(S, static_cast<const T*>(S.uvt), rd, r, y, w, timeout_ns);
+    if (t1) cudaEventRecord(t1, s);
+    backward_dag<G, T><<<grid, kDagThreads, smem, s>>>(S, uv, rd, y, y + S.n, z, w, timeout_ns);
+}
+
+template <typename T>
+cudaError_t launch_dag_t(const SolvePlan& S, const T* uv, const T* rd, const double* r, double* z, T* y, T* w,
+                         int grid, unsigned long long timeout_ns, cudaStream_t s, cudaEvent_t t1) {
+    const size_t smem = size_t(S.max_range_rows) * sizeof(T);
+    switch (S.lanes_per_row) {
+        case 4: launch_dag<4, T>(S, uv, rd, r, z, y, w, grid, smem, timeout_ns, s, t1); break;
+        case 8: launch_dag<8, T>(S, uv, rd, r, z, y, w, grid, smem, timeout_ns, s, t1); break;
+        case 16: launch_dag<16, T>(S, uv, rd, r, z, y, w, grid, smem, timeout_ns, s, t1); break;
+        default: launch_dag<32, T>(S, uv, rd, r, z, y, w, grid, smem, timeout_ns, s, t1); break;
+    }
+    return cudaGetLastError();
+}
+
+// uvt[q] = value of the U entry the column-list entry q refers to.
+template <typename T>
+__global__ void transpose_values(int noff, const int2* __restrict__ csc, const T* __restrict__ uv,
+                                 T* __restrict__ uvt) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < noff; q += gridDim.x * blockDim.x)
+        uvt[q] = uv[__ldg(&csc[q].y)];
+}
+
+// out[q] = uv[pos[q]].
+template <typename T>
+__global__ void gather_values(int cnt, const int* __restrict__ pos, const T* __restrict__ uv, T* __restrict__ out) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) out[q] = uv[__ldg(pos + q)];
+}
+
+template <typename T>
+void launch_gathers(const SolvePlan& S, const T* uv, cudaStream_t s) {
+    auto grid = [](int cnt) { return (cnt + 255) / 256 < 8192 ? (cnt + 255) / 256 : 8192; };
+    if (S.noff > 0) transpose_values<T><<<grid(S.noff), 256, 0, s>>>(S.noff, S.csc, uv, static_cast<T*>(S.uvt));
+    if (S.nxf > 0) gather_values<T><<<grid(S.nxf), 256, 0, s>>>(S.nxf, S.xf_pos, uv, static_cast<T*>(S.xf_val));
+    if (S.nxb > 0) gather_values<T><<<grid(S.nxb), 256, 0, s>>>(S.nxb, S.xb_pos, uv, static_cast<T*>(S.xb_val));
+}
+
+}  // namespace
+
+// Number of kernels launch_dag_prepare launches.
+int dag_prepare_launches(const SolvePlan& S) {
+    return S.solve_mode != 0 ? 0 : (S.noff > 0) + (S.nxf > 0) + (S.nxb > 0);
+}
+
+cudaError_t launch_dag_prepare(const SolvePlan& S, cudaStream_t s) {
+    if (S.solve_mode != 0) return cudaSuccess;
+    if (S.dtype == IC_F32) launch_gathers<float>(S, S.uval32, s);
+    else launch_gathers<double>(S, S.uval, s);
+    return cudaGetLastError();
+}
+
+cudaError_t dag_blocks_per_sm(int lanes, int dtype, int max_range_rows, int* blocks) {
+    const size_t smem = size_t(max_range_rows < 1 ? 1 : max_range_rows) * (dtype == IC_F32 ? 4 : 8);
+    if (dtype == IC_F32) {
+        switch (lanes) {
+            case 4: return set_smem_and_occupancy<4, float>(smem, blocks);
+            case 8: return set_smem_and_occupancy<8, float>(smem, blocks);
+            case 16: return set_smem_and_occupancy<16, float>(smem, blocks);
+            default: return set_smem_and_occupancy<32, float>(smem, blocks);
+        }
+    }
+    switch (lanes) {
+        case 4: return set_smem_and_occupancy<4, double>(smem, blocks);
+        case 8: return set_smem_and_occupancy<8, double>(smem, blocks);
+        case 16: return set_smem_and_occupancy<16, double>(smem, blocks);
+        default: return set_smem_and_occupancy<32, double>(smem, blocks);
+    }
+}
+
+cudaError_t launch_apply_dag(const SolvePlan& S, const double* r, double* z, unsigned long long timeout_ns,
+                             int grid, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1) {
+    if (S.n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(S.dag_cnt, S.dag_cnt0, 4 * size_t(S.nranges) * sizeof(int),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(S.counter, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if (t0) cudaEventRecord(t0, s);
+    if (S.dtype == IC_F32)
+        return launch_dag_t<float>(S, S.uval32, S.rdiag32, r, z, reinterpret_cast<float*>(S.y),
+                                   reinterpret_cast<float*>(S.dag_w), grid, timeout_ns, s, t1);
+    return launch_dag_t<double>(S, S.uval, S.rdiag, r, z, S.y, reinterpret_cast<double*>(S.dag_w), grid,
+                                timeout_ns, s, t1);
+}
+
+}  // namespace ick

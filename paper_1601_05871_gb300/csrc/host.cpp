@@ -632,6 +632,7 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
     // write L (values and column indices) and its row pointers
     const double nnz_low = double(P.nnz_a + n) / 2.0;
     P.bytes = nnz_low * (8 + 4) + double(P.nnz_u) * (8 + 4) + double(n + 1) * 8;
+    build_solve_dag(P, nthr);
     return IC_OK;
 }
 

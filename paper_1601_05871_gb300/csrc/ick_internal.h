@@ -19,6 +19,13 @@ constexpr int kMaxBlockRows = 8192;  // per-row completion flags of one block li
 constexpr int kSegCap = 128;         // target-segment entries staged per warp in shared memory
 constexpr int kClaimPad = 8;         // level runs of the padded solve orders are multiples of this
 
+// Internal entries of the rows of a block-DAG solve (host_solve.cpp): per row i the
+// entries [ptr[i], ptr[i+1]); j = source row - range start, pos = position of the
+// value in U's row-major storage.
+struct SolveLayout {
+    std::vector<int32_t> ptr, j, pos;
+};
+
 // Everything the symbolic phase produces, in host memory.
 struct HostPlan {
     int64_t n = 0, nnz_a = 0, nnz_u = 0;
@@ -58,6 +65,19 @@ struct HostPlan {
     std::vector<int32_t> fwd_order, bwd_order;  // claim orders of the triangular solves
     std::vector<int32_t> fwd_pad, bwd_pad;      // the same, each level padded with -1
     int64_t fwd_depth = 0, bwd_depth = 0;        // levels of the row dependence DAGs
+    // block-DAG solves (host_solve.cpp): per row the start of the internal entries
+    // (forward: absolute column-list index; backward: count after the diagonal), per
+    // range the padded local orders, the tasks in claim order (type 0 = E, 1 = L;
+    // range; first row; end row), range successors, and the initial counters
+    // [forward pending ranges | forward pending E tasks | backward ... | backward ...]
+    std::vector<int32_t> sf_split, sb_nint;
+    std::vector<int32_t> lf_ptr, lf_ord, lb_ptr, lb_ord;
+    std::vector<int32_t> lf_need, lb_need;  // per order position: rows of lower levels
+    SolveLayout xf, xb;                     // forward / backward internal entries
+    std::vector<int4> ftask, btask;
+    std::vector<int32_t> fsucc_ptr, fsucc, bsucc_ptr, bsucc;
+    std::vector<int32_t> dag_cnt0;
+    int32_t max_range_rows = 0;
     int64_t total_items = 0;
     int64_t critical_path = 0;
     int64_t max_level = 0;
@@ -134,6 +154,40 @@ struct SolvePlan {
     const float* uval32;   // IC_F32 factor values
     const double* udiag;   // IC_F32 FP64 pivots
     float* rdiag32;        // IC_F32 reciprocal pivots
+    // block-DAG solves (blocksolve.cu); see HostPlan for the meaning of the arrays
+    int solve_mode;        // 0: block-DAG solves, 1: row-level solves in level order
+    int nranges, max_range_rows, nftask, nbtask, noff;
+    const int* sf_split;
+    const int* sb_nint;
+    const int* lf_ptr;
+    const int* lf_ord;
+    const int* lb_ptr;
+    const int* lb_ord;
+    const int* lf_need;
+    const int* lb_need;
+    // internal entries per direction (SolveLayout) and their values (solve type),
+    // gathered from the factor after each numeric phase
+    const int* xf_ptr;
+    const int* xf_j;
+    const int* xf_pos;
+    void* xf_val;
+    const int* xb_ptr;
+    const int* xb_j;
+    const int* xb_pos;
+    void* xb_val;
+    int nxf, nxb;
+    void* uvt;             // factor values in column-list (csc) order, refreshed after each
+                           // numeric phase: the forward solve reads them contiguously
+    const int4* ftask;
+    const int4* btask;
+    const int* fsucc_ptr;
+    const int* fsucc;
+    const int* bsucc_ptr;
+    const int* bsucc;
+    const int* dag_cnt0;   // initial range counters, copied into dag_cnt before each apply
+    int* dag_cnt;
+    void* dag_w;           // external sums of the rows (n values of the solve type)
+    unsigned long long* trace;  // NULL, or 4 words per task: forward tasks, then backward
 };
 
 // Kernel entry points (numeric.cu, solve.cu).
@@ -143,8 +197,16 @@ cudaError_t launch_numeric(const DevPlan& P, int epoch, int warps, bool exact, i
                            unsigned long long timeout_ns, cudaStream_t s);
 cudaError_t numeric_blocks_per_sm(int warps, bool exact, int dtype, int* blocks);
 
+// t0 / t1 (may be NULL): events recorded just before the forward and just before the
+// backward solve kernel.
 cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epoch,
-                         unsigned long long timeout_ns, int grid, cudaStream_t s);
+                         unsigned long long timeout_ns, int grid, cudaStream_t s,
+                         cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
+cudaError_t launch_apply_dag(const SolvePlan& S, const double* r, double* z, unsigned long long timeout_ns,
+                             int grid, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1);
+cudaError_t launch_dag_prepare(const SolvePlan& S, cudaStream_t s);
+int dag_prepare_launches(const SolvePlan& S);
+cudaError_t dag_blocks_per_sm(int lanes, int dtype, int max_range_rows, int* blocks);
 cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, double* y,
                         cudaStream_t s);
 cudaError_t apply_blocks_per_sm(int* blocks);
@@ -190,6 +252,7 @@ cudaError_t batch_p(int n, const int* sys, const double* beta, const int* active
 int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
                int64_t nranges, int block_rows, int rows_per_item, int threads, HostPlan& P,
                std::string& err);
+void build_solve_dag(HostPlan& P, int threads);
 int block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, std::vector<int4>& task,
               std::vector<int64_t>& pred_ptr, std::vector<int32_t>& pred);
 int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep, int32_t* perm,

@@ -268,22 +268,28 @@ __global__ void rdiag_kernel(SolvePlan S) {
 
 template <typename T>
 cudaError_t launch_solves(const SolvePlan& S, const T* uv, const T* rd, const double* r, double* z,
-                          T* y, int grid, unsigned long long timeout_ns, cudaStream_t s) {
+                          T* y, int grid, unsigned long long timeout_ns, cudaStream_t s,
+                          cudaEvent_t t0, cudaEvent_t t1) {
+    if (t0) cudaEventRecord(t0, s);
     switch (S.lanes_per_row) {
         case 4:
             forward_solve_v<4, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, r, y, timeout_ns);
+            if (t1) cudaEventRecord(t1, s);
             backward_solve_v<4, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, y, y + S.n, z, timeout_ns);
             break;
         case 8:
             forward_solve_v<8, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, r, y, timeout_ns);
+            if (t1) cudaEventRecord(t1, s);
             backward_solve_v<8, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, y, y + S.n, z, timeout_ns);
             break;
         case 16:
             forward_solve_v<16, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, r, y, timeout_ns);
+            if (t1) cudaEventRecord(t1, s);
             backward_solve_v<16, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, y, y + S.n, z, timeout_ns);
             break;
         default:
             forward_solve_v<32, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, r, y, timeout_ns);
+            if (t1) cudaEventRecord(t1, s);
             backward_solve_v<32, T><<<grid, kApplyThreads, 0, s>>>(S, uv, rd, y, y + S.n, z, timeout_ns);
             break;
     }
@@ -404,9 +410,11 @@ cudaError_t apply_blocks_per_sm(int* blocks) {
 }
 
 cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epoch,
-                         unsigned long long timeout_ns, int grid, cudaStream_t s) {
+                         unsigned long long timeout_ns, int grid, cudaStream_t s, cudaEvent_t t0,
+                         cudaEvent_t t1) {
     if (S.n == 0) return cudaSuccess;
     (void)epoch;
+    if (S.solve_mode == 0) return launch_apply_dag(S, r, z, timeout_ns, grid, s, t0, t1);
     // S.y holds 2n doubles: the forward then the backward result (2n floats for IC_F32)
     const size_t bytes = 2 * size_t(S.n) * (S.dtype == IC_F32 ? sizeof(float) : sizeof(double));
     cudaError_t e = cudaMemsetAsync(S.y, 0xff, bytes, s);
@@ -415,15 +423,17 @@ cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epo
     if (e != cudaSuccess) return e;
     if (S.dtype == IC_F32)
         return launch_solves<float>(S, S.uval32, S.rdiag32, r, z, reinterpret_cast<float*>(S.y), grid,
-                                    timeout_ns, s);
-    return launch_solves<double>(S, S.uval, S.rdiag, r, z, S.y, grid, timeout_ns, s);
+                                    timeout_ns, s, t0, t1);
+    return launch_solves<double>(S, S.uval, S.rdiag, r, z, S.y, grid, timeout_ns, s, t0, t1);
 }
 
 cudaError_t launch_solve_prepare(const SolvePlan& S, cudaStream_t s) {
     if (S.n == 0) return cudaSuccess;
     int g = (S.n + 255) / 256;
     rdiag_kernel<<<g > 4096 ? 4096 : g, 256, 0, s>>>(S);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_dag_prepare(S, s);
 }
 
 // ---------------------------------------------------------------------------------

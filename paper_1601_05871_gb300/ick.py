@@ -35,7 +35,8 @@ class ic_opts(C.Structure):
     _fields_ = [("block_rows", C.c_int), ("dtype", C.c_int), ("warps_per_cta", C.c_int),
                 ("rows_per_item", C.c_int), ("timeout_s", C.c_double), ("shift_alpha", C.c_double),
                 ("exact", C.c_int), ("threads", C.c_int), ("host_only", C.c_int),
-                ("solve_ctas_per_sm", C.c_int), ("solve_lanes", C.c_int), ("reserved", C.c_int * 3)]
+                ("solve_ctas_per_sm", C.c_int), ("solve_lanes", C.c_int), ("solve_mode", C.c_int),
+                ("reserved", C.c_int * 2)]
 
 
 class ic_stats_t(C.Structure):
@@ -70,6 +71,7 @@ def load():
         "ic_get_task_targets": (I, [P, I64, P, P]),
         "ic_get_upper": (I, [P, P, P, P, P, P]),
         "ic_get_blocks": (I, [P, P, P, P]),
+        "ic_get_solve_tasks": (I, [P, I, P, P, P, P, P, P, P, P, P]),
         "ic_set_timing": (I, [P, I]),
         "ic_reset_timing": (I, [P]),
         "ic_get_timing": (I, [P, P]),
@@ -82,6 +84,8 @@ def load():
         "ic_autotune": (I, [I64, P, I, P, P, P, P, P, I, P, P, P]),
         "ic_set_trace": (I, [P, I]),
         "ic_get_trace": (I, [P, P]),
+        "ic_get_solve_trace": (I, [P, I, P]),
+        "ic_get_solve_entries": (I, [P, I, P, P, P]),
         "ic_destroy": (None, [P]),
         "ic_strerror": (C.c_char_p, [I]),
         "ic_last_error": (C.c_char_p, []),
@@ -181,14 +185,14 @@ class Handle:
 
 def ic_symbolic(rowptr, colind, k, perm=None, ranges=None, *, block_rows=0, dtype=IC_F64,
                 warps_per_cta=0, rows_per_item=0, timeout_s=0.0, shift_alpha=0.0, exact=0,
-                threads=0, host_only=0, solve_ctas_per_sm=0, solve_lanes=0):
+                threads=0, host_only=0, solve_ctas_per_sm=0, solve_lanes=0, solve_mode=0):
     L = load()
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     n = len(rowptr) - 1
     pat = ic_csr_pattern(n, _p(rowptr), _p(colind))
     o = ic_opts(block_rows, dtype, warps_per_cta, rows_per_item, timeout_s, shift_alpha, exact, threads,
-                host_only, solve_ctas_per_sm, solve_lanes)
+                host_only, solve_ctas_per_sm, solve_lanes, solve_mode)
     perm_a = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
     ranges_a = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
     nr = 0 if ranges_a is None else len(ranges_a) - 1
@@ -311,9 +315,61 @@ def ic_get_blocks(h):
     return ranges, bptr, bcol[:nbk]
 
 
+def ic_get_solve_tasks(h, backward=False):
+    """Block-DAG solve plan of one direction: dict with tasks (ntasks x 4: type 0 = E /
+    1 = L, range, first row, end row) in claim order, counters (2 x nranges: ranges
+    waited for, E tasks), succ_ptr/succ, split (per row) and order_ptr/order."""
+    L = load()
+    st = ic_stats(h)
+    n, nr = st["n"], st["nranges"]
+    nt = np.zeros(1, dtype=np.int64)
+    _check(L.ic_get_solve_tasks(h.ptr, int(bool(backward)), _p(nt), None, None, None, None, None, None, None,
+                                None))
+    tasks = np.empty((max(1, int(nt[0])), 4), dtype=np.int32)
+    cnt = np.empty((2, max(1, nr)), dtype=np.int32)
+    sptr = np.empty(nr + 1, dtype=np.int32)
+    optr = np.empty(nr + 1, dtype=np.int32)
+    split = np.empty(max(1, n), dtype=np.int32)
+    _check(L.ic_get_solve_tasks(h.ptr, int(bool(backward)), None, None, _p(cnt), _p(sptr), None, None, _p(optr),
+                                None, None))
+    succ = np.empty(max(1, int(sptr[-1])), dtype=np.int32)
+    order = np.empty(max(1, int(optr[-1])), dtype=np.int32)
+    need = np.empty(max(1, int(optr[-1])), dtype=np.int32)
+    _check(L.ic_get_solve_tasks(h.ptr, int(bool(backward)), None, _p(tasks), None, None, _p(succ), _p(split), None,
+                                _p(order), _p(need)))
+    return {"tasks": tasks[: int(nt[0])], "counters": cnt[:, :nr], "succ_ptr": sptr, "succ": succ[: int(sptr[-1])],
+            "split": split[:n], "order_ptr": optr, "order": order[: int(optr[-1])], "need": need[: int(optr[-1])]}
+
+
+def ic_get_solve_entries(h, backward=False):
+    """Internal entries of the rows as the L tasks apply them: dict with ptr (n+1),
+    j and pos (ptr[-1] each)."""
+    L = load()
+    n = ic_stats(h)["n"]
+    ptr = np.empty(n + 1, dtype=np.int32)
+    _check(L.ic_get_solve_entries(h.ptr, int(bool(backward)), _p(ptr), None, None))
+    m = int(ptr[-1])
+    j = np.empty(max(1, m), dtype=np.int32)
+    pos = np.empty(max(1, m), dtype=np.int32)
+    _check(L.ic_get_solve_entries(h.ptr, int(bool(backward)), None, _p(j), _p(pos)))
+    return {"ptr": ptr, "j": j[:m], "pos": pos[:m]}
+
+
+def ic_get_solve_trace(h, backward=False):
+    """(ntasks, 4) uint64 of the last block-DAG solve: claim ns, wait end ns, end ns,
+    task | SM << 32 (tasks in ic_get_solve_tasks' claim order)."""
+    nt = np.zeros(1, dtype=np.int64)
+    _check(load().ic_get_solve_tasks(h.ptr, int(bool(backward)), _p(nt), None, None, None, None, None, None, None,
+                                     None))
+    out = np.zeros((max(1, int(nt[0])), 4), dtype=np.uint64)
+    _check(load().ic_get_solve_trace(h.ptr, int(bool(backward)), _p(out)))
+    return out[: int(nt[0])]
+
+
 class ic_timing_t(C.Structure):
     _fields_ = [("prepare_ms", C.c_double), ("numeric_ms", C.c_double), ("apply_ms", C.c_double),
-                ("apply_calls", C.c_int64), ("launches", C.c_int64)]
+                ("apply_calls", C.c_int64), ("launches", C.c_int64), ("fwd_ms", C.c_double),
+                ("bwd_ms", C.c_double)]
 
 
 def ic_set_timing(h, on=True):
@@ -347,9 +403,9 @@ def ic_get_trace(h):
 
 
 def _opts(block_rows=0, dtype=IC_F64, warps_per_cta=0, rows_per_item=0, timeout_s=0.0, shift_alpha=0.0,
-          exact=0, threads=0, host_only=0, solve_ctas_per_sm=0, solve_lanes=0):
+          exact=0, threads=0, host_only=0, solve_ctas_per_sm=0, solve_lanes=0, solve_mode=0):
     return ic_opts(block_rows, dtype, warps_per_cta, rows_per_item, timeout_s, shift_alpha, exact, threads,
-                   host_only, solve_ctas_per_sm, solve_lanes)
+                   host_only, solve_ctas_per_sm, solve_lanes, solve_mode)
 
 
 def _batch_args(patterns, perms, ranges):
