@@ -2,8 +2,9 @@
 
 This package holds only input generation: sparse SPD matrices in CSR form
 (full symmetric pattern, sorted columns), right-hand sides and the small
-random test matrices.  It contains none of the factorization's arithmetic
-and imports neither the oracle nor the CUDA library.
+random test matrices, and the seeded initial weights of the shift-predictor
+network.  It contains none of the method's arithmetic and imports neither the
+oracle nor the CUDA library.
 """
 from .matrices import (  # noqa: F401
     Problem,
@@ -18,3 +19,4 @@ from .matrices import (  # noqa: F401
     config_problem,
     is_exactly_symmetric,
 )
+from .params import mlp_init  # noqa: F401,E402
