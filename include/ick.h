@@ -345,6 +345,61 @@ int ic_get_trace(const ic_handle* h, uint64_t* out);
  * (backward = 0) or backward (1) solve.  Errors: IC_ERR_ARG, IC_ERR_STATE, IC_ERR_CUDA. */
 int ic_get_solve_trace(const ic_handle* h, int backward, uint64_t* out);
 
+/* ----------------------------------------------------------------------------
+ * Diagonal shift.  IC(k) of a matrix that is not an M-matrix can break down (a pivot
+ * <= 0 once fill is dropped; Section 1 motivates IC(k) for SPD matrices, which does
+ * not guarantee positive incomplete pivots).  Factoring B + alpha * diag(B) restores
+ * positive pivots for a large enough alpha, at the price of a weaker preconditioner.
+ * ------------------------------------------------------------------------- */
+
+/* Features of the handle's matrix with the given values (device, CSR order of A),
+ * computed on the GPU in FP64 with deterministic reductions: for row i with d = A_ii,
+ * s = sum_{j != i} |A_ij| and r = ||row i||_2, dd_i = d / max(s, d / 1000) and
+ * rn_i = r / d; out (host, 8 doubles) = [min dd, mean dd, mean rn, max rn, fraction
+ * of off-diagonal entries > 0, k, log10 n, nu].  nu: a material parameter supplied by
+ * the caller (0 when none applies).  Errors: IC_ERR_ARG (also when a diagonal entry
+ * is missing or not positive), IC_ERR_CUDA. */
+int ic_shift_features(const ic_handle* h, const void* A_vals, double nu, double* out, void* stream);
+
+/* Numeric factorization with the shift-doubling retry: attempts are made with
+ * alpha = alpha_first, then twice the previous alpha (alpha0 after a zero alpha),
+ * until one has no breakdown or max_tries attempts have broken down.  The handle's
+ * own shift_alpha is not changed.  alpha_used and attempts (host, may be NULL)
+ * receive the successful alpha and the number of attempts made.  Returns IC_OK, or
+ * IC_ERR_BREAKDOWN when every attempt broke down (the handle then holds no factor),
+ * or the error of a failing attempt. */
+int ic_numeric_shifted(ic_handle* h, const void* A_vals, double alpha_first, double alpha0, int max_tries,
+                       double* alpha_used, int* attempts, void* stream);
+
+/* Shift-predictor MLP (8 standardised features -> 32 ReLU -> 32 ReLU -> log10 alpha),
+ * FP32 parameters on the device of creation, trained and evaluated by the library's
+ * kernels.  Parameters (ic_mlp_n_params() floats) in the order W1 (8 x 32 row-major,
+ * feature f to unit h at f*32 + h), b1 (32), W2 (32 x 32 row-major, unit g to unit h
+ * at g*32 + h), b2 (32), w3 (32), b3.  The paper has no counterpart: this is the
+ * learned part of the shift retry. */
+typedef struct ic_mlp ic_mlp;
+int ic_mlp_n_params(void);
+/* params (host, NULL: zeros) are copied; Adam moments start at zero. */
+int ic_mlp_create(const float* params, ic_mlp** out);
+int ic_mlp_set_params(ic_mlp* m, const float* params);
+int ic_mlp_get_params(const ic_mlp* m, float* params);
+/* Feature standardisation z = (x - mean) / std (host, 8 floats each; std > 0). */
+int ic_mlp_set_scaling(ic_mlp* m, const float* mean, const float* std);
+int ic_mlp_get_scaling(const ic_mlp* m, float* mean, float* std);
+/* y[i] = network(X[i]) for n samples; X (device, n x 8 row-major), y (device, n). */
+int ic_mlp_forward(ic_mlp* m, const float* X, int64_t n, float* y, void* stream);
+/* Loss (1 / 2n) sum (y_i - t_i)^2 and its gradient with respect to the parameters,
+ * without an update; X, t device; grad (host, n_params floats) and loss (host) may be
+ * NULL.  The stream is synchronised. */
+int ic_mlp_gradient(ic_mlp* m, const float* X, const float* t, int64_t n, float* grad, float* loss, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected; the handle counts the
+ * steps) on the loss above with learning rate lr; loss (host, may be NULL) receives
+ * the loss before the step (the stream is then synchronised). */
+int ic_mlp_train_step(ic_mlp* m, const float* X, const float* t, int64_t n, float lr, float* loss, void* stream);
+/* alpha = 10^network(features) for one feature vector (host, 8 doubles). */
+int ic_mlp_predict_shift(ic_mlp* m, const double* features, double* alpha, void* stream);
+void ic_mlp_destroy(ic_mlp* m);
+
 void ic_destroy(ic_handle* h);
 
 /* Static English text for a status code. */

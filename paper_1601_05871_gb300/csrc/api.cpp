@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -1208,6 +1209,204 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
         times[1] = best_apply;
     }
     return IC_OK;
+}
+
+int ic_shift_features(const ic_handle* h, const void* A_vals, double nu, double* out, void* stream) {
+    if (!h || !out || (!A_vals && h->hp.n > 0)) return fail(IC_ERR_ARG, "NULL argument");
+    if (h->device < 0) return fail(IC_ERR_STATE, "host-only handle");
+    if (h->hp.n == 0) return fail(IC_ERR_ARG, "empty matrix");
+    DeviceGuard g(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, features_scratch_bytes() + 16 * sizeof(double), s));
+    double* dout = reinterpret_cast<double*>(static_cast<char*>(scratch) + features_scratch_bytes());
+    cudaError_t e = launch_features(int(h->hp.n), h->sp.arp, h->sp.acol, static_cast<const double*>(A_vals),
+                                    h->hp.k, nu, scratch, dout, s);
+    double tmp[9] = {0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, dout, 9 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ic_shift_features");
+    if (tmp[8] != 0.0) return fail(IC_ERR_ARG, "a diagonal entry is missing or not positive");
+    for (int q = 0; q < 8; ++q) out[q] = tmp[q];
+    return IC_OK;
+}
+
+int ic_numeric_shifted(ic_handle* h, const void* A_vals, double alpha_first, double alpha0, int max_tries,
+                       double* alpha_used, int* attempts, void* stream) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    if (max_tries < 1 || !(alpha_first >= 0.0) || !(alpha0 > 0.0)) return fail(IC_ERR_ARG, "bad retry parameters");
+    const double keep = h->opts.shift_alpha;
+    double a = alpha_first;
+    int st = IC_ERR_BREAKDOWN;
+    int t = 0;
+    while (t < max_tries) {
+        h->opts.shift_alpha = a;
+        ++t;
+        st = ic_numeric(h, A_vals, stream, nullptr);
+        if (st != IC_ERR_BREAKDOWN) break;
+        a = a > 0.0 ? 2.0 * a : alpha0;
+    }
+    h->opts.shift_alpha = keep;
+    if (attempts) *attempts = t;
+    if (st == IC_OK && alpha_used) *alpha_used = a;  // the loop stops on the first success
+    if (st == IC_ERR_BREAKDOWN) return fail(IC_ERR_BREAKDOWN, "every shift attempt broke down");
+    return st;
+}
+
+}  // extern "C"
+
+struct ic_mlp {
+    int device = -1;
+    int step = 0;
+    MlpDev d{};
+    float* X1 = nullptr;    // device scratch for one feature vector and its output
+    float* hbuf = nullptr;  // pinned loss
+    std::vector<void*> allocs;
+    ~ic_mlp() {
+        for (void* p : allocs) cudaFree(p);
+        if (hbuf) cudaFreeHost(hbuf);
+    }
+    int alloc(float** out, size_t count) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(float));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        allocs.push_back(p);
+        *out = static_cast<float*>(p);
+        return IC_OK;
+    }
+};
+
+extern "C" {
+
+int ic_mlp_n_params(void) { return kMlpParams; }
+
+int ic_mlp_create(const float* params, ic_mlp** out) {
+    if (!out) return fail(IC_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    ic_mlp* m = new ic_mlp();
+    int st = IC_OK;
+    CK(cudaGetDevice(&m->device));
+    MlpDev& D = m->d;
+    float** bufs[] = {&D.theta, &D.m, &D.v, &D.grad};
+    for (float** b : bufs)
+        if (!st) st = m->alloc(b, kMlpParams);
+    if (!st) st = m->alloc(&D.mean, kMlpFeatures);
+    if (!st) st = m->alloc(&D.rstd, kMlpFeatures);
+    if (!st) st = m->alloc(&D.part, size_t(kMlpMaxBlocks) * kMlpParams);
+    if (!st) st = m->alloc(&D.loss_part, kMlpMaxBlocks);
+    if (!st) st = m->alloc(&D.loss, 1);
+    if (!st) st = m->alloc(&m->X1, 16);
+    if (st) {
+        delete m;
+        return st;
+    }
+    cudaError_t e = cudaMallocHost(&m->hbuf, 16 * sizeof(float));
+    for (float* b : {D.theta, D.m, D.v, D.grad})
+        if (e == cudaSuccess) e = cudaMemset(b, 0, kMlpParams * sizeof(float));
+    if (e == cudaSuccess && params)
+        e = cudaMemcpy(D.theta, params, kMlpParams * sizeof(float), cudaMemcpyHostToDevice);
+    const float zero[kMlpFeatures] = {0}, one[kMlpFeatures] = {1, 1, 1, 1, 1, 1, 1, 1};
+    if (e == cudaSuccess) e = cudaMemcpy(D.mean, zero, sizeof(zero), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(D.rstd, one, sizeof(one), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "ic_mlp_create");
+    }
+    *out = m;
+    return IC_OK;
+}
+
+int ic_mlp_set_params(ic_mlp* m, const float* params) {
+    if (!m || !params) return fail(IC_ERR_ARG, "NULL argument");
+    DeviceGuard g(m->device);
+    CK(cudaMemcpy(m->d.theta, params, kMlpParams * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemset(m->d.m, 0, kMlpParams * sizeof(float)));
+    CK(cudaMemset(m->d.v, 0, kMlpParams * sizeof(float)));
+    m->step = 0;
+    return IC_OK;
+}
+
+int ic_mlp_get_params(const ic_mlp* m, float* params) {
+    if (!m || !params) return fail(IC_ERR_ARG, "NULL argument");
+    DeviceGuard g(m->device);
+    CK(cudaMemcpy(params, m->d.theta, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost));
+    return IC_OK;
+}
+
+int ic_mlp_set_scaling(ic_mlp* m, const float* mean, const float* std) {
+    if (!m || !mean || !std) return fail(IC_ERR_ARG, "NULL argument");
+    float r[kMlpFeatures];
+    for (int f = 0; f < kMlpFeatures; ++f) {
+        if (!(std[f] > 0.0f)) return fail(IC_ERR_ARG, "std must be positive");
+        r[f] = 1.0f / std[f];
+    }
+    DeviceGuard g(m->device);
+    CK(cudaMemcpy(m->d.mean, mean, sizeof(r), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d.rstd, r, sizeof(r), cudaMemcpyHostToDevice));
+    return IC_OK;
+}
+
+int ic_mlp_get_scaling(const ic_mlp* m, float* mean, float* std) {
+    if (!m || !mean || !std) return fail(IC_ERR_ARG, "NULL argument");
+    DeviceGuard g(m->device);
+    float r[kMlpFeatures];
+    CK(cudaMemcpy(mean, m->d.mean, sizeof(r), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(r, m->d.rstd, sizeof(r), cudaMemcpyDeviceToHost));
+    for (int f = 0; f < kMlpFeatures; ++f) std[f] = 1.0f / r[f];
+    return IC_OK;
+}
+
+int ic_mlp_forward(ic_mlp* m, const float* X, int64_t n, float* y, void* stream) {
+    if (!m || n < 0 || (n > 0 && (!X || !y))) return fail(IC_ERR_ARG, "bad argument");
+    DeviceGuard g(m->device);
+    CK(launch_mlp_forward(m->d, X, n, y, static_cast<cudaStream_t>(stream)));
+    return IC_OK;
+}
+
+int ic_mlp_gradient(ic_mlp* m, const float* X, const float* t, int64_t n, float* grad, float* loss, void* stream) {
+    if (!m || n < 1 || !X || !t) return fail(IC_ERR_ARG, "bad argument");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(launch_mlp_grad(m->d, X, t, n, s));
+    if (grad) CK(cudaMemcpyAsync(grad, m->d.grad, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(m->hbuf, m->d.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (loss) *loss = m->hbuf[0];
+    return IC_OK;
+}
+
+int ic_mlp_train_step(ic_mlp* m, const float* X, const float* t, int64_t n, float lr, float* loss, void* stream) {
+    if (!m || n < 1 || !X || !t || !(lr > 0.0f)) return fail(IC_ERR_ARG, "bad argument");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(launch_mlp_grad(m->d, X, t, n, s));
+    CK(launch_mlp_adam(m->d, lr, ++m->step, s));
+    if (loss) {
+        CK(cudaMemcpyAsync(m->hbuf, m->d.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *loss = m->hbuf[0];
+    }
+    return IC_OK;
+}
+
+int ic_mlp_predict_shift(ic_mlp* m, const double* features, double* alpha, void* stream) {
+    if (!m || !features || !alpha) return fail(IC_ERR_ARG, "NULL argument");
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int f = 0; f < kMlpFeatures; ++f) m->hbuf[f] = float(features[f]);
+    CK(cudaMemcpyAsync(m->X1, m->hbuf, kMlpFeatures * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(launch_mlp_forward(m->d, m->X1, 1, m->X1 + kMlpFeatures, s));
+    CK(cudaMemcpyAsync(m->hbuf + kMlpFeatures, m->X1 + kMlpFeatures, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *alpha = std::pow(10.0, double(m->hbuf[kMlpFeatures]));
+    return IC_OK;
+}
+
+void ic_mlp_destroy(ic_mlp* m) {
+    if (!m) return;
+    DeviceGuard g(m->device);
+    delete m;
 }
 
 void ic_destroy(ic_handle* h) {

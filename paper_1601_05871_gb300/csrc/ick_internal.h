@@ -248,6 +248,26 @@ cudaError_t batch_xr(int n, const int* sys, const double* alpha, double* x, doub
 cudaError_t batch_p(int n, const int* sys, const double* beta, const int* active, double* p,
                     const double* z, cudaStream_t s);
 
+// Learned diagonal shift (shift.cu).
+constexpr double kShiftDdCap = 1000.0;  // diagonal dominance of a row without off-diagonals
+constexpr int kMlpFeatures = 8;
+constexpr int kMlpHidden = 32;
+constexpr int kMlpParams = kMlpFeatures * kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden +
+                           kMlpHidden + 1;
+constexpr int kMlpMaxBlocks = 1024;     // partial-gradient blocks of one gradient evaluation
+struct MlpDev {
+    float *theta, *m, *v, *grad;  // parameters, Adam moments, last gradient (kMlpParams each)
+    float *mean, *rstd;           // feature standardisation: (x - mean) * rstd
+    float *part, *loss_part, *loss;  // per-block partial gradients and losses, the loss
+};
+int mlp_grad_blocks(long long n);
+cudaError_t launch_features(int n, const long long* rp, const int* ci, const double* v, int k, double nu,
+                            void* scratch, double* out, cudaStream_t s);
+size_t features_scratch_bytes();
+cudaError_t launch_mlp_forward(const MlpDev& M, const float* X, long long n, float* y, cudaStream_t s);
+cudaError_t launch_mlp_grad(const MlpDev& M, const float* X, const float* t, long long n, cudaStream_t s);
+cudaError_t launch_mlp_adam(const MlpDev& M, float lr, int step, cudaStream_t s);
+
 // Host symbolic phase (host.cpp).
 int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
                int64_t nranges, int block_rows, int rows_per_item, int threads, HostPlan& P,

@@ -86,6 +86,19 @@ def load():
         "ic_get_trace": (I, [P, P]),
         "ic_get_solve_trace": (I, [P, I, P]),
         "ic_get_solve_entries": (I, [P, I, P, P, P]),
+        "ic_shift_features": (I, [P, P, D, P, P]),
+        "ic_numeric_shifted": (I, [P, P, D, D, I, P, P, P]),
+        "ic_mlp_n_params": (I, []),
+        "ic_mlp_create": (I, [P, P]),
+        "ic_mlp_set_params": (I, [P, P]),
+        "ic_mlp_get_params": (I, [P, P]),
+        "ic_mlp_set_scaling": (I, [P, P, P]),
+        "ic_mlp_get_scaling": (I, [P, P, P]),
+        "ic_mlp_forward": (I, [P, P, I64, P, P]),
+        "ic_mlp_gradient": (I, [P, P, P, I64, P, P, P]),
+        "ic_mlp_train_step": (I, [P, P, P, I64, C.c_float, P, P]),
+        "ic_mlp_predict_shift": (I, [P, P, P, P]),
+        "ic_mlp_destroy": (None, [P]),
         "ic_destroy": (None, [P]),
         "ic_strerror": (C.c_char_p, [I]),
         "ic_last_error": (C.c_char_p, []),
@@ -506,3 +519,111 @@ def ic_autotune(patterns, k, values, perms=None, ranges=None, reps=3, stream=Non
 
 def ic_destroy(h):
     h.close()
+
+
+# ------------------------------------------------------------- diagonal shift
+
+
+def ic_shift_features(h, values, nu=0.0, stream=None):
+    """The 8 matrix features of the shift predictor (numpy float64)."""
+    out = np.zeros(8, dtype=np.float64)
+    _check(load().ic_shift_features(h.ptr, _p(values), float(nu), _p(out), _stream(stream)))
+    return out
+
+
+def ic_numeric_shifted(h, values, alpha_first=0.0, alpha0=1e-3, max_tries=20, stream=None):
+    """Numeric IC(k) with the shift-doubling retry; returns (alpha used, attempts)."""
+    a = np.zeros(1, dtype=np.float64)
+    t = np.zeros(1, dtype=np.int32)
+    st = load().ic_numeric_shifted(h.ptr, _p(values), float(alpha_first), float(alpha0), int(max_tries), _p(a),
+                                   _p(t), _stream(stream))
+    if st == IC_ERR_BREAKDOWN:
+        e = IckError(st, f"all {int(t[0])} shift attempts broke down")
+        e.attempts = int(t[0])
+        raise e
+    _check(st)
+    return float(a[0]), int(t[0])
+
+
+def ic_mlp_n_params():
+    return int(load().ic_mlp_n_params())
+
+
+class Mlp:
+    """The shift-predictor network (owns an ic_mlp)."""
+
+    def __init__(self, params=None):
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        out = C.c_void_p()
+        _check(load().ic_mlp_create(_p(p), C.byref(out)))
+        self._m = out.value
+
+    @property
+    def ptr(self):
+        return self._m
+
+    def close(self):
+        if self._m:
+            load().ic_mlp_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ic_mlp_create(params=None):
+    return Mlp(params)
+
+
+def ic_mlp_set_params(m, params):
+    _check(load().ic_mlp_set_params(m.ptr, _p(np.ascontiguousarray(params, dtype=np.float32))))
+
+
+def ic_mlp_get_params(m):
+    out = np.empty(ic_mlp_n_params(), dtype=np.float32)
+    _check(load().ic_mlp_get_params(m.ptr, _p(out)))
+    return out
+
+
+def ic_mlp_set_scaling(m, mean, std):
+    _check(load().ic_mlp_set_scaling(m.ptr, _p(np.ascontiguousarray(mean, dtype=np.float32)),
+                                     _p(np.ascontiguousarray(std, dtype=np.float32))))
+
+
+def ic_mlp_get_scaling(m):
+    mean = np.empty(8, dtype=np.float32)
+    std = np.empty(8, dtype=np.float32)
+    _check(load().ic_mlp_get_scaling(m.ptr, _p(mean), _p(std)))
+    return mean, std
+
+
+def ic_mlp_forward(m, X, y, stream=None):
+    """X: CUDA float32 tensor (n, 8); y: CUDA float32 tensor (n,)."""
+    _check(load().ic_mlp_forward(m.ptr, _p(X), int(X.shape[0]), _p(y), _stream(stream)))
+
+
+def ic_mlp_gradient(m, X, t, stream=None):
+    """(gradient as numpy float32, loss) of (1/2n) sum (y - t)^2; no update."""
+    g = np.empty(ic_mlp_n_params(), dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(load().ic_mlp_gradient(m.ptr, _p(X), _p(t), int(X.shape[0]), _p(g), _p(loss), _stream(stream)))
+    return g, float(loss[0])
+
+
+def ic_mlp_train_step(m, X, t, lr, stream=None, want_loss=True):
+    """One Adam step; returns the loss before the step (None when want_loss is false:
+    the call then does not synchronise)."""
+    loss = np.zeros(1, dtype=np.float32) if want_loss else None
+    _check(load().ic_mlp_train_step(m.ptr, _p(X), _p(t), int(X.shape[0]), float(lr), _p(loss), _stream(stream)))
+    return float(loss[0]) if want_loss else None
+
+
+def ic_mlp_predict_shift(m, features, stream=None):
+    a = np.zeros(1, dtype=np.float64)
+    _check(load().ic_mlp_predict_shift(m.ptr, _p(np.ascontiguousarray(features, dtype=np.float64)), _p(a),
+                                       _stream(stream)))
+    return float(a[0])
+
