@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-f32", action="store_true", help="skip the mixed-precision arm")
     ap.add_argument("--solve-mode", type=int, default=0, choices=[0, 1],
                     help="triangular solves: 0 block-DAG, 1 row-level")
+    ap.add_argument("--shift", action="store_true",
+                    help="learned-shift workload instead: Q1 elasticity, FP32 + learned shift vs plain FP64")
+    ap.add_argument("--ne", type=int, default=48, help="elements per side of the --shift workload")
     return ap.parse_args()
 
 
@@ -175,8 +178,82 @@ def reference_arm(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+SHIFT_NU_TRAIN = (0.40, 0.44, 0.46, 0.47, 0.475, 0.48, 0.485, 0.49, 0.493, 0.496, 0.499)
+SHIFT_NU_TEST = (0.4725, 0.4875, 0.4965)
+SHIFT_ALPHAS = [0.0] + [1e-3 * 2 ** j for j in range(13)]
+SHIFT_NE_TRAIN = (6, 8, 12, 16, 24)
+
+
+def shift_workload(a):
+    """Q1 hex elasticity (ne^3 elements, clamped face, IC(0), geometric ND): time to a
+    relative residual of 1e-8, all factorization attempts included, for the plain FP64
+    form (FP64 factor, shift 0 then 1e-3 doubling) and the FP32 + learned-shift form
+    (FP32 factor with FP64 pivots, first shift from the network trained on shift
+    sweeps of 6^3 to 24^3 meshes, doubling as the fallback).  Poisson ratios of the
+    timed instances are held out of training."""
+    import torch
+    import synth
+    import paper_1601_05871_gb300 as ick
+    from paper_1601_05871_gb300 import shift_train as T
+    from paper_1601_05871_gb300.build import build
+
+    build()
+    ick.load()
+    t0 = time.perf_counter()
+    X, y = [], []
+    for ne in SHIFT_NE_TRAIN:
+        for nu in SHIFT_NU_TRAIN:
+            p = synth.elasticity3d_q1(ne, nu=nu)
+            perm, ranges = ick.ic_nd_grid(*p.grid, 3, 256, p.keep)
+            h = ick.ic_symbolic(p.rowptr, p.colind, 0, perm, ranges, block_rows=256, dtype=ick.IC_F32)
+            av = torch.from_numpy(p.vals).cuda()
+            b = torch.from_numpy(synth.rhs(p.n, 11)).cuda()
+            x = torch.empty_like(b)
+            X.append(ick.ic_shift_features(h, av, nu))
+            y.append(T.label(T.sweep(h, av, b, x, SHIFT_ALPHAS)))
+    mlp, loss = T.train(np.array(X), np.array(y), steps=1500, lr=1e-2, seed=1)
+    train_s = time.perf_counter() - t0
+    rows = []
+    for nu in SHIFT_NU_TEST:
+        p = synth.elasticity3d_q1(a.ne, nu=nu)
+        perm, ranges = ick.ic_nd_grid(*p.grid, 3, 4096, p.keep)
+        av = torch.from_numpy(p.vals).cuda()
+        b = torch.from_numpy(synth.rhs(p.n, 13)).cuda()
+        x = torch.empty_like(b)
+        res = {}
+        for name, dtype, model in (("fp64_plain", ick.IC_F64, None), ("fp32_learned", ick.IC_F32, mlp)):
+            h = ick.ic_symbolic(p.rowptr, p.colind, 0, perm, ranges, block_rows=4096, dtype=dtype)
+            T.solve(h, av, b, x, mlp=model, nu=nu)  # warm-up
+            runs = [T.solve(h, av, b, x, mlp=model, nu=nu) for _ in range(max(1, a.steps))]
+            r = min(runs, key=lambda q: q["seconds"])
+            xh = x.cpu().numpy()
+            r["true_relres"] = float(np.linalg.norm(p.scipy() @ xh - synth.rhs(p.n, 13)) /
+                                     np.linalg.norm(synth.rhs(p.n, 13)))
+            r["ms"] = r.pop("seconds") * 1e3
+            res[name] = r
+            del h
+        rows.append({"nu": nu, "n": p.n, "nnz": int(p.rowptr[-1]), **res,
+                     "speedup": res["fp64_plain"]["ms"] / res["fp32_learned"]["ms"]})
+    tot64 = sum(r["fp64_plain"]["ms"] for r in rows)
+    tot32 = sum(r["fp32_learned"]["ms"] for r in rows)
+    line = {"metric": "elasticity IC(0) time to PCG relres 1e-8, FP32 + learned shift vs plain FP64",
+            "value": tot64 / tot32, "unit": "x (plain FP64 time / FP32 learned-shift time)", "n_gpus": 1,
+            "steps": a.steps, "warmup": 1, "higher_is_better": True, "dtype": "f32 factor, f64 PCG",
+            "data": "synthetic",
+            "config": {"workload": f"Q1 hex elasticity {a.ne}^3 elements (clamped face, 3 dof/node), E = 1, "
+                                   f"held-out nu {list(SHIFT_NU_TEST)}, geometric ND, IC(0), b ~ N(0,1)",
+                       "training": f"shift sweeps of {list(SHIFT_NE_TRAIN)}^3-element meshes, "
+                                   f"nu {list(SHIFT_NU_TRAIN)}",
+                       "train_seconds": train_s, "train_loss": loss},
+            "instances": rows, "total_ms_fp64_plain": tot64, "total_ms_fp32_learned": tot32}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.shift:
+        shift_workload(a)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
