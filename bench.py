@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--shift", action="store_true",
                     help="learned-shift workload instead: Q1 elasticity, FP32 + learned shift vs plain FP64")
     ap.add_argument("--ne", type=int, default=48, help="elements per side of the --shift workload")
+    ap.add_argument("--c5", action="store_true",
+                    help="7-point diffusion workload instead: 160^3 (--side), sigma 2, z faces x100, IC(3)")
     return ap.parse_args()
 
 
@@ -249,10 +251,83 @@ def shift_workload(a):
     print(json.dumps(line), flush=True)
 
 
+def c5_workload(a):
+    """7-point variable-coefficient diffusion (kappa ~ LogNormal(0, 2), z faces x100),
+    geometric ND, 2D blocks <= 4096 rows, IC(3): FP32 factor + FP64 PCG to 1e-8, with
+    the FP64 form beside it.  Reports the largest block density of the factor (the
+    dense-block tensor-core path applies only to dense blocks)."""
+    import torch
+    import synth
+    import paper_1601_05871_gb300 as ick
+    from paper_1601_05871_gb300.build import build
+
+    build()
+    ick.load()
+    side = a.side if a.side != 96 else 160
+    p = synth.config_problem(5, scale=side)
+    perm, ranges = ick.ic_nd_grid(side, side, side, 1, a.block_rows)
+    av = torch.from_numpy(p.vals).cuda()
+    b_host = synth.rhs(p.n, 5000)
+    b = torch.from_numpy(b_host).cuda()
+    x = torch.empty_like(b)
+    out = {}
+    st = None
+    for name, dtype in (("fp32", ick.IC_F32), ("fp64", ick.IC_F64)):
+        h = ick.ic_symbolic(p.rowptr, p.colind, 3, perm, ranges, block_rows=a.block_rows, dtype=dtype)
+        st = ick.ic_stats(h)
+        ick.ic_set_timing(h, True)
+        for _ in range(a.warmup):
+            ick.ic_numeric(h, av)
+            ick.pcg_solve(h, av, b, x, 1e-8, 5000)
+        torch.cuda.synchronize()
+        fact, tts, its = [], [], 0
+        for _ in range(a.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ick.ic_numeric(h, av)
+            t = ick.ic_get_timing(h)
+            its, rel = ick.pcg_solve(h, av, b, x, 1e-8, 5000)
+            e1.record()
+            torch.cuda.synchronize()
+            fact.append(t["prepare_ms"] + t["numeric_ms"])
+            tts.append(e0.elapsed_time(e1))
+        true_rel = float(np.linalg.norm(p.scipy() @ x.cpu().numpy() - b_host) / np.linalg.norm(b_host))
+        mf = statistics.median(fact)
+        out[name] = {"factor_ms": mf, "factor_gflops": st["flops"] / (mf * 1e-3) / 1e9,
+                     "time_to_solution_ms": statistics.median(tts), "pcg_iters": int(its), "relres": float(rel),
+                     "true_relres": true_rel}
+        del h
+    # largest block density: entries of each (row range, column range) block over its area
+    hh = ick.ic_symbolic(p.rowptr, p.colind, 3, perm, ranges, block_rows=a.block_rows, host_only=1)
+    urp, ucol, _, _, _ = ick.ic_get_upper(hh)
+    rg, _, _ = ick.ic_get_blocks(hh)
+    blk = np.searchsorted(rg, np.arange(p.n), side="right") - 1
+    rows = np.repeat(np.arange(p.n), np.diff(urp))
+    nb = len(rg) - 1
+    cnt = np.bincount(blk[rows].astype(np.int64) * nb + blk[ucol], minlength=nb * nb).reshape(nb, nb)
+    sz = np.diff(rg).astype(np.float64)
+    area = np.outer(sz, sz)
+    area[np.diag_indices(nb)] = sz * (sz + 1) / 2
+    dens = np.where(cnt > 0, cnt / area, 0.0)
+    line = {"metric": "IC(3) FP32 factor + FP64 PCG time to 1e-8 (7-point diffusion)",
+            "value": out["fp32"]["time_to_solution_ms"], "unit": "ms", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "higher_is_better": False, "dtype": "f32 factor, f64 PCG", "data": "synthetic",
+            "config": {"workload": f"7-point diffusion {side}^3, kappa ~ LogNormal(0, 2), z faces x100, "
+                                   f"geometric ND, 2D blocks <= {a.block_rows} rows, IC(3)",
+                       "n": st["n"], "nnz_a": st["nnz_a"], "nnz_l": st["nnz_l"], "blocks": st["nblocks"],
+                       "tasks": st["ntasks"], "flops": st["flops"]},
+            "max_block_density": float(dens.max()), "blocks_denser_than_5pct": int((dens >= 0.05).sum()),
+            **out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.shift:
         shift_workload(a)
+        return
+    if a.c5:
+        c5_workload(a)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
