@@ -226,16 +226,18 @@ int ic_get_upper(const ic_handle* h, int64_t* urp, int32_t* ucol, int64_t* cptr,
 int ic_get_blocks(const ic_handle* h, int64_t* ranges, int64_t* bptr, int32_t* bcol);
 
 /* The block-DAG triangular solves of ic_apply (solve_mode 0), for inspection and
- * tests.  A block row (range) k is solved by task L(k) (one CTA, rows in the range's
- * local dependence-level order) after tasks E(k, c), which sum the entries that
- * reach outside the range, each for a chunk of its rows.  backward = 0: L y = r;
- * 1: L^T z = y.  Every pointer may be NULL (that output is skipped).
+ * tests.  Each block row (range) has its rows in local dependence-level order
+ * (order); a range with entries reaching outside it is cut into parts of a few
+ * levels.  Per part, task L (one CTA) solves the part's rows after the range's
+ * previous part, and tasks E sum, for chunks of the part's rows, the entries that
+ * reach outside the range, once the parts holding those source rows have finished.
+ * backward = 0: L y = r; 1: L^T z = y.  Every pointer may be NULL (output skipped).
  *   ntasks      receives the number of tasks.
- *   tasks       4 per task in claim order: type (0 = E, 1 = L), range, first row,
- *               end row.
- *   counters    2 * nranges: per range, the ranges it waits for, then its E tasks.
- *   succ_ptr, succ  nranges + 1 offsets and the ranges each L(k) releases (use
- *               ic_stats' nblocks - nranges as the size bound of succ).
+ *   tasks       4 per task in claim order: type (0 = E, 1 = L), range, first and end
+ *               position in order (a position may hold -1: padding).
+ *   counters    ntasks: the number of tasks each task waits for.
+ *   succ_ptr, succ  ntasks + 1 offsets and the tasks each task releases (size
+ *               succ_ptr[ntasks]).
  *   split       n: forward, the column-list index (into ic_get_upper's cp) where
  *               the entries inside the row's range begin; backward, the number of
  *               entries after the diagonal of the row that lie inside its range.

@@ -56,7 +56,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     for src in cpp:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
-        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-Wall", "-Wno-unused-function",
+        # -ffp-contract=off: the host cost models give the same claim orders on every
+        # architecture (no machine-dependent fused multiply-adds)
+        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-Wall",
+                     "-Wno-unused-function",
                      *inc, "-c", src, "-o", obj])
     for src in cu:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

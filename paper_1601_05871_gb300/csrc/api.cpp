@@ -240,8 +240,9 @@ int upload_plan(ic_handle* h) {
     S.solve_mode = h->opts.solve_mode;
     S.nranges = int(P.ranges.size()) - 1;
     S.max_range_rows = P.max_range_rows;
-    S.nftask = int(P.ftask.size());
-    S.nbtask = int(P.btask.size());
+    S.ranges = D.ranges;
+    S.nftask = int(P.fs.task.size());
+    S.nbtask = int(P.bs.task.size());
     S.noff = int(P.nnz_u - P.n);
     if ((st = h->upload(&S.sf_split, P.sf_split))) return st;
     if ((st = h->upload(&S.sb_nint, P.sb_nint))) return st;
@@ -275,14 +276,21 @@ int upload_plan(ic_handle* h) {
             }
         }
     }
-    if ((st = h->upload(&S.ftask, P.ftask))) return st;
-    if ((st = h->upload(&S.btask, P.btask))) return st;
-    if ((st = h->upload(&S.fsucc_ptr, P.fsucc_ptr))) return st;
-    if ((st = h->upload(&S.fsucc, P.fsucc))) return st;
-    if ((st = h->upload(&S.bsucc_ptr, P.bsucc_ptr))) return st;
-    if ((st = h->upload(&S.bsucc, P.bsucc))) return st;
-    if ((st = h->upload(&S.dag_cnt0, P.dag_cnt0))) return st;
-    if ((st = h->alloc(&S.dag_cnt, P.dag_cnt0.size()))) return st;
+    if ((st = h->upload(&S.ftask, P.fs.task))) return st;
+    if ((st = h->upload(&S.btask, P.bs.task))) return st;
+    if ((st = h->upload(&S.f_succ_ptr, P.fs.succ_ptr))) return st;
+    if ((st = h->upload(&S.f_succ, P.fs.succ))) return st;
+    if ((st = h->upload(&S.b_succ_ptr, P.bs.succ_ptr))) return st;
+    if ((st = h->upload(&S.b_succ, P.bs.succ))) return st;
+    {
+        std::vector<int32_t> deg(P.fs.indeg0);
+        deg.insert(deg.end(), P.bs.indeg0.begin(), P.bs.indeg0.end());
+        if ((st = h->upload(&S.dag_indeg0, deg))) return st;
+        if ((st = h->alloc(&S.dag_indeg, deg.size()))) return st;
+        if ((st = h->alloc(&S.dag_taken, deg.size()))) return st;
+    }
+    if ((st = h->upload(&S.f_next, P.fs.next))) return st;
+    if ((st = h->upload(&S.b_next, P.bs.next))) return st;
     {
         double* w = nullptr;
         if ((st = h->alloc(&w, size_t(P.n)))) return st;
@@ -969,8 +977,8 @@ int ic_get_solve_tasks(const ic_handle* h, int backward, int64_t* ntasks, int32_
                        int32_t* need) {
     if (!h || (backward != 0 && backward != 1)) return fail(IC_ERR_ARG, "NULL handle or bad direction");
     const HostPlan& P = h->hp;
-    const std::vector<int4>& T = backward ? P.btask : P.ftask;
-    const size_t nb = P.ranges.size() - 1;
+    const SolveTasks& ST = backward ? P.bs : P.fs;
+    const std::vector<int4>& T = ST.task;
     if (ntasks) *ntasks = int64_t(T.size());
     if (tasks)
         for (size_t t = 0; t < T.size(); ++t) {
@@ -979,9 +987,9 @@ int ic_get_solve_tasks(const ic_handle* h, int backward, int64_t* ntasks, int32_
             tasks[4 * t + 2] = T[t].z;
             tasks[4 * t + 3] = T[t].w;
         }
-    if (counters && nb) std::memcpy(counters, P.dag_cnt0.data() + (backward ? 2 * nb : 0), 2 * nb * sizeof(int32_t));
-    const std::vector<int32_t>& sp = backward ? P.bsucc_ptr : P.fsucc_ptr;
-    const std::vector<int32_t>& sc = backward ? P.bsucc : P.fsucc;
+    if (counters && !ST.indeg0.empty()) std::memcpy(counters, ST.indeg0.data(), ST.indeg0.size() * sizeof(int32_t));
+    const std::vector<int32_t>& sp = ST.succ_ptr;
+    const std::vector<int32_t>& sc = ST.succ;
     if (succ_ptr) std::memcpy(succ_ptr, sp.data(), sp.size() * sizeof(int32_t));
     if (succ && !sc.empty()) std::memcpy(succ, sc.data(), sc.size() * sizeof(int32_t));
     const std::vector<int32_t>& spl = backward ? P.sb_nint : P.sf_split;
@@ -1050,7 +1058,7 @@ int ic_set_trace(ic_handle* h, int on) {
         if (st) return st;
         CK(cudaMemset(t, 0, 4 * size_t(h->hp.total_items > 0 ? h->hp.total_items : 1) * 8));
         h->trace_buf = t;
-        const size_t nt = h->hp.ftask.size() + h->hp.btask.size();
+        const size_t nt = h->hp.fs.task.size() + h->hp.bs.task.size();
         st = h->alloc(&t, 4 * (nt > 0 ? nt : 1));
         if (st) return st;
         CK(cudaMemset(t, 0, 4 * (nt > 0 ? nt : 1) * 8));
@@ -1065,8 +1073,8 @@ int ic_get_solve_trace(const ic_handle* h, int backward, uint64_t* out) {
     if (!h || !out || (backward != 0 && backward != 1)) return fail(IC_ERR_ARG, "bad argument");
     if (!h->solve_trace_buf) return fail(IC_ERR_STATE, "tracing was never enabled");
     DeviceGuard g(h->device);
-    const size_t off = backward ? h->hp.ftask.size() : 0;
-    const size_t cnt = backward ? h->hp.btask.size() : h->hp.ftask.size();
+    const size_t off = backward ? h->hp.fs.task.size() : 0;
+    const size_t cnt = backward ? h->hp.bs.task.size() : h->hp.fs.task.size();
     CK(cudaMemcpy(out, h->solve_trace_buf + 4 * off, 4 * cnt * 8, cudaMemcpyDeviceToHost));
     return IC_OK;
 }

@@ -96,19 +96,20 @@ __device__ __forceinline__ void complete_rows(int* done, unsigned rows_mask) {
 
 // ------------------------------------------------------------------ forward tasks
 
-// E(k, c): w_i = sum of U_pi y_p over the column-list entries of row i with p outside
-// the row's range (a prefix of the list, pivots ascending), for rows [lo, hi).  The
-// values come from the column-ordered copy, contiguous with the column lists.
+// E: w_i = sum of U_pi y_p over the column-list entries of row i with p outside the
+// row's range (a prefix of the list, pivots ascending), for the rows at order
+// positions [lo, hi).  The values come from the column-ordered copy, contiguous with
+// the column lists.
 template <int G, typename T>
 __device__ void fwd_external(const SolvePlan& S, const T* __restrict__ uvt, const T* y, T* w, int lo, int hi) {
     constexpr int R = 32 / G;
     const int lane = threadIdx.x & 31, sub = lane / G, sl = lane % G;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int base = lo + warp * R; base < hi; base += nw * R) {
-        const int i = base + sub;
+        const int i = base + sub < hi ? __ldg(S.lf_ord + base + sub) : -1;
         T acc = T(0);
         int a = 0, b = 0;
-        if (i < hi) {
+        if (i >= 0) {
             a = __ldg(S.cptr + i);
             b = __ldg(S.sf_split + i);
             for (int q = a + sl; q < b; q += G) acc = fma(__ldg(uvt + q), ldcg(y + __ldg(&S.csc[q].x)), acc);
@@ -118,16 +119,19 @@ __device__ void fwd_external(const SolvePlan& S, const T* __restrict__ uvt, cons
     }
 }
 
-// L(k) of either direction: the range's rows in its padded local order, G lanes per
-// row and 32/G rows per warp (one level per claim).  A row runs once every row of the
-// lower levels is complete (done >= need); its internal operands come from shared
-// memory and its other operands are loaded before the wait.
+// L of either direction: the rows at order positions [lo, hi) of range k (whole
+// levels), G lanes per row and 32/G rows per warp (one level per claim).  The range's
+// earlier results (positions before lo, finished by the range's previous parts) are
+// first loaded into shared memory and counted as complete; a row runs once every row
+// of the lower levels is complete (done >= need); its internal operands come from
+// shared memory and its other operands are loaded before the wait.
 //   forward:  y_i = (r_perm(i) - w_i - sum) / U_ii, stored to y
 //   backward: z_i = (y_i - w_i - sum) / U_ii, stored to zv and to z at perm(i)
 template <int G, typename T, bool BW>
 __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const T* __restrict__ rd_all,
                             const double* __restrict__ r, const T* y, T* out, double* __restrict__ z, const T* w,
-                            int k, int s, T* sh, int* claim, int* done, unsigned long long deadline) {
+                            int k, int lo, int hi, T* sh, int* claim, int* done, bool cont,
+                            unsigned long long deadline) {
     constexpr int R = 32 / G, M = Held<G>::M;
     const int lane = threadIdx.x & 31, sl = lane % G;
     const int* ord = BW ? S.lb_ord : S.lf_ord;
@@ -135,14 +139,26 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
     const int* xptr = BW ? S.xb_ptr : S.xf_ptr;
     const int* xj = BW ? S.xb_j : S.xf_j;
     const int base = __ldg((BW ? S.lb_ptr : S.lf_ptr) + k);
-    const int len = __ldg((BW ? S.lb_ptr : S.lf_ptr) + k + 1) - base;
-    for (;;) {
-        int t0 = 0;
-        if (lane == 0) t0 = atomicAdd(claim, R);
-        t0 = __shfl_sync(0xffffffffu, t0, 0);
+    const int s = __ldg(S.ranges + k);
+    if (!cont) {  // a continuation already holds the range's earlier results and count
+        for (int q = base + int(threadIdx.x); q < lo; q += blockDim.x) {
+            const int i = __ldg(ord + q);
+            if (i >= 0) sh[i - s] = ldcg(out + i);
+        }
+        if (threadIdx.x == 0) *done = lo > base ? __ldg(need_a + lo) : 0;
+        __syncthreads();
+    }
+    const int len = hi - lo;
+    // group g of R positions goes to warp g mod (warps): the groups of one level sit on
+    // consecutive warps, i.e. on different SM sub-partitions, whose FP64 units then
+    // work in parallel; each warp takes its groups in order, and a group depends only
+    // on lower groups, so the waits cannot cycle
+    (void)claim;
+    const int nw = blockDim.x >> 5;
+    for (int t0 = (threadIdx.x >> 5) * R;; t0 += nw * R) {
         if (t0 >= len) break;
-        const int i = __ldg(ord + base + t0 + lane / G);
-        const int need = __ldg(need_a + base + t0);
+        const int i = __ldg(ord + lo + t0 + lane / G);
+        const int need = __ldg(need_a + lo + t0);
         T t = T(0), rd = T(0);
         int a = 0, c = 0, dst = 0;
         if (i >= 0) {
@@ -160,6 +176,7 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
                     ext = __ldg(S.cptr + i) < __ldg(S.sf_split + i);
                 }
                 if (ext) t -= ldcg(w + i);
+                t *= rd;  // the row's result is t - rd * (sum of the internal products)
             }
         }
         int j[M];
@@ -182,17 +199,19 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
         if (lane == 0) ok = await_count(done, need, S.counter + 2, deadline);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
-        T acc = T(0);
+        // two accumulators halve the dependent FMA chain (64 cycles per FP64 FMA)
+        T acc0 = T(0), acc1 = T(0);
 #pragma unroll
-        for (int x = 0; x < M; ++x) {
+        for (int x = 0; x < M; x += 2) {
             if (x >= most) break;
-            if (x < cnt) acc = fma(u[x], sh[j[x]], acc);
+            if (x < cnt) acc0 = fma(u[x], sh[j[x]], acc0);
+            if (x + 1 < cnt) acc1 = fma(u[x + 1], sh[j[x + 1]], acc1);
         }
-        for (int q = a + sl + M * G; q < c; q += G) acc = fma(__ldg(xv + q), sh[__ldg(xj + q)], acc);
-        acc = sum_group<G>(acc);
+        for (int q = a + sl + M * G; q < c; q += G) acc0 = fma(__ldg(xv + q), sh[__ldg(xj + q)], acc0);
+        const T acc = sum_group<G>(acc0 + acc1);
         T v = T(0);
         if (sl == 0 && i >= 0) {
-            v = (t - acc) * rd;
+            v = fma(-rd, acc, t);
             sh[i - s] = v;
         }
         // the count is raised before the global stores, so its fence waits only for
@@ -208,18 +227,19 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
 
 // ----------------------------------------------------------------- backward tasks
 
-// E'(k, c): w_i = sum of U_im z_m over the entries of row i with m beyond the row's
-// range (a suffix of the row, columns ascending), for rows [lo, hi).
+// E (backward): w_i = sum of U_im z_m over the entries of row i with m beyond the
+// row's range (a suffix of the row, columns ascending), for the rows at order
+// positions [lo, hi).
 template <int G, typename T>
 __device__ void bwd_external(const SolvePlan& S, const T* __restrict__ uv, const T* zv, T* w, int lo, int hi) {
     constexpr int R = 32 / G;
     const int lane = threadIdx.x & 31, sub = lane / G, sl = lane % G;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int base = lo + warp * R; base < hi; base += nw * R) {
-        const int i = base + sub;
+        const int i = base + sub < hi ? __ldg(S.lb_ord + base + sub) : -1;
         T acc = T(0);
         long long a = 0, b = 0;
-        if (i < hi) {
+        if (i >= 0) {
             a = __ldg(S.urp + i) + 1 + __ldg(S.sb_nint + i);
             b = __ldg(S.urp + i + 1);
             for (long long q = a + sl; q < b; q += G) acc = fma(__ldg(uv + q), ldcg(zv + __ldg(S.ucol + q)), acc);
@@ -231,27 +251,28 @@ __device__ void bwd_external(const SolvePlan& S, const T* __restrict__ uv, const
 
 // ------------------------------------------------------------------ the two grids
 
-// Claims the next task of `tasks`; thread 0 waits for its range counter.  Returns the
-// task index, or -1 when the list is exhausted or the solve was aborted.
 __device__ __forceinline__ unsigned smid() {
     unsigned r;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
     return r;
 }
 
-__device__ int claim_task(int* claim_ctr, const int4* tasks, int ntasks, const int* pend, const int* epend,
-                          int* abort_word, unsigned long long deadline, int* s_task, int* s_claim,
-                          int* s_done, unsigned long long* trace) {
+// Claims the next task; thread 0 waits until its in-degree is zero.  Returns the task
+// index, or -1 when the list is exhausted or the solve was aborted.
+__device__ int claim_task(int* claim_ctr, int ntasks, const int* indeg, int* taken, int* abort_word,
+                          unsigned long long deadline, int* s_task, int* s_claim, int* s_done,
+                          unsigned long long* trace) {
     if (threadIdx.x == 0) {
         int t = -1;
         if (!aborted(abort_word)) {
-            t = atomicAdd(claim_ctr, 1);
+            do {  // tasks already taken as a continuation are skipped
+                t = atomicAdd(claim_ctr, 1);
+            } while (t < ntasks && atomicExch(taken + t, 1) != 0);
             if (t >= ntasks) {
                 t = -1;
             } else {
                 const unsigned long long t0 = gclock();
-                const int4 tk = tasks[t];
-                if (!await_zero(tk.x == 0 ? pend + tk.y : epend + tk.y, abort_word, deadline)) t = -1;
+                if (!await_zero(indeg + t, abort_word, deadline)) t = -1;
                 if (trace && t >= 0) {
                     trace[4 * t] = t0;
                     trace[4 * t + 1] = gclock();
@@ -267,6 +288,38 @@ __device__ int claim_task(int* claim_ctr, const int4* tasks, int ntasks, const i
     return *s_task;
 }
 
+// After a task: its results are made visible, then its successors are released.  If
+// the task was an L part whose range's next part is now ready and not yet taken, the
+// CTA takes it (returned; -1 otherwise) and runs it with the shared-memory state it
+// already holds.
+__device__ __forceinline__ int release(int t, bool is_l, const int* succ_ptr, const int* succ, const int* next,
+                                       int* indeg, int* taken, unsigned long long* trace, int* s_task,
+                                       int* s_claim) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (trace) trace[4 * t + 2] = gclock();
+        const int a = __ldg(succ_ptr + t), b = __ldg(succ_ptr + t + 1);
+        for (int q = a; q < b; ++q) atomicSub(indeg + __ldg(succ + q), 1);
+        int nx = is_l ? __ldg(next + t) : -1;
+        if (nx >= 0 && !(*reinterpret_cast<volatile int*>(indeg + nx) == 0 && atomicExch(taken + nx, 1) == 0))
+            nx = -1;
+        if (nx >= 0) {
+            __threadfence();
+            if (trace) {
+                const unsigned long long now = gclock();
+                trace[4 * nx] = now;
+                trace[4 * nx + 1] = now;
+                trace[4 * nx + 3] = (unsigned long long)nx | ((unsigned long long)smid() << 32);
+            }
+        }
+        *s_task = nx;
+        *s_claim = 0;
+    }
+    __syncthreads();
+    return *s_task;
+}
+
 template <int G, typename T>
 __global__ void __launch_bounds__(kDagThreads)
 forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all, const double* __restrict__ r,
@@ -275,29 +328,25 @@ forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all
     T* sh = reinterpret_cast<T*>(smem);
     __shared__ int s_task, s_claim, s_done;
     const unsigned long long deadline = gclock() + timeout_ns;
-    int* pend = S.dag_cnt;
-    int* epend = S.dag_cnt + S.nranges;
+    int* indeg = S.dag_indeg;
+    int* taken = S.dag_taken;
+    int t = -1;
+    bool cont = false;
     for (;;) {
-        const int t = claim_task(S.counter + 0, S.ftask, S.nftask, pend, epend, S.counter + 2, deadline,
-                                 &s_task, &s_claim, &s_done, S.trace);
+        if (t < 0) {
+            t = claim_task(S.counter + 0, S.nftask, indeg, taken, S.counter + 2, deadline, &s_task, &s_claim,
+                           &s_done, S.trace);
+            cont = false;
+        }
         if (t < 0) break;
         const int4 tk = S.ftask[t];
         if (tk.x == 0)
             fwd_external<G, T>(S, uvt, y, w, tk.z, tk.w);
         else
             solve_local<G, T, false>(S, static_cast<const T*>(S.xf_val), rd_all, r, nullptr, y, nullptr, w, tk.y,
-                                     tk.z, sh, &s_claim, &s_done, deadline);
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (S.trace) S.trace[4 * t + 2] = gclock();
-            if (tk.x == 0) {
-                atomicSub(epend + tk.y, 1);
-            } else {
-                const int a = __ldg(S.fsucc_ptr + tk.y), b = __ldg(S.fsucc_ptr + tk.y + 1);
-                for (int q = a; q < b; ++q) atomicSub(pend + __ldg(S.fsucc + q), 1);
-            }
-        }
+                                     tk.z, tk.w, sh, &s_claim, &s_done, cont, deadline);
+        t = release(t, tk.x == 1, S.f_succ_ptr, S.f_succ, S.f_next, indeg, taken, S.trace, &s_task, &s_claim);
+        cont = t >= 0;
     }
 }
 
@@ -309,30 +358,26 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
     T* sh = reinterpret_cast<T*>(smem);
     __shared__ int s_task, s_claim, s_done;
     const unsigned long long deadline = gclock() + timeout_ns;
-    int* pend = S.dag_cnt + 2 * S.nranges;
-    int* epend = S.dag_cnt + 3 * S.nranges;
+    int* indeg = S.dag_indeg + S.nftask;
+    int* taken = S.dag_taken + S.nftask;
+    unsigned long long* tr = S.trace ? S.trace + 4 * size_t(S.nftask) : nullptr;
+    int t = -1;
+    bool cont = false;
     for (;;) {
-        unsigned long long* tr = S.trace ? S.trace + 4 * size_t(S.nftask) : nullptr;
-        const int t = claim_task(S.counter + 1, S.btask, S.nbtask, pend, epend, S.counter + 2, deadline,
-                                 &s_task, &s_claim, &s_done, tr);
+        if (t < 0) {
+            t = claim_task(S.counter + 1, S.nbtask, indeg, taken, S.counter + 2, deadline, &s_task, &s_claim,
+                           &s_done, tr);
+            cont = false;
+        }
         if (t < 0) break;
         const int4 tk = S.btask[t];
         if (tk.x == 0)
             bwd_external<G, T>(S, uv, zv, w, tk.z, tk.w);
         else
             solve_local<G, T, true>(S, static_cast<const T*>(S.xb_val), rd_all, nullptr, y, zv, z, w, tk.y, tk.z,
-                                    sh, &s_claim, &s_done, deadline);
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (tr) tr[4 * t + 2] = gclock();
-            if (tk.x == 0) {
-                atomicSub(epend + tk.y, 1);
-            } else {
-                const int a = __ldg(S.bsucc_ptr + tk.y), b = __ldg(S.bsucc_ptr + tk.y + 1);
-                for (int q = a; q < b; ++q) atomicSub(pend + __ldg(S.bsucc + q), 1);
-            }
-        }
+                                    tk.w, sh, &s_claim, &s_done, cont, deadline);
+        t = release(t, tk.x == 1, S.b_succ_ptr, S.b_succ, S.b_next, indeg, taken, tr, &s_task, &s_claim);
+        cont = t >= 0;
     }
 }
 
@@ -431,8 +476,10 @@ cudaError_t dag_blocks_per_sm(int lanes, int dtype, int max_range_rows, int* blo
 cudaError_t launch_apply_dag(const SolvePlan& S, const double* r, double* z, unsigned long long timeout_ns,
                              int grid, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1) {
     if (S.n == 0) return cudaSuccess;
-    cudaError_t e = cudaMemcpyAsync(S.dag_cnt, S.dag_cnt0, 4 * size_t(S.nranges) * sizeof(int),
+    cudaError_t e = cudaMemcpyAsync(S.dag_indeg, S.dag_indeg0, size_t(S.nftask + S.nbtask) * sizeof(int),
                                     cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(S.dag_taken, 0, size_t(S.nftask + S.nbtask) * sizeof(int), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(S.counter, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;

@@ -3,17 +3,19 @@
 // The factor's 2D block structure (Section 3.2) also organises the solves with L and
 // L^T: every block row (a range of rows) is a unit of work.  For the forward solve
 // L y = r, a row i of range k needs y_p for the entries U_pi of column i of U; the
-// entries with p in an earlier range are "external", the others "internal".  Two task
-// kinds per range:
-//   E(k, c)  sums the external entries of a chunk of k's rows (many CTAs in parallel)
-//            once every range k depends on has finished;
-//   L(k)     one CTA solves k's rows with the internal entries, rows taken in local
-//            dependence-level order, the range's results held in shared memory.
-// The backward solve L^T z = y is the mirror image (external = entries of row i in a
-// later range).  Nested-dissection leaves have no external entries in the forward
-// solve, so they start at once; separators wait for their subdomains.  Tasks are
-// claimed in a fixed order: ascending start time of an as-soon-as-possible schedule
-// under a simple cost model, which is a topological order of the task DAG.
+// entries with p in an earlier range are "external", the others "internal".  A
+// range's rows are taken in local dependence-level order and cut into parts of a few
+// levels; two task kinds per part:
+//   E  sums the external entries of a chunk of the part's rows (many CTAs in
+//      parallel) once the parts holding their source rows have finished;
+//   L  one CTA solves the part's rows with the internal entries, after the range's
+//      previous part, the range's results held in shared memory.
+// So a separator's first levels run while its subdomains are still finishing their
+// last ones.  The backward solve L^T z = y is the mirror image (external = entries of
+// row i in a later range).  Nested-dissection leaves have no external entries in the
+// forward solve: each is one L task and they start at once.  Tasks are claimed in a
+// fixed order: ascending start time of an as-soon-as-possible schedule under a simple
+// cost model, which is a topological order of the task DAG.
 #include <omp.h>
 
 #include <algorithm>
@@ -29,8 +31,9 @@ namespace {
 constexpr double kTaskStartUs = 2.0;    // claim, dependence check, release
 constexpr double kLevelUs = 0.25;       // one local dependence level in shared memory
 constexpr double kFmaUs = 1.0e-3;       // one FP64 multiply-add of a CTA sharing its SM
-constexpr int64_t kChunkEntries = 8192; // external entries per E task, at most
-constexpr int kChunkRows = 512;         // rows per E task, at most
+constexpr int64_t kChunkEntries = 4096; // external entries per E task, at most
+constexpr int kChunkRows = 256;         // order positions per E task, at most
+constexpr int kPartLevels = 16;         // local levels per L task of a range with external entries
 
 // Rows of one range sorted by local level, each level's run padded with -1 to a
 // multiple of kClaimPad; appended to out.  need receives, per position, the number of
@@ -90,8 +93,6 @@ void build_solve_dag(HostPlan& P, int nthr) {
     P.sf_split.assign(n, 0);
     P.sb_nint.assign(n, 0);
     std::vector<int32_t> lf(n, 0), lb(n, 0);
-    std::vector<int64_t> int_f(nb, 0), int_b(nb, 0);
-    std::vector<int32_t> dep_f(nb, 0), dep_b(nb, 0);
     P.max_range_rows = 0;
     for (int32_t k = 0; k < nb; ++k)
         P.max_range_rows = std::max(P.max_range_rows, P.ranges[k + 1] - P.ranges[k]);
@@ -100,8 +101,6 @@ void build_solve_dag(HostPlan& P, int nthr) {
 #pragma omp parallel for num_threads(nthr) schedule(dynamic, 4)
     for (int32_t k = 0; k < nb; ++k) {
         const int32_t s = P.ranges[k], e = P.ranges[k + 1];
-        int64_t fi = 0, bi = 0;
-        int32_t df = 0, db = 0;
         for (int32_t i = s; i < e; ++i) {
             // column list of i: pivot rows ascending, so the internal ones are a suffix
             int32_t a = P.cptr[i];
@@ -111,8 +110,6 @@ void build_solve_dag(HostPlan& P, int nthr) {
             int32_t d = 0;
             for (int32_t q = a; q < b; ++q) d = std::max(d, lf[P.csc[q].x] + 1);
             lf[i] = d;
-            df = std::max(df, d);
-            fi += b - a;
         }
         for (int32_t i = e - 1; i >= s; --i) {
             // row i: columns ascending after the diagonal, the internal ones a prefix
@@ -125,13 +122,7 @@ void build_solve_dag(HostPlan& P, int nthr) {
             }
             P.sb_nint[i] = int32_t(q - a);
             lb[i] = d;
-            db = std::max(db, d);
-            bi += q - a;
         }
-        int_f[k] = fi;
-        int_b[k] = bi;
-        dep_f[k] = df + 1;
-        dep_b[k] = db + 1;
     }
 
     P.lf_ptr.assign(nb + 1, 0);
@@ -160,94 +151,131 @@ void build_solve_dag(HostPlan& P, int nthr) {
         },
         P.xb);
 
-    // range dependences from the block pattern (upper, diagonal block first): block
-    // (k, j), j > k, means j needs k in the forward solve and k needs j backward
-    std::vector<int32_t> bcnt(nb + 1, 0);
-    P.fsucc_ptr.assign(nb + 1, 0);
-    P.fsucc.clear();
-    for (int32_t k = 0; k < nb; ++k) {
-        for (int64_t q = P.bptr[k]; q < P.bptr[k + 1]; ++q) {
-            const int32_t j = P.bcol[q];
-            if (j == k) continue;
-            P.fsucc.push_back(j);
-            ++bcnt[j + 1];
-        }
-        P.fsucc_ptr[k + 1] = int32_t(P.fsucc.size());
-    }
-    P.bsucc_ptr.assign(nb + 1, 0);
-    for (int32_t j = 0; j < nb; ++j) P.bsucc_ptr[j + 1] = P.bsucc_ptr[j] + bcnt[j + 1];
-    P.bsucc.assign(P.fsucc.size(), 0);
-    {
-        std::vector<int32_t> fill(P.bsucc_ptr.begin(), P.bsucc_ptr.end() - 1);
-        for (int32_t k = 0; k < nb; ++k)
-            for (int32_t q = P.fsucc_ptr[k]; q < P.fsucc_ptr[k + 1]; ++q)
-                P.bsucc[fill[P.fsucc[q]]++] = k;  // ascending k within each list
-    }
-
-    // tasks, counters and the as-soon-as-possible claim order, one direction at a time
-    P.dag_cnt0.assign(4 * size_t(nb), 0);
-    auto build = [&](bool fwd, std::vector<int4>& out) {
-        struct T { double start, cost; int4 t; };
-        std::vector<T> tasks;
-        std::vector<double> done(nb, 0.0);  // finish time of L(k)
-        std::vector<int32_t> order(nb);
-        std::iota(order.begin(), order.end(), 0);
-        if (!fwd) std::reverse(order.begin(), order.end());
-        int32_t* pend = P.dag_cnt0.data() + (fwd ? 0 : 2 * size_t(nb));
-        int32_t* epend = pend + nb;
-        for (int32_t k : order) {
-            const int32_t s = P.ranges[k], e = P.ranges[k + 1];
-            // ranges k depends on: all finished earlier in this direction's range order
-            double ready = 0.0;
-            if (fwd) {
-                for (int32_t q = P.bsucc_ptr[k]; q < P.bsucc_ptr[k + 1]; ++q)
-                    ready = std::max(ready, done[P.bsucc[q]]);
-                pend[k] = P.bsucc_ptr[k + 1] - P.bsucc_ptr[k];
-            } else {
-                for (int32_t q = P.fsucc_ptr[k]; q < P.fsucc_ptr[k + 1]; ++q)
-                    ready = std::max(ready, done[P.fsucc[q]]);
-                pend[k] = P.fsucc_ptr[k + 1] - P.fsucc_ptr[k];
-            }
-            // external entries of each row, cut into chunks
-            double lstart = ready;
-            int32_t chunks = 0;
-            if (pend[k] > 0) {
-                int32_t lo = s;
-                int64_t acc = 0;
-                for (int32_t i = s; i < e; ++i) {
-                    const int64_t ext = fwd ? int64_t(P.sf_split[i] - P.cptr[i])
-                                            : (P.urp[i + 1] - P.urp[i] - 1) - P.sb_nint[i];
-                    acc += ext;
-                    if (i + 1 == e || acc >= kChunkEntries || i + 1 - lo >= kChunkRows) {
-                        if (acc > 0) {
-                            const double c = kTaskStartUs + kFmaUs * double(acc);
-                            tasks.push_back({ready, c, make_int4(0, k, lo, i + 1)});
-                            lstart = std::max(lstart, ready + c);
-                            ++chunks;
-                        }
-                        lo = i + 1;
-                        acc = 0;
-                    }
+    // tasks, their dependences and the claim order, one direction at a time.  A range
+    // whose rows have entries outside it is cut into parts of kPartLevels local levels
+    // (one L task each, after the previous part); each part's external sums form E
+    // tasks (chunks of at most kChunkEntries entries / kChunkRows order positions) that
+    // depend on the L tasks holding their source rows.  A range without external
+    // entries is one L task.  Claim order: ascending start of an as-soon-as-possible
+    // schedule under the cost model (a topological order).
+    auto build = [&](bool fwd, SolveTasks& out) {
+        struct Tk {
+            double start, cost;
+            int4 t;
+            std::vector<int32_t> preds;
+        };
+        std::vector<Tk> tk;
+        std::vector<int32_t> row_L(n, -1);  // L task holding each row
+        const std::vector<int32_t>& lev = fwd ? lf : lb;
+        const std::vector<int32_t>& optr = fwd ? P.lf_ptr : P.lb_ptr;
+        const std::vector<int32_t>& ord = fwd ? P.lf_ord : P.lb_ord;
+        auto ext_of = [&](int32_t i) -> int64_t {
+            return fwd ? int64_t(P.sf_split[i] - P.cptr[i]) : (P.urp[i + 1] - P.urp[i] - 1) - P.sb_nint[i];
+        };
+        auto int_of = [&](int32_t i) -> int64_t {
+            return fwd ? int64_t(P.cptr[i + 1] - P.sf_split[i]) : int64_t(P.sb_nint[i]);
+        };
+        auto finish = [&](int32_t t) { return tk[t].start + tk[t].cost; };
+        for (int32_t kk = 0; kk < nb; ++kk) {
+            const int32_t k = fwd ? kk : nb - 1 - kk;
+            const int32_t base = optr[k], end = optr[k + 1];
+            bool any_ext = false;
+            for (int32_t i = P.ranges[k]; i < P.ranges[k + 1] && !any_ext; ++i) any_ext = ext_of(i) > 0;
+            int32_t prevL = -1;
+            int32_t lo = base;
+            while (lo < end) {
+                // the part: whole levels [lev(lo), lev(lo) + kPartLevels) (all levels when
+                // the range has no external entries); padding carries its level
+                int32_t l0 = -1, hi = lo;
+                int32_t lastlev = -1;
+                for (; hi < end; ++hi) {
+                    const int32_t i = ord[hi];
+                    if (i < 0) continue;
+                    if (l0 < 0) l0 = lev[i];
+                    if (any_ext && lev[i] >= l0 + kPartLevels) break;
+                    lastlev = lev[i];
                 }
+                // E tasks of the part
+                std::vector<int32_t> es;
+                int32_t c0 = lo;
+                int64_t acc = 0;
+                std::vector<int32_t> preds;
+                auto close_chunk = [&](int32_t c1) {
+                    if (acc > 0) {
+                        std::sort(preds.begin(), preds.end());
+                        preds.erase(std::unique(preds.begin(), preds.end()), preds.end());
+                        double st = 0.0;
+                        for (int32_t q : preds) st = std::max(st, finish(q));
+                        tk.push_back({st, kTaskStartUs + kFmaUs * double(acc), make_int4(0, k, c0, c1), preds});
+                        es.push_back(int32_t(tk.size()) - 1);
+                    }
+                    c0 = c1;
+                    acc = 0;
+                    preds.clear();
+                };
+                for (int32_t q = lo; q < hi; ++q) {
+                    const int32_t i = ord[q];
+                    if (i >= 0 && ext_of(i) > 0) {
+                        acc += ext_of(i);
+                        if (fwd) {
+                            for (int32_t e = P.cptr[i]; e < P.sf_split[i]; ++e) preds.push_back(row_L[P.csc[e].x]);
+                        } else {
+                            for (int64_t e = P.urp[i] + 1 + P.sb_nint[i]; e < P.urp[i + 1]; ++e)
+                                preds.push_back(row_L[P.ucol[e]]);
+                        }
+                    }
+                    if (acc >= kChunkEntries || q + 1 - c0 >= kChunkRows) close_chunk(q + 1);
+                }
+                close_chunk(hi);
+                // the L task
+                std::vector<int32_t> lp(es);
+                if (prevL >= 0) lp.push_back(prevL);
+                double st = 0.0;
+                for (int32_t q : lp) st = std::max(st, finish(q));
+                int64_t inner = 0;
+                for (int32_t q = lo; q < hi; ++q)
+                    if (ord[q] >= 0) inner += int_of(ord[q]);
+                const double cost = kTaskStartUs + kLevelUs * double(lastlev - l0 + 1) + kFmaUs * double(inner) +
+                                    kFmaUs * double(lo - base);  // reload of the earlier parts' results
+                tk.push_back({st, cost, make_int4(1, k, lo, hi), lp});
+                prevL = int32_t(tk.size()) - 1;
+                for (int32_t q = lo; q < hi; ++q)
+                    if (ord[q] >= 0) row_L[ord[q]] = prevL;
+                lo = hi;
             }
-            epend[k] = chunks;
-            const double lc = kTaskStartUs + kLevelUs * double(fwd ? dep_f[k] : dep_b[k]) +
-                              kFmaUs * double(fwd ? int_f[k] : int_b[k]);
-            tasks.push_back({lstart, lc, make_int4(1, k, s, e)});
-            done[k] = lstart + lc;
         }
-        // ascending start; at equal start, the longer task first; then generation order
-        std::vector<size_t> idx(tasks.size());
-        std::iota(idx.begin(), idx.end(), size_t(0));
-        std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
-            if (tasks[a].start != tasks[b].start) return tasks[a].start < tasks[b].start;
-            return tasks[a].cost > tasks[b].cost;
+        // claim order: ascending start; at equal start, the longer task first
+        const size_t nt = tk.size();
+        std::vector<int32_t> idx(nt), pos(nt);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+            if (tk[x].start != tk[y].start) return tk[x].start < tk[y].start;
+            return tk[x].cost > tk[y].cost;
         });
-        out.resize(tasks.size());
-        for (size_t q = 0; q < idx.size(); ++q) out[q] = tasks[idx[q]].t;
+        for (size_t q = 0; q < nt; ++q) pos[idx[q]] = int32_t(q);
+        out.task.resize(nt);
+        out.indeg0.assign(nt, 0);
+        std::vector<int32_t> cnt(nt + 1, 0);
+        for (size_t q = 0; q < nt; ++q) {
+            out.task[q] = tk[idx[q]].t;
+            out.indeg0[q] = int32_t(tk[idx[q]].preds.size());
+            for (int32_t pr : tk[idx[q]].preds) ++cnt[pos[pr] + 1];
+        }
+        out.succ_ptr.assign(nt + 1, 0);
+        for (size_t q = 0; q < nt; ++q) out.succ_ptr[q + 1] = out.succ_ptr[q] + cnt[q + 1];
+        out.succ.assign(out.succ_ptr[nt], 0);
+        std::vector<int32_t> fill(out.succ_ptr.begin(), out.succ_ptr.end() - 1);
+        for (size_t q = 0; q < nt; ++q)
+            for (int32_t pr : tk[idx[q]].preds) out.succ[fill[pos[pr]]++] = int32_t(q);
+        // next part of the same range (its L task lists the previous part as a predecessor)
+        out.next.assign(nt, -1);
+        for (size_t q = 0; q < nt; ++q)
+            if (tk[idx[q]].t.x == 1)
+                for (int32_t pr : tk[idx[q]].preds)
+                    if (tk[pr].t.x == 1) out.next[pos[pr]] = int32_t(q);
     };
-    build(true, P.ftask);
-    build(false, P.btask);
+    build(true, P.fs);
+    build(false, P.bs);
 }
 
 }  // namespace ick

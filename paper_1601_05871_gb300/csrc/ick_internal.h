@@ -26,6 +26,14 @@ struct SolveLayout {
     std::vector<int32_t> ptr, j, pos;
 };
 
+// Tasks of one direction of the block-DAG solves, in claim order: (type 0 = E /
+// 1 = L, range, first order position, end order position), in-degrees, successors.
+struct SolveTasks {
+    std::vector<int4> task;
+    std::vector<int32_t> indeg0, succ_ptr, succ;
+    std::vector<int32_t> next;  // per L task: the same range's next part (-1: none; E tasks -1)
+};
+
 // Everything the symbolic phase produces, in host memory.
 struct HostPlan {
     int64_t n = 0, nnz_a = 0, nnz_u = 0;
@@ -67,16 +75,12 @@ struct HostPlan {
     int64_t fwd_depth = 0, bwd_depth = 0;        // levels of the row dependence DAGs
     // block-DAG solves (host_solve.cpp): per row the start of the internal entries
     // (forward: absolute column-list index; backward: count after the diagonal), per
-    // range the padded local orders, the tasks in claim order (type 0 = E, 1 = L;
-    // range; first row; end row), range successors, and the initial counters
-    // [forward pending ranges | forward pending E tasks | backward ... | backward ...]
+    // range the padded local orders, and each direction's tasks
     std::vector<int32_t> sf_split, sb_nint;
     std::vector<int32_t> lf_ptr, lf_ord, lb_ptr, lb_ord;
     std::vector<int32_t> lf_need, lb_need;  // per order position: rows of lower levels
     SolveLayout xf, xb;                     // forward / backward internal entries
-    std::vector<int4> ftask, btask;
-    std::vector<int32_t> fsucc_ptr, fsucc, bsucc_ptr, bsucc;
-    std::vector<int32_t> dag_cnt0;
+    SolveTasks fs, bs;
     int32_t max_range_rows = 0;
     int64_t total_items = 0;
     int64_t critical_path = 0;
@@ -157,6 +161,7 @@ struct SolvePlan {
     // block-DAG solves (blocksolve.cu); see HostPlan for the meaning of the arrays
     int solve_mode;        // 0: block-DAG solves, 1: row-level solves in level order
     int nranges, max_range_rows, nftask, nbtask, noff;
+    const int* ranges;     // nranges + 1 row boundaries of the block rows
     const int* sf_split;
     const int* sb_nint;
     const int* lf_ptr;
@@ -178,14 +183,17 @@ struct SolvePlan {
     int nxf, nxb;
     void* uvt;             // factor values in column-list (csc) order, refreshed after each
                            // numeric phase: the forward solve reads them contiguously
-    const int4* ftask;
+    const int4* ftask;     // tasks in claim order: (0 = E / 1 = L, range, first, end order position)
     const int4* btask;
-    const int* fsucc_ptr;
-    const int* fsucc;
-    const int* bsucc_ptr;
-    const int* bsucc;
-    const int* dag_cnt0;   // initial range counters, copied into dag_cnt before each apply
-    int* dag_cnt;
+    const int* f_succ_ptr; // successors of each task (indices into the same direction's list)
+    const int* f_succ;
+    const int* b_succ_ptr;
+    const int* b_succ;
+    const int* dag_indeg0; // in-degrees, forward tasks then backward, copied into dag_indeg
+    int* dag_indeg;        // before each apply
+    const int* f_next;     // per task: the same range's next L part, or -1
+    const int* b_next;
+    int* dag_taken;        // per task (forward then backward): 1 once a CTA has taken it
     void* dag_w;           // external sums of the rows (n values of the solve type)
     unsigned long long* trace;  // NULL, or 4 words per task: forward tasks, then backward
 };

@@ -330,17 +330,19 @@ def ic_get_blocks(h):
 
 def ic_get_solve_tasks(h, backward=False):
     """Block-DAG solve plan of one direction: dict with tasks (ntasks x 4: type 0 = E /
-    1 = L, range, first row, end row) in claim order, counters (2 x nranges: ranges
-    waited for, E tasks), succ_ptr/succ, split (per row) and order_ptr/order."""
+    1 = L, range, first and end order position) in claim order, counters (in-degree of
+    each task), succ_ptr/succ (tasks each task releases), split (per row),
+    order_ptr/order and need."""
     L = load()
     st = ic_stats(h)
     n, nr = st["n"], st["nranges"]
     nt = np.zeros(1, dtype=np.int64)
     _check(L.ic_get_solve_tasks(h.ptr, int(bool(backward)), _p(nt), None, None, None, None, None, None, None,
                                 None))
-    tasks = np.empty((max(1, int(nt[0])), 4), dtype=np.int32)
-    cnt = np.empty((2, max(1, nr)), dtype=np.int32)
-    sptr = np.empty(nr + 1, dtype=np.int32)
+    ntk = int(nt[0])
+    tasks = np.empty((max(1, ntk), 4), dtype=np.int32)
+    cnt = np.empty(max(1, ntk), dtype=np.int32)
+    sptr = np.empty(ntk + 1, dtype=np.int32)
     optr = np.empty(nr + 1, dtype=np.int32)
     split = np.empty(max(1, n), dtype=np.int32)
     _check(L.ic_get_solve_tasks(h.ptr, int(bool(backward)), None, None, _p(cnt), _p(sptr), None, None, _p(optr),
@@ -350,7 +352,7 @@ def ic_get_solve_tasks(h, backward=False):
     need = np.empty(max(1, int(optr[-1])), dtype=np.int32)
     _check(L.ic_get_solve_tasks(h.ptr, int(bool(backward)), None, _p(tasks), None, None, _p(succ), _p(split), None,
                                 _p(order), _p(need)))
-    return {"tasks": tasks[: int(nt[0])], "counters": cnt[:, :nr], "succ_ptr": sptr, "succ": succ[: int(sptr[-1])],
+    return {"tasks": tasks[:ntk], "counters": cnt[:ntk], "succ_ptr": sptr, "succ": succ[: int(sptr[-1])],
             "split": split[:n], "order_ptr": optr, "order": order[: int(optr[-1])], "need": need[: int(optr[-1])]}
 
 

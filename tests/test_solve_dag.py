@@ -118,31 +118,57 @@ def _check_direction(h, backward):
         else:
             want_pos = np.arange(urp[i] + 1, urp[i] + 1 + split[i])
         assert np.array_equal(np.sort(x["pos"][a:c]), want_pos)
-    # tasks: one L per range, E chunks cover exactly the rows with external entries
-    tasks, cnt = d["tasks"], d["counters"].copy()
-    assert np.sum(tasks[:, 0] == 1) == nr
-    for k in range(nr):
-        e_rows = np.zeros(rg[k + 1] - rg[k], dtype=int)
-        for t in tasks[(tasks[:, 0] == 0) & (tasks[:, 1] == k)]:
-            assert rg[k] <= t[2] < t[3] <= rg[k + 1]
-            e_rows[t[2] - rg[k]:t[3] - rg[k]] += 1
-        assert e_rows.max(initial=0) <= 1
-        assert np.sum((tasks[:, 0] == 0) & (tasks[:, 1] == k)) == cnt[1, k]
-        for i in range(rg[k], rg[k + 1]):
-            ext = (split[i] > cptr[i]) if not backward else (split[i] < urp[i + 1] - urp[i] - 1)
-            if ext:
-                assert e_rows[i - rg[k]] == 1
-    # sequential execution in claim order never waits
+    # tasks: per range, L parts cover its order positions contiguously and in order; E
+    # tasks cover exactly the rows with external entries, each inside one part
+    tasks, indeg = d["tasks"], d["counters"]
     sptr, succ = d["succ_ptr"], d["succ"]
-    cnt = d["counters"].copy()
-    for t in tasks:
-        if t[0] == 0:
-            assert cnt[0, t[1]] == 0, t
-            cnt[1, t[1]] -= 1
+    has_ext = np.array([(split[i] > cptr[i]) if not backward else (split[i] < urp[i + 1] - urp[i] - 1)
+                        for i in range(n)])
+    part_of = np.full(n, -1)
+    for k in range(nr):
+        Ls = sorted([t for t in range(len(tasks)) if tasks[t, 0] == 1 and tasks[t, 1] == k], key=lambda t: tasks[t, 2])
+        assert Ls and tasks[Ls[0], 2] == optr[k] and tasks[Ls[-1], 3] == optr[k + 1]
+        for a_, b_ in zip(Ls, Ls[1:]):
+            assert tasks[a_, 3] == tasks[b_, 2]
+        for t in Ls:
+            lo, hi = tasks[t, 2], tasks[t, 3]
+            rows = order[lo:hi]
+            part_of[rows[rows >= 0]] = t
+            if lo > optr[k]:   # a part starts on a level boundary
+                assert d["need"][lo] == np.sum(order[optr[k]:lo] >= 0)
+        if not has_ext[rg[k]:rg[k + 1]].any():
+            assert len(Ls) == 1
+    covered = np.zeros(n, dtype=int)
+    for t in range(len(tasks)):
+        if tasks[t, 0] == 0:
+            lo, hi = tasks[t, 2], tasks[t, 3]
+            rows = order[lo:hi]
+            rows = rows[rows >= 0]
+            covered[rows[has_ext[rows]]] += 1
+            assert len(set(part_of[rows])) == 1
+    assert np.array_equal(covered, has_ext.astype(int))
+    # sequential execution in claim order never meets an unmet counter, and every
+    # dependence of the data is ordered before its use
+    cnt = indeg.copy()
+    done_t = np.zeros(len(tasks), dtype=bool)
+    for t in range(len(tasks)):
+        assert cnt[t] == 0, t
+        lo, hi = tasks[t, 2], tasks[t, 3]
+        rows = order[lo:hi]
+        rows = rows[rows >= 0]
+        if tasks[t, 0] == 0:
+            for i in rows[has_ext[rows]]:
+                srcs = cp[cptr[i]:split[i]] if not backward else ucol[urp[i] + 1 + split[i]:urp[i + 1]]
+                assert done_t[part_of[srcs]].all(), (t, i)
         else:
-            assert cnt[1, t[1]] == 0 and cnt[0, t[1]] == 0, t
-            for j in succ[sptr[t[1]]:sptr[t[1] + 1]]:
-                cnt[0, j] -= 1
+            k = tasks[t, 1]
+            earlier = order[optr[k]:lo]
+            assert done_t[part_of[earlier[earlier >= 0]]].all()
+            mine = [u for u in range(len(tasks)) if tasks[u, 0] == 0 and tasks[u, 1] == k and lo <= tasks[u, 2] < hi]
+            assert done_t[mine].all(), (t, mine)
+        done_t[t] = True
+        for s_ in succ[sptr[t]:sptr[t + 1]]:
+            cnt[s_] -= 1
     assert np.all(cnt == 0)
     return d
 
@@ -166,7 +192,9 @@ def _execute(h, uval, b, backward, rhs):
     w = np.zeros(n)
     for t in d["tasks"]:
         if t[0] == 0:
-            for i in range(t[2], t[3]):
+            for i in order[t[2]:t[3]]:
+                if i < 0 or not ((split[i] > cptr[i]) if not backward else (split[i] < urp[i + 1] - urp[i] - 1)):
+                    continue
                 if not backward:
                     q = np.arange(cptr[i], split[i])
                     vals = x[cp[q]]
@@ -179,7 +207,7 @@ def _execute(h, uval, b, backward, rhs):
                     w[i] = np.dot(uval[q], vals)
         else:
             s = rg[t[1]]
-            for i in order[optr[t[1]]:optr[t[1] + 1]]:
+            for i in order[t[2]:t[3]]:
                 if i < 0:
                     continue
                 a, c = lay["ptr"][i], lay["ptr"][i + 1]
@@ -217,10 +245,11 @@ def test_solve_plan_batch_union(orc):
                               block_rows=48, host_only=1)
     for backward in (False, True):
         d = _check_direction(h, backward)
-        # the systems are independent: no range releases a range of another system
+        # the systems are independent: no task releases a task of another system
         rg, _, _ = ick.ic_get_blocks(h)
         off = ick.ic_batch_info(h)
         sys_of = np.searchsorted(off, rg[:-1], side="right") - 1
-        for k in range(len(rg) - 1):
-            for j in d["succ"][d["succ_ptr"][k]:d["succ_ptr"][k + 1]]:
-                assert sys_of[j] == sys_of[k]
+        tk = d["tasks"]
+        for t in range(len(tk)):
+            for u in d["succ"][d["succ_ptr"][t]:d["succ_ptr"][t + 1]]:
+                assert sys_of[tk[u, 1]] == sys_of[tk[t, 1]]
