@@ -60,7 +60,7 @@ typedef struct {
     int block_rows;    /* [4096] largest block; longer ranges are split evenly; <= 8192 */
     int dtype;         /* [IC_F64] factor precision                                      */
     int warps_per_cta; /* [16] warps in each CTA of the persistent numeric kernel: 8|16  */
-    int rows_per_item; /* [32] target rows per work item of a Herk/Gemm task             */
+    int rows_per_item; /* [16] target rows per work item of a Herk/Gemm task             */
     double timeout_s;  /* [10] bound on every device wait of one call                    */
     double shift_alpha;/* [0] factor B + alpha * diag(B) instead of B                    */
     int exact;         /* [0] 1: each update is a separately rounded multiply then

@@ -130,7 +130,7 @@ ic_opts normalise(const ic_opts* o) {
     if (o) r = *o;
     if (r.block_rows == 0) r.block_rows = 4096;
     if (r.warps_per_cta == 0) r.warps_per_cta = 16;
-    if (r.rows_per_item == 0) r.rows_per_item = 32;
+    if (r.rows_per_item == 0) r.rows_per_item = 16;
     if (r.timeout_s == 0.0) r.timeout_s = 10.0;
     if (r.solve_lanes == 0) r.solve_lanes = r.solve_mode == 0 ? 8 : 32;
     if (r.solve_ctas_per_sm == 0) r.solve_ctas_per_sm = r.solve_mode == 0 ? 2 : 3;
