@@ -35,10 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = "IC(k) factor GFLOP/s & HBM GB/s; PCG time-to-1e-8 vs plain FP64 on GB300"
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (see the alu roofline in the design notes)
 # DRAM bytes (read + write) per launch of a solve kernel, keyed by (side, k, kernel):
-# ncu captures at 48^3 and 64^3 give 14.80 / 15.20 bytes per factor entry (forward /
-# backward) at both sizes, scaled here to the 96^3 factor (57,510,348 entries);
-# profiles/ holds the captures' summary
-SOLVE_TRAFFIC = {(96, 2, "forward_dag"): 14.80 * 57510348, (96, 2, "backward_dag"): 15.20 * 57510348}
+# ncu captures at 48^3 and 64^3 give 14.95 / 14.83 (forward) and 15.51 / 15.18
+# (backward) bytes per factor entry; the 64^3 figures are scaled here to the 96^3
+# factor (57,510,348 entries); profiles/ holds the captures' summary
+SOLVE_TRAFFIC = {(96, 2, "forward_dag"): 14.83 * 57510348, (96, 2, "backward_dag"): 15.18 * 57510348}
 
 
 def parse():
