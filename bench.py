@@ -156,6 +156,24 @@ def run_oracle_sample(side, k, reps=1):
     return h.flops, statistics.median(times)
 
 
+def max_over_ranks(values, world, device="cuda"):
+    """Element-wise maximum of `values` (floats) over the ranks of the default process
+    group (a no-op for one rank): the job's time is its slowest replica's."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(units_per_replica, world, seconds):
+    """Whole-job throughput of `world` replicas each processing units_per_replica in
+    at most `seconds`."""
+    return world * units_per_replica / seconds
+
+
 def reference_arm(a, rank, world):
     if rank != 0:
         return
@@ -400,13 +418,10 @@ def main():
     tim = ick.ic_get_timing(h)
     clocks = clk.summary()
     mean_fact = sum(fact_ms) / len(fact_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms, mean_fact], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, mean_fact = tt.tolist()
+    total_ms, mean_fact = max_over_ranks([total_ms, mean_fact], world)
     ms_per_step = total_ms / a.steps
-    value = world * st["flops"] / (mean_fact * 1e-3) / 1e9
-    hbm = world * st["bytes"] / (mean_fact * 1e-3) / 1e9
+    value = job_rate(st["flops"], world, mean_fact * 1e-3) / 1e9
+    hbm = job_rate(st["bytes"], world, mean_fact * 1e-3) / 1e9
     apply_ms_step = tim["apply_ms"] / a.steps
     mean_kern = sum(kern_ms) / len(kern_ms)
 
@@ -487,11 +502,8 @@ def main():
         for _ in range(a.steps):
             e2e_step()
         t_e2e = (time.perf_counter() - t0) / a.steps
-        if world > 1:
-            tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = tt.item()
-        line["e2e"] = {"value": world * st["flops"] / t_e2e / 1e9, "unit": "GFLOP/s",
+        t_e2e = max_over_ranks([t_e2e], world)[0]
+        line["e2e"] = {"value": job_rate(st["flops"], world, t_e2e) / 1e9, "unit": "GFLOP/s",
                        "h2d_bytes_per_step": int(prob.vals.nbytes + b_host.nbytes),
                        "d2h_bytes_per_step": int(xh.nbytes), "ms_per_step": t_e2e * 1e3,
                        "note": "factor flops / end-to-end step time (copies + factor + PCG)"}
