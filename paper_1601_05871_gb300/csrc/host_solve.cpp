@@ -29,8 +29,8 @@ namespace {
 
 // Cost model of the claim order (microseconds); only the order depends on it.
 constexpr double kTaskStartUs = 2.0;    // claim, dependence check, release
-constexpr double kLevelUs = 0.25;       // one local dependence level in shared memory
-constexpr double kFmaUs = 1.0e-3;       // one FP64 multiply-add of a CTA sharing its SM
+constexpr double kLevelUs = 1.0;        // one local dependence level in shared memory (measured)
+constexpr double kFmaUs = 2.0e-3;       // one external FP64 multiply-add of an E task (measured)
 constexpr int64_t kChunkEntries = 4096; // external entries per E task, at most
 constexpr int kChunkRows = 256;         // order positions per E task, at most
 constexpr int kPartLevels = 16;         // local levels per L task of a range with external entries
@@ -172,9 +172,6 @@ void build_solve_dag(HostPlan& P, int nthr) {
         auto ext_of = [&](int32_t i) -> int64_t {
             return fwd ? int64_t(P.sf_split[i] - P.cptr[i]) : (P.urp[i + 1] - P.urp[i] - 1) - P.sb_nint[i];
         };
-        auto int_of = [&](int32_t i) -> int64_t {
-            return fwd ? int64_t(P.cptr[i + 1] - P.sf_split[i]) : int64_t(P.sb_nint[i]);
-        };
         auto finish = [&](int32_t t) { return tk[t].start + tk[t].cost; };
         for (int32_t kk = 0; kk < nb; ++kk) {
             const int32_t k = fwd ? kk : nb - 1 - kk;
@@ -232,11 +229,8 @@ void build_solve_dag(HostPlan& P, int nthr) {
                 if (prevL >= 0) lp.push_back(prevL);
                 double st = 0.0;
                 for (int32_t q : lp) st = std::max(st, finish(q));
-                int64_t inner = 0;
-                for (int32_t q = lo; q < hi; ++q)
-                    if (ord[q] >= 0) inner += int_of(ord[q]);
-                const double cost = kTaskStartUs + kLevelUs * double(lastlev - l0 + 1) + kFmaUs * double(inner) +
-                                    kFmaUs * double(lo - base);  // reload of the earlier parts' results
+                const double cost = kTaskStartUs + kLevelUs * double(lastlev - l0 + 1) +
+                                    1e-3 * double(lo - base);  // reload of the earlier parts' results
                 tk.push_back({st, cost, make_int4(1, k, lo, hi), lp});
                 prevL = int32_t(tk.size()) - 1;
                 for (int32_t q = lo; q < hi; ++q)
