@@ -130,7 +130,7 @@ __device__ void fwd_external(const SolvePlan& S, const T* __restrict__ uvt, cons
 template <int G, typename T, bool BW>
 __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const T* __restrict__ rd_all,
                             const double* __restrict__ r, const T* y, T* out, double* __restrict__ z, const T* w,
-                            int k, int lo, int hi, T* sh, int* claim, int* done, bool cont,
+                            int k, int lo, int hi, T* sh, int* done, bool cont,
                             unsigned long long deadline) {
     constexpr int R = 32 / G, M = Held<G>::M;
     const int lane = threadIdx.x & 31, sl = lane % G;
@@ -153,7 +153,6 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
     // consecutive warps, i.e. on different SM sub-partitions, whose FP64 units then
     // work in parallel; each warp takes its groups in order, and a group depends only
     // on lower groups, so the waits cannot cycle
-    (void)claim;
     const int nw = blockDim.x >> 5;
     for (int t0 = (threadIdx.x >> 5) * R;; t0 += nw * R) {
         if (t0 >= len) break;
@@ -260,7 +259,7 @@ __device__ __forceinline__ unsigned smid() {
 // Claims the next task; thread 0 waits until its in-degree is zero.  Returns the task
 // index, or -1 when the list is exhausted or the solve was aborted.
 __device__ int claim_task(int* claim_ctr, int ntasks, const int* indeg, int* taken, int* abort_word,
-                          unsigned long long deadline, int* s_task, int* s_claim, int* s_done,
+                          unsigned long long deadline, int* s_task, int* s_done,
                           unsigned long long* trace) {
     if (threadIdx.x == 0) {
         int t = -1;
@@ -281,7 +280,6 @@ __device__ int claim_task(int* claim_ctr, int ntasks, const int* indeg, int* tak
             }
         }
         *s_task = t;
-        *s_claim = 0;
         *s_done = 0;
     }
     __syncthreads();
@@ -293,8 +291,7 @@ __device__ int claim_task(int* claim_ctr, int ntasks, const int* indeg, int* tak
 // CTA takes it (returned; -1 otherwise) and runs it with the shared-memory state it
 // already holds.
 __device__ __forceinline__ int release(int t, bool is_l, const int* succ_ptr, const int* succ, const int* next,
-                                       int* indeg, int* taken, unsigned long long* trace, int* s_task,
-                                       int* s_claim) {
+                                       int* indeg, int* taken, unsigned long long* trace, int* s_task) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -314,7 +311,6 @@ __device__ __forceinline__ int release(int t, bool is_l, const int* succ_ptr, co
             }
         }
         *s_task = nx;
-        *s_claim = 0;
     }
     __syncthreads();
     return *s_task;
@@ -326,7 +322,7 @@ forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all
             T* y, T* w, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_task, s_claim, s_done;
+    __shared__ int s_task, s_done;
     const unsigned long long deadline = gclock() + timeout_ns;
     int* indeg = S.dag_indeg;
     int* taken = S.dag_taken;
@@ -334,8 +330,8 @@ forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all
     bool cont = false;
     for (;;) {
         if (t < 0) {
-            t = claim_task(S.counter + 0, S.nftask, indeg, taken, S.counter + 2, deadline, &s_task, &s_claim,
-                           &s_done, S.trace);
+            t = claim_task(S.counter + 0, S.nftask, indeg, taken, S.counter + 2, deadline, &s_task, &s_done,
+                           S.trace);
             cont = false;
         }
         if (t < 0) break;
@@ -344,8 +340,8 @@ forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all
             fwd_external<G, T>(S, uvt, y, w, tk.z, tk.w);
         else
             solve_local<G, T, false>(S, static_cast<const T*>(S.xf_val), rd_all, r, nullptr, y, nullptr, w, tk.y,
-                                     tk.z, tk.w, sh, &s_claim, &s_done, cont, deadline);
-        t = release(t, tk.x == 1, S.f_succ_ptr, S.f_succ, S.f_next, indeg, taken, S.trace, &s_task, &s_claim);
+                                     tk.z, tk.w, sh, &s_done, cont, deadline);
+        t = release(t, tk.x == 1, S.f_succ_ptr, S.f_succ, S.f_next, indeg, taken, S.trace, &s_task);
         cont = t >= 0;
     }
 }
@@ -356,7 +352,7 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
              double* __restrict__ z, T* w, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_task, s_claim, s_done;
+    __shared__ int s_task, s_done;
     const unsigned long long deadline = gclock() + timeout_ns;
     int* indeg = S.dag_indeg + S.nftask;
     int* taken = S.dag_taken + S.nftask;
@@ -365,8 +361,7 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
     bool cont = false;
     for (;;) {
         if (t < 0) {
-            t = claim_task(S.counter + 1, S.nbtask, indeg, taken, S.counter + 2, deadline, &s_task, &s_claim,
-                           &s_done, tr);
+            t = claim_task(S.counter + 1, S.nbtask, indeg, taken, S.counter + 2, deadline, &s_task, &s_done, tr);
             cont = false;
         }
         if (t < 0) break;
@@ -375,8 +370,8 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
             bwd_external<G, T>(S, uv, zv, w, tk.z, tk.w);
         else
             solve_local<G, T, true>(S, static_cast<const T*>(S.xb_val), rd_all, nullptr, y, zv, z, w, tk.y, tk.z,
-                                    tk.w, sh, &s_claim, &s_done, cont, deadline);
-        t = release(t, tk.x == 1, S.b_succ_ptr, S.b_succ, S.b_next, indeg, taken, tr, &s_task, &s_claim);
+                                    tk.w, sh, &s_done, cont, deadline);
+        t = release(t, tk.x == 1, S.b_succ_ptr, S.b_succ, S.b_next, indeg, taken, tr, &s_task);
         cont = t >= 0;
     }
 }
