@@ -2,18 +2,22 @@
 // with L = U^T the incomplete factor.
 //
 // The 2D block structure of Section 3.2 organises the solve like the factorization's
-// task DAG (Section 3.3): a range of rows (a block row) is one unit.  Task E(k, c)
-// sums, for a chunk of range k's rows, the entries whose other index lies in another
-// range (all finished when E starts); task L(k) is one CTA that solves the range's
-// rows with the remaining, internal entries, the rows taken in local dependence-level
-// order and the range's results kept in shared memory, so a dependence inside a range
-// costs a shared-memory round trip rather than an L2 one.  Nested-dissection leaves
-// are independent in the forward solve and run concurrently; separators follow.
+// task DAG (Section 3.3): a range of rows (a block row), its rows in local
+// dependence-level order, is cut into parts of whole levels.  Task E sums, for a chunk
+// of a part's rows, the entries whose other index lies in another range, once the
+// parts holding those rows have finished; task L is one CTA that solves a part's rows
+// with the remaining, internal entries after the range's previous part, the range's
+// results kept in shared memory, so a dependence inside a range costs a
+// shared-memory round trip rather than an L2 one.  Nested-dissection leaves are
+// independent in the forward solve and run concurrently; a separator's first parts
+// run while its subdomains are still finishing.
 //
-// Scheduling: one persistent grid claims tasks in a fixed topological order (atomic
-// counter), waits (bounded) until the task's range counter reaches zero, runs it and
-// releases its successors.  Every task a CTA waits for was claimed earlier by a
-// resident CTA, so the claims cannot deadlock.  All waits give up at the deadline or
+// Scheduling: one persistent grid per direction claims tasks in a fixed topological
+// order (atomic counter), waits (bounded) until the task's in-degree reaches zero,
+// runs it and releases its successors; a CTA that finishes an L part runs the same
+// range's next part itself when it is ready, keeping its shared-memory state.  Every
+// task a CTA waits for was claimed earlier by a resident CTA (or is running as a
+// continuation), so the claims cannot deadlock.  All waits give up at the deadline or
 // when another CTA has set the abort word, and the host reports IC_ERR_TIMEOUT.
 #include <cstdint>
 
