@@ -4,7 +4,7 @@
 // dropped); factoring B + alpha * diag(B) restores positive pivots for a large enough
 // alpha at the price of a weaker preconditioner.  A small network reads 8 features of
 // the matrix and predicts log10 alpha, so the first attempt is usually the last; the
-// doubling retry (api.cpp, ic_numeric_shifted) remains the fallback and the judge.
+// doubling retry (api.cpp, ic_numeric_shifted) remains the fallback and has the last word.
 //
 // Features (FP64, deterministic two-stage reductions), for row i with d = B_ii,
 // s = sum_{j != i} |B_ij| and r = ||row i||_2:  dd_i = d / max(s, d / 1000),

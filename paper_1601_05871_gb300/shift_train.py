@@ -9,7 +9,7 @@ reach the tolerance.  The label is the largest shift whose iteration count is wi
 max(1, 2%) of the sweep's best: the cheapest preconditioner, with a margin above the
 breakdown threshold.  The network learns log10 of that shift from the 8 matrix
 features; at solve time its prediction is the first attempt of the shift-doubling
-retry, which stays the fallback and the judge (ic_numeric_shifted).
+retry, which stays the fallback and has the last word (ic_numeric_shifted).
 """
 from __future__ import annotations
 
