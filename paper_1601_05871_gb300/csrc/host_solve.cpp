@@ -31,9 +31,9 @@ namespace {
 constexpr double kTaskStartUs = 2.0;    // claim, dependence check, release
 constexpr double kLevelUs = 1.0;        // one local dependence level in shared memory (measured)
 constexpr double kFmaUs = 2.0e-3;       // one external FP64 multiply-add of an E task (measured)
-constexpr int64_t kChunkEntries = 4096; // external entries per E task, at most
-constexpr int kChunkRows = 256;         // order positions per E task, at most
-constexpr int kPartLevels = 16;         // local levels per L task of a range with external entries
+constexpr int64_t kChunkEntries = 8192; // external entries per E task, at most
+constexpr int kChunkRows = 512;         // order positions per E task, at most
+constexpr int kPartLevels = 24;         // local levels per L task of a range with external entries
 
 // Rows of one range sorted by local level, each level's run padded with -1 to a
 // multiple of kClaimPad; appended to out.  need receives, per position, the number of
