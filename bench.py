@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--k", type=int, default=2)
     ap.add_argument("--block-rows", type=int, default=4096)
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--warps", type=int, default=16)
+    ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--numeric-only", action="store_true",
@@ -227,7 +227,8 @@ def shift_workload(a):
         for nu in SHIFT_NU_TRAIN:
             p = synth.elasticity3d_q1(ne, nu=nu)
             perm, ranges = ick.ic_nd_grid(*p.grid, 3, 256, p.keep)
-            h = ick.ic_symbolic(p.rowptr, p.colind, 0, perm, ranges, block_rows=256, dtype=ick.IC_F32)
+            h = ick.ic_symbolic(p.rowptr, p.colind, 0, perm, ranges, block_rows=256, dtype=ick.IC_F32,
+                               warps_per_cta=a.warps)
             av = torch.from_numpy(p.vals).cuda()
             b = torch.from_numpy(synth.rhs(p.n, 11)).cuda()
             x = torch.empty_like(b)
@@ -244,7 +245,8 @@ def shift_workload(a):
         x = torch.empty_like(b)
         res = {}
         for name, dtype, model in (("fp64_plain", ick.IC_F64, None), ("fp32_learned", ick.IC_F32, mlp)):
-            h = ick.ic_symbolic(p.rowptr, p.colind, 0, perm, ranges, block_rows=4096, dtype=dtype)
+            h = ick.ic_symbolic(p.rowptr, p.colind, 0, perm, ranges, block_rows=4096, dtype=dtype,
+                               warps_per_cta=a.warps)
             T.solve(h, av, b, x, mlp=model, nu=nu)  # warm-up
             runs = [T.solve(h, av, b, x, mlp=model, nu=nu) for _ in range(max(1, a.steps))]
             r = min(runs, key=lambda q: q["seconds"])
@@ -286,7 +288,8 @@ def c3_workload(a):
     probs = synth.config_problem(3)
     nd = [ick.ic_nd_grid(*p.grid, 1, 4096) for p in probs]
     pats = [(p.rowptr, p.colind) for p in probs]
-    h = ick.ic_symbolic_batch(pats, 1, [x[0] for x in nd], [x[1] for x in nd], dtype=ick.IC_F32, block_rows=4096)
+    h = ick.ic_symbolic_batch(pats, 1, [x[0] for x in nd], [x[1] for x in nd], dtype=ick.IC_F32, block_rows=4096,
+                              warps_per_cta=a.warps)
     st = ick.ic_stats(h)
     vals = torch.from_numpy(np.concatenate([p.vals for p in probs])).cuda()
     b_host = np.concatenate([synth.rhs(p.n, 3000 + s) for s, p in enumerate(probs)])
@@ -344,7 +347,8 @@ def c5_workload(a):
     out = {}
     st = None
     for name, dtype in (("fp32", ick.IC_F32), ("fp64", ick.IC_F64)):
-        h = ick.ic_symbolic(p.rowptr, p.colind, 3, perm, ranges, block_rows=a.block_rows, dtype=dtype)
+        h = ick.ic_symbolic(p.rowptr, p.colind, 3, perm, ranges, block_rows=a.block_rows, dtype=dtype,
+                            warps_per_cta=a.warps)
         st = ick.ic_stats(h)
         ick.ic_set_timing(h, True)
         for _ in range(a.warmup):
@@ -523,7 +527,7 @@ def main():
             "config": {"workload": workload_name(a), "n": n, "nnz_a": st["nnz_a"], "nnz_l": nnz_l,
                        "k": a.k, "block_rows": a.block_rows, "ranges": st["nranges"],
                        "blocks": st["nblocks"], "tasks": st["ntasks"], "items": st["nitems"],
-                       "critical_path_tasks": st["critical_path"], "warps_per_cta": a.warps,
+                       "critical_path_tasks": st["critical_path"], "warps_per_cta": st["warps_per_cta"],
                        "grid_ctas": st["grid_ctas"], "flops": st["flops"], "bytes": st["bytes"],
                        "l2": "inputs larger than L2 (factor values alone 8*nnz(L) bytes)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

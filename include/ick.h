@@ -59,14 +59,19 @@ typedef struct {
 typedef struct {
     int block_rows;    /* [4096] largest block; longer ranges are split evenly; <= 8192 */
     int dtype;         /* [IC_F64] factor precision                                      */
-    int warps_per_cta; /* [16] warps in each CTA of the persistent numeric kernel: 8|16  */
-    int rows_per_item; /* [16] target rows per work item of a Herk/Gemm task             */
+    int warps_per_cta; /* [32 for one system, 16 for a batch] warps in each CTA of the
+                          persistent numeric kernel: 8|16|32 (32: one CTA per SM,
+                          16: two)                                                      */
+    int rows_per_item; /* [warps_per_cta] target rows per work item of a Herk/Gemm task */
     double timeout_s;  /* [10] bound on every device wait of one call                    */
     double shift_alpha;/* [0] factor B + alpha * diag(B) instead of B                    */
     int exact;         /* [0] 1: each update is a separately rounded multiply then
-                          subtract (no FMA), the same operation sequence per entry as
-                          the up-looking row order, so the FP64 factor is reproducible
-                          bit for bit; 0: fused multiply-add                            */
+                          subtract (no FMA), and the updates of a block are applied in
+                          ascending k: the same operation sequence per entry as the
+                          up-looking row order, so the FP64 factor is reproducible
+                          bit for bit; 0: fused multiply-add, and the updates of a block
+                          chained in the order of their inputs' estimated readiness
+                          (deterministic: one fixed order per entry)                    */
     int threads;       /* [0 = all] host threads for the symbolic phase                  */
     int host_only;     /* [0] 1: ic_symbolic builds the plan in host memory only (no GPU
                           needed); such a handle serves the ic_get_* and ic_stats calls   */
@@ -96,6 +101,8 @@ typedef struct {
     double symbolic_s;    /* wall time of ic_symbolic                                */
     int64_t grid_ctas;    /* CTAs of the persistent kernel launch                    */
     int64_t solve_depth[2];/* levels of the forward / backward solve's row DAG        */
+    int64_t warps_per_cta;/* warps per CTA of the persistent kernel (defaults resolved) */
+    int64_t rows_per_item;/* target rows per Herk/Gemm work item (defaults resolved)    */
 } ic_stats_t;
 
 typedef struct ic_handle ic_handle;
@@ -194,7 +201,12 @@ int ic_stats(const ic_handle* h, ic_stats_t* out);
 /* Task list of the handle in generation order (the loop of Section 3.3's task
  * generator figure).  type: 0 Chol, 1 Trsm, 2 Herk, 3 Gemm; (tk, ti, tj) block
  * indices: Chol (k,k,k), Trsm (k,k,j), Herk (k,i,i), Gemm (k,i,j).  pred_ptr
- * (ntasks+1) and pred list the distinct predecessors.  Call with NULL arrays to get
+ * (ntasks+1) and pred list the distinct predecessors.  With exact = 1 these are the
+ * generator's (the updates of a block chained in k order, every predecessor earlier
+ * in the list); with exact = 0 the updates of a block are chained in another order
+ * (see ic_opts.exact), so an update's predecessor may come later in the list.  The
+ * dependencies on data (Trsm on Chol, an update on its two Trsm inputs, a block's
+ * Chol/Trsm on its last update) are the same in both.  Call with NULL arrays to get
  * *ntasks and *npred, then again with buffers of at least those sizes.
  * Errors: IC_ERR_ARG. */
 int ic_get_tasks(const ic_handle* h, int32_t* type, int32_t* tk, int32_t* ti, int32_t* tj,
@@ -320,7 +332,7 @@ int ic_numeric_status(ic_handle* h, int64_t* breakdown_row);
 /* Autotuner for the task granularity trade-offs of Section 4 (block size and the work
  * per task) and the solve launch shape.  For the given matrix or batch (count = 1 for
  * one matrix; arguments as ic_symbolic_batch), it times ic_numeric (median of reps)
- * over block_rows in {1024, 2048, 4096, 8192}, then warps_per_cta in {8, 16}, then
+ * over block_rows in {1024, 2048, 4096, 8192}, then warps_per_cta in {8, 16, 32}, then
  * rows_per_item in {16, 32, 64} (coordinate search, each best kept), and ic_apply over
  * solve_lanes in {8, 16, 32} (8 only for the block-DAG solves) x solve_ctas_per_sm in
  * {2, 3, 4, 6} (within occupancy) on the chosen plan.

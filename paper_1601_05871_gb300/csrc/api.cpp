@@ -125,12 +125,15 @@ struct ic_handle {
 
 namespace {
 
-ic_opts normalise(const ic_opts* o) {
+// count: systems in the handle.  One system: a CTA of 32 warps per SM, so the Chol
+// tasks of the top separators, which run alone, get a whole SM; a batch of small
+// systems: two CTAs of 16 warps per SM, twice the tasks in flight.
+ic_opts normalise(const ic_opts* o, int64_t count) {
     ic_opts r{};
     if (o) r = *o;
     if (r.block_rows == 0) r.block_rows = 4096;
-    if (r.warps_per_cta == 0) r.warps_per_cta = 16;
-    if (r.rows_per_item == 0) r.rows_per_item = 16;
+    if (r.warps_per_cta == 0) r.warps_per_cta = count > 1 ? 16 : 32;
+    if (r.rows_per_item == 0) r.rows_per_item = r.warps_per_cta;
     if (r.timeout_s == 0.0) r.timeout_s = 10.0;
     if (r.solve_lanes == 0) r.solve_lanes = r.solve_mode == 0 ? 8 : 32;
     if (r.solve_ctas_per_sm == 0) r.solve_ctas_per_sm = r.solve_mode == 0 ? 2 : 3;
@@ -417,10 +420,10 @@ static int symbolic_impl(const ic_csr_pattern* A, int k, const int32_t* perm, co
     ic_handle* h = nullptr;
     try {
         h = new ic_handle();
-        h->opts = normalise(opts);
-        if (h->opts.warps_per_cta != 8 && h->opts.warps_per_cta != 16) {
+        h->opts = normalise(opts, count);
+        if (h->opts.warps_per_cta != 8 && h->opts.warps_per_cta != 16 && h->opts.warps_per_cta != 32) {
             delete h;
-            return fail(IC_ERR_ARG, "warps_per_cta must be 8 or 16");
+            return fail(IC_ERR_ARG, "warps_per_cta must be 8, 16 or 32");
         }
         if ((h->opts.dtype != IC_F64 && h->opts.dtype != IC_F32) ||
             (h->opts.dtype == IC_F32 && h->opts.exact)) {
@@ -435,7 +438,7 @@ static int symbolic_impl(const ic_csr_pattern* A, int k, const int32_t* perm, co
         }
         std::string err;
         int st = build_plan(A, k, perm, ranges, nranges, h->opts.block_rows, h->opts.rows_per_item,
-                            h->opts.threads, h->hp, err);
+                            h->opts.threads, h->opts.exact != 0, h->hp, err);
         if (st) {
             delete h;
             return fail(st, err);
@@ -888,6 +891,8 @@ int ic_stats(const ic_handle* h, ic_stats_t* out) {
     out->grid_ctas = h->grid_numeric;
     out->solve_depth[0] = P.fwd_depth;
     out->solve_depth[1] = P.bwd_depth;
+    out->warps_per_cta = h->opts.warps_per_cta;
+    out->rows_per_item = h->opts.rows_per_item;
     return IC_OK;
 }
 
@@ -1114,7 +1119,7 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
                 const int64_t* const* ranges, const int64_t* nranges, const void* values,
                 const ic_opts* base, int reps, ic_opts* best, double* times, void* stream) {
     if (!best || !values || reps < 1) return fail(IC_ERR_ARG, "NULL best/values or reps < 1");
-    ic_opts cur = normalise(base);
+    ic_opts cur = normalise(base, count);
     cur.host_only = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // median numeric time of a candidate (rebuilds the plan), or < 0 on error
@@ -1144,7 +1149,7 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
         if (best_num < 0) return fail(IC_ERR_ARG, "autotune: no candidate factored (" + std::string(ic_last_error()) + ")");
         cur = pick;
     }
-    for (int w : {8, 16}) {
+    for (int w : {8, 16, 32}) {
         if (w == cur.warps_per_cta) continue;
         ic_opts o = cur;
         o.warps_per_cta = w;

@@ -21,6 +21,7 @@
 // tested for breakdown in FP64 (array udiag): in Chol and Herk each pivot row's source
 // segment starts at column r, so its contribution to U_rr is exactly U_pr^2, which the
 // owning warp subtracts in FP64.
+#include <climits>
 #include <cstdint>
 #include <type_traits>
 
@@ -109,9 +110,11 @@ __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int loc
     return true;
 }
 
-constexpr int kHash = 256;     // per-warp open-addressing table: target column -> slot
-constexpr int kRing = 4;       // staging slots per warp: kRing - 1 pivots in flight
-constexpr int kSegStage = 64;  // source elements of one pivot staged by copies
+constexpr int kMapWords = 128;  // per-warp column map: 4096 column offsets
+constexpr int kMapBits = 32 * kMapWords;
+constexpr int kRing = 4;        // staging slots per warp: kRing - 1 pivots in flight
+constexpr int kSegStage = 64;   // source elements of one pivot staged by copies
+static_assert(kSegStage <= 64, "a staged segment is applied as two elements per lane");
 
 // One staged pivot segment: values and columns copied as the enclosing 16-byte
 // aligned spans, plus the 16 bytes holding U_pr when it lies outside the segment.
@@ -123,36 +126,47 @@ struct Slot {
 };
 
 // Per-warp shared-memory work area (16-byte multiples first for the async copies).
+// The target chunk's columns, offsets from its first column c_0, are a bit map with
+// the rank of each word's first bit: column c sits at slot
+// rank[w] + popc(bits[w] below bit b), w = (c - c_0) / 32, b = (c - c_0) % 32.
 template <typename T>
 struct WarpBuf {
     Slot<T> ring[kRing];
+    int4 piv[32];          // pivot row, position of U_pr, source segment start, length
     double dacc;           // FP64 diagonal accumulator (T = float)
     double pad;
+    uint2 cmap[kMapWords]; // (bits, rank) per 32 column offsets
     T tval[kSegCap];       // target segment values (one chunk)
     int tcol[kSegCap];     // target segment columns
-    int hkey[kHash];       // hash keys (column, or -1)
-    short hslot[kHash];    // slot in the target chunk of each key
 };
 
-__device__ __forceinline__ int hash_of(int c) { return int((unsigned(c) * 2654435761u) >> 24); }
-
+// Slot of column c in the target chunk, or -1.
 template <typename T>
-__device__ __forceinline__ int hash_find(const WarpBuf<T>& W, int c) {
-    int h = hash_of(c);
-    for (;;) {
-        const int k = W.hkey[h];
-        if (k == c) return W.hslot[h];
-        if (k == -1) return -1;
-        h = (h + 1) & (kHash - 1);
-    }
+__device__ __forceinline__ int find_col(const WarpBuf<T>& W, int c, int c_0, unsigned span) {
+    const unsigned off = unsigned(c - c_0);
+    const uint2 e = W.cmap[min(off >> 5, unsigned(kMapWords - 1))];
+    const unsigned b = off & 31u;
+    return (off < span && ((e.x >> b) & 1u)) ? int(e.y) + __popc(e.x & ((1u << b) - 1u)) : -1;
 }
 
 template <bool EXACT, typename T>
-__device__ __forceinline__ void apply_one(WarpBuf<T>& W, int c, int cmin, int cmax, T a, T v) {
-    if (c >= cmin && c <= cmax) {
-        const int idx = hash_find(W, c);
-        if (idx >= 0) W.tval[idx] = sub_product<EXACT>(W.tval[idx], a, v);
-    }
+__device__ __forceinline__ void apply_one(WarpBuf<T>& W, int c, int c_0, unsigned span, T a, T v) {
+    const int idx = find_col(W, c, c_0, span);
+    if (idx >= 0) W.tval[idx] = sub_product<EXACT>(W.tval[idx], a, v);
+}
+
+// Elements lane and lane + 32 of a staged segment of n <= 64 elements: the two
+// lookups and loads overlap (the slots differ: a pivot row's columns are distinct).
+template <bool EXACT, typename T>
+__device__ __forceinline__ void apply_staged(WarpBuf<T>& W, const int* cols, const T* vals, int n,
+                                             int c_0, unsigned span, T a) {
+    const int lane = threadIdx.x & 31;
+    const int i0 = lane < n ? find_col(W, cols[lane], c_0, span) : -1;
+    const int i1 = lane + 32 < n ? find_col(W, cols[lane + 32], c_0, span) : -1;
+    const T v0 = vals[lane], v1 = vals[lane + 32];
+    const T t0 = W.tval[max(i0, 0)], t1 = W.tval[max(i1, 0)];
+    if (i0 >= 0) W.tval[i0] = sub_product<EXACT>(t0, a, v0);
+    if (i1 >= 0) W.tval[i1] = sub_product<EXACT>(t1, a, v1);
 }
 
 // Issue the copies of pivot q's source segment into ring slot q % kRing.  Returns 1
@@ -160,29 +174,31 @@ __device__ __forceinline__ void apply_one(WarpBuf<T>& W, int c, int cmin, int cm
 // not complete yet (Chol/Trsm): then the consumer waits and loads it directly.
 template <int MODE, typename T>
 __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf<T>& W, int q,
-                                           int p, int pos, int sb, int len, bool start_at_r,
-                                           int rbase, volatile unsigned char* done) {
+                                           bool start_at_r, int rbase, volatile unsigned char* done) {
     constexpr int EPC = 16 / sizeof(T);  // elements per 16-byte chunk
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    const int pq = __shfl_sync(full, p, q), posq = __shfl_sync(full, pos, q);
-    const int sbq = __shfl_sync(full, sb, q), lq = __shfl_sync(full, len, q);
-    if (lq == 0) return 1;
+    const int4 pi = W.piv[q];
+    if (pi.w == 0) return 1;
     if (MODE != M_UPDATE) {
         int f = 0;
-        if (lane == 0) f = done[pq - rbase];
+        if (lane == 0) f = done[pi.x - rbase];
         if (!__shfl_sync(full, f, 0)) return 0;
         __threadfence_block();
     }
     Slot<T>& S = W.ring[q % kRing];
-    const int n = min(lq, kSegStage);
-    const int vb = sbq & ~(EPC - 1), nv = (((sbq + n + EPC - 1) & ~(EPC - 1)) - vb) / EPC;
-    const int cb = sbq & ~3, nc = (((sbq + n + 3) & ~3) - cb) >> 2;
+    const int n = min(pi.w, kSegStage);
+    const int vb = pi.z & ~(EPC - 1), nv = (((pi.z + n + EPC - 1) & ~(EPC - 1)) - vb) / EPC;
+    const int cb = pi.z & ~3, nc = (((pi.z + n + 3) & ~3) - cb) >> 2;
     const int total = nv + nc + (start_at_r ? 0 : 1);
     for (int t = lane; t < total; t += 32) {
-        if (t < nv) cp_async16(&S.vals[EPC * t], U + vb + EPC * t);
-        else if (t < nv + nc) cp_async16(&S.cols[4 * (t - nv)], P.ucol + cb + 4 * (t - nv));
-        else cp_async16(&S.aval[0], U + (posq & ~(EPC - 1)));
+        const bool isv = t < nv, isc = !isv && t < nv + nc;
+        const void* src = isv ? static_cast<const void*>(U + vb + EPC * t)
+                        : isc ? static_cast<const void*>(P.ucol + cb + 4 * (t - nv))
+                              : static_cast<const void*>(U + (pi.y & ~(EPC - 1)));
+        void* dst = isv ? static_cast<void*>(&S.vals[EPC * t])
+                  : isc ? static_cast<void*>(&S.cols[4 * (t - nv)]) : static_cast<void*>(&S.aval[0]);
+        cp_async16(dst, src);
     }
     return 1;
 }
@@ -194,8 +210,10 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf
 // all inputs final).  start_at_r: the source segment starts at the pivot's entry in
 // column r (target block column == block of r).
 //
-// Pivots are applied one at a time in ascending order, lane l taking source elements
-// l, l+32, ...; a target column is found through a per-warp hash table.  The source
+// The target segment is processed in chunks of at most kSegCap entries whose columns
+// lie within kMapBits of the chunk's first column, so that a column is found through
+// the chunk's bit map and word ranks with no probing.  Pivots are applied one at a
+// time in ascending order, lane l taking source elements l, l+32, ...  The source
 // segments of the next kRing-1 pivots are copied asynchronously into a ring of
 // shared-memory slots while the current one is applied.  For Chol and Trsm a copy is
 // issued only once the pivot row's completion flag is seen; a pivot that was not
@@ -216,81 +234,87 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
         if (MIXED) scale = T(1.0 / __ldcg(P.udiag + r));
         else scale = ld_cg(U + __ldg(P.urp + r));
     }
-    for (int c0 = tb; c0 < te; c0 += kSegCap) {
-        const int m = min(kSegCap, te - c0);
+    int m = 0;
+    for (int c0 = tb; c0 < te; c0 += m) {
+        // a chunk: at most kSegCap entries whose columns lie within kMapBits of its first
+        const int c_0 = __ldg(P.ucol + c0);
+        const int mx = min(kSegCap, te - c0);
+        m = 0;
+        for (int x0 = 0; x0 < mx; x0 += 32) {
+            const int x = x0 + lane;
+            const int c = x < mx ? __ldg(P.ucol + c0 + x) : INT_MAX;
+            const bool in = c - c_0 < kMapBits;  // a prefix: the columns ascend
+            if (in) {
+                W.tcol[x] = c;
+                W.tval[x] = ld_cg(U + c0 + x);
+            }
+            m += __popc(__ballot_sync(full, in));
+        }
         // the FP64 diagonal of a Chol/Herk target row (T = float): first chunk only
         const bool dchunk = MIXED && start_at_r && c0 == tb;
-        for (int x = lane; x < kHash; x += 32) W.hkey[x] = -1;
-        for (int x = lane; x < m; x += 32) {
-            W.tcol[x] = __ldg(P.ucol + c0 + x);
-            W.tval[x] = ld_cg(U + c0 + x);
-        }
         if (dchunk && lane == 0) W.dacc = __ldcg(P.udiag + r);
         __syncwarp();
+        const int nw = ((W.tcol[m - 1] - c_0) >> 5) + 1;
+        const unsigned span = unsigned(nw) * 32u;
+        for (int w = lane; w < nw; w += 32) W.cmap[w].x = 0u;
+        __syncwarp();
         for (int x = lane; x < m; x += 32) {
-            const int c = W.tcol[x];
-            int h = hash_of(c);
-            while (atomicCAS(&W.hkey[h], -1, c) != -1) h = (h + 1) & (kHash - 1);
-            W.hslot[h] = short(x);
+            const int off = W.tcol[x] - c_0;
+            atomicOr(&W.cmap[off >> 5].x, 1u << (off & 31));
+            if (x == 0 || ((W.tcol[x - 1] - c_0) >> 5) != (off >> 5)) W.cmap[off >> 5].y = unsigned(x);
         }
         __syncwarp();
-        const int cmin = W.tcol[0], cmax = W.tcol[m - 1];
         for (int q0 = ca; q0 < cb; q0 += 32) {
             const int nq = min(32, cb - q0);
-            int p = 0, pos = 0, sb = 0, len = 0;
             if (lane < nq) {
                 const int2 pe = __ldg(P.csc + q0 + lane);
-                p = pe.x;
-                pos = pe.y;
+                int sb, len;
                 if (start_at_r) {
-                    sb = pos;
-                    len = __ldg(P.cseg_end + q0 + lane) - pos;
+                    sb = pe.y;
+                    len = __ldg(P.cseg_end + q0 + lane) - pe.y;
                 } else {
-                    const int2 s = row_segment(P, p, srcblk);
+                    const int2 s = row_segment(P, pe.x, srcblk);
                     sb = s.x;
                     len = s.y - s.x;
                 }
+                W.piv[lane] = make_int4(pe.x, pe.y, sb, len);
             }
+            __syncwarp();
             unsigned issued = 0;
 #pragma unroll
             for (int s = 0; s < kRing - 1; ++s) {
-                if (s < nq)
-                    issued |= unsigned(issue_pivot<MODE>(P, U, W, s, p, pos, sb, len, start_at_r, rbase,
-                                                         done)) << s;
+                if (s < nq) issued |= unsigned(issue_pivot<MODE>(P, U, W, s, start_at_r, rbase, done)) << s;
                 cp_async_commit();
             }
             for (int q = 0; q < nq; ++q) {
                 const int nxt = q + kRing - 1;
                 if (nxt < nq)
-                    issued |= unsigned(issue_pivot<MODE>(P, U, W, nxt, p, pos, sb, len, start_at_r,
-                                                         rbase, done)) << nxt;
+                    issued |= unsigned(issue_pivot<MODE>(P, U, W, nxt, start_at_r, rbase, done)) << nxt;
                 cp_async_commit();
                 cp_async_wait<kRing - 1>();
                 __syncwarp();
-                const int pq = __shfl_sync(full, p, q), posq = __shfl_sync(full, pos, q);
-                const int sbq = __shfl_sync(full, sb, q), lq = __shfl_sync(full, len, q);
-                if (lq > 0) {
+                const int4 pi = W.piv[q];
+                if (pi.w > 0) {
                     int first_direct = 0;
                     T a;
                     if ((issued >> q) & 1u) {
                         const Slot<T>& S = W.ring[q % kRing];
-                        const int n = min(lq, kSegStage);
-                        const int vo = sbq - (sbq & ~(EPC - 1)), co = sbq - (sbq & ~3);
-                        a = start_at_r ? S.vals[vo] : S.aval[posq & (EPC - 1)];
-                        for (int x = lane; x < n; x += 32)
-                            apply_one<EXACT>(W, S.cols[co + x], cmin, cmax, a, S.vals[vo + x]);
+                        const int n = min(pi.w, kSegStage);
+                        const int vo = pi.z - (pi.z & ~(EPC - 1)), co = pi.z - (pi.z & ~3);
+                        a = start_at_r ? S.vals[vo] : S.aval[pi.y & (EPC - 1)];
+                        apply_staged<EXACT>(W, S.cols + co, S.vals + vo, n, c_0, span, a);
                         first_direct = n;
                     } else {
                         int ok = 1;
-                        if (lane == 0) ok = wait_row(P, done, pq - rbase, deadline);
+                        if (lane == 0) ok = wait_row(P, done, pi.x - rbase, deadline);
                         if (!__shfl_sync(full, ok, 0)) {
                             cp_async_wait<0>();
                             return;
                         }
-                        a = ld_cg(U + posq);
+                        a = ld_cg(U + pi.y);
                     }
-                    for (int o = first_direct + lane; o < lq; o += 32)
-                        apply_one<EXACT>(W, __ldg(P.ucol + sbq + o), cmin, cmax, a, ld_cg(U + sbq + o));
+                    for (int o = first_direct + lane; o < pi.w; o += 32)
+                        apply_one<EXACT>(W, __ldg(P.ucol + pi.z + o), c_0, span, a, ld_cg(U + pi.z + o));
                     if (dchunk && lane == 0) W.dacc = fma(-double(a), double(a), W.dacc);
                 }
                 __syncwarp();
@@ -539,8 +563,10 @@ cudaError_t occupancy_t(int* blocks) {
 
 cudaError_t numeric_blocks_per_sm(int warps, bool exact, int dtype, int* blocks) {
     if (dtype == IC_F32)
-        return warps == 8 ? occupancy_t<8, false, float>(blocks) : occupancy_t<16, false, float>(blocks);
+        return warps == 8 ? occupancy_t<8, false, float>(blocks)
+             : warps == 32 ? occupancy_t<32, false, float>(blocks) : occupancy_t<16, false, float>(blocks);
     if (warps == 8) return exact ? occupancy_t<8, true, double>(blocks) : occupancy_t<8, false, double>(blocks);
+    if (warps == 32) return exact ? occupancy_t<32, true, double>(blocks) : occupancy_t<32, false, double>(blocks);
     return exact ? occupancy_t<16, true, double>(blocks) : occupancy_t<16, false, double>(blocks);
 }
 
@@ -563,10 +589,14 @@ cudaError_t launch_numeric(const DevPlan& P, int epoch, int warps, bool exact, i
                            unsigned long long timeout_ns, cudaStream_t s) {
     if (dtype == IC_F32)
         return warps == 8 ? launch_t<8, false, float>(P, grid, epoch, timeout_ns, s)
-                          : launch_t<16, false, float>(P, grid, epoch, timeout_ns, s);
+             : warps == 32 ? launch_t<32, false, float>(P, grid, epoch, timeout_ns, s)
+                           : launch_t<16, false, float>(P, grid, epoch, timeout_ns, s);
     if (warps == 8)
         return exact ? launch_t<8, true, double>(P, grid, epoch, timeout_ns, s)
                      : launch_t<8, false, double>(P, grid, epoch, timeout_ns, s);
+    if (warps == 32)
+        return exact ? launch_t<32, true, double>(P, grid, epoch, timeout_ns, s)
+                     : launch_t<32, false, double>(P, grid, epoch, timeout_ns, s);
     return exact ? launch_t<16, true, double>(P, grid, epoch, timeout_ns, s)
                  : launch_t<16, false, double>(P, grid, epoch, timeout_ns, s);
 }

@@ -44,7 +44,8 @@ class ic_stats_t(C.Structure):
                 ("nblocks", C.c_int64), ("ntasks", C.c_int64), ("ntasks_type", C.c_int64 * 4),
                 ("nitems", C.c_int64), ("critical_path", C.c_int64), ("max_level", C.c_int64),
                 ("flops", C.c_double), ("bytes", C.c_double), ("symbolic_s", C.c_double),
-                ("grid_ctas", C.c_int64), ("solve_depth", C.c_int64 * 2)]
+                ("grid_ctas", C.c_int64), ("solve_depth", C.c_int64 * 2), ("warps_per_cta", C.c_int64),
+                ("rows_per_item", C.c_int64)]
 
 
 def load():

@@ -77,12 +77,21 @@ def test_c1_nd_ranges(ick, orc):
     check_parity(ick, orc, prob, perm, ranges, 1, exact=1, block_rows=256)
 
 
-@pytest.mark.parametrize("warps", [8, 16])
+@pytest.mark.parametrize("warps", [8, 16, 32])
 def test_27pt_ic2(ick, orc, warps):
     prob = synth.laplace3d_27pt(14)
     perm, ranges = ick.ic_nd_grid(14, 14, 14, 1, 300)
     check_parity(ick, orc, prob, perm, ranges, 2, exact=1, block_rows=300, warps_per_cta=warps)
     check_parity(ick, orc, prob, perm, ranges, 2, exact=0, block_rows=300, warps_per_cta=warps)
+
+
+def test_rows_wider_than_the_column_map(ick, orc):
+    """Natural order of a 5000 x 3 grid in two 7500-row blocks: a row's segment in a
+    block reaches 5000 columns past its diagonal, so a target row is cut into chunks
+    whose columns each span at most 4096."""
+    prob = synth.poisson2d_5pt(5000, 3)
+    for exact in (1, 0):
+        check_parity(ick, orc, prob, None, None, 1, exact=exact, block_rows=8192)
 
 
 def test_anisotropic_ic3_ragged_blocks(ick, orc):

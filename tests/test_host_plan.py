@@ -5,10 +5,12 @@ lists.  No GPU is used: handles are built with host_only=1.
 The plan executor below runs the work lists of every task on the CPU, in random
 topological orders of the DAG, with each update a separately rounded multiply then
 subtract.  It is a test of the plan only (DAG edges and target lists), never a
-product path.  Because the DAG serialises every update to a block in k order and a
-task applies its pivots in ascending order, every entry sees the same operation
+product path.  With exact=1 the DAG serialises every update to a block in k order and
+a task applies its pivots in ascending order, so every entry sees the same operation
 sequence as the oracle's up-looking order: the result must match the oracle bit for
-bit in any valid order.
+bit in any valid order.  Without it the updates of a block are chained in another
+order (their inputs' estimated readiness): the result is the oracle's within rounding
+and the same bits in every valid order.
 """
 import os
 import subprocess
@@ -175,6 +177,23 @@ def test_pattern_errors():
     assert e.value.status == ick.ick.IC_ERR_ARG
     with pytest.raises(ick.IckError):
         ick.ic_symbolic(p.rowptr, p.colind, 1, block_rows=9000, host_only=1)
+    with pytest.raises(ick.IckError) as e:
+        ick.ic_symbolic(p.rowptr, p.colind, 1, warps_per_cta=24, host_only=1)
+    assert e.value.status == ick.ick.IC_ERR_ARG
+
+
+def test_launch_shape_defaults():
+    """One system: 32-warp CTAs; a batch: 16-warp CTAs; rows per Herk/Gemm item follow
+    the warps unless given."""
+    p = synth.poisson2d_5pt(6, 5)
+    one = ick.ic_stats(ick.ic_symbolic(p.rowptr, p.colind, 1, host_only=1))
+    assert (one["warps_per_cta"], one["rows_per_item"]) == (32, 32)
+    batch = ick.ic_stats(ick.ic_symbolic_batch([(p.rowptr, p.colind)] * 3, 1, host_only=1))
+    assert (batch["warps_per_cta"], batch["rows_per_item"]) == (16, 16)
+    given = ick.ic_stats(ick.ic_symbolic(p.rowptr, p.colind, 1, warps_per_cta=8, rows_per_item=5, host_only=1))
+    assert (given["warps_per_cta"], given["rows_per_item"]) == (8, 5)
+    only_warps = ick.ic_stats(ick.ic_symbolic(p.rowptr, p.colind, 1, warps_per_cta=16, host_only=1))
+    assert only_warps["rows_per_item"] == 16
 
 
 def test_empty_matrix():
@@ -196,7 +215,7 @@ def _plan(h):
 def test_block_pattern_and_dag_invariants():
     prob = synth.laplace3d_27pt(8)
     perm, ranges = ick.ic_nd_grid(8, 8, 8, 1, 40)
-    h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=48, host_only=1)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=48, host_only=1, exact=1)
     urp, ucol, cp, cpos, rng, bptr, bcol, d, tg = _plan(h)
     n = prob.n
     blk = np.searchsorted(rng, np.arange(n), side="right") - 1
@@ -304,21 +323,97 @@ def test_plan_in_random_orders_matches_oracle_bitwise(orc, case):
         prob = synth.elasticity3d_q1(4, seed=4004)
         perm, ranges = ick.ic_nd_grid(5, 5, 5, 3, 90, keep=prob.keep)
         k, br = 1, 70
-    h = ick.ic_symbolic(prob.rowptr, prob.colind, k, perm, ranges, block_rows=br, host_only=1)
     o = orc.OracleIC.from_problem(prob, perm, k)
     assert o.numeric(prob.vals) == 0
     lref = o.values()
     lrp, lci, _ = o.pattern()
-    d = ick.ic_get_tasks(h)
+    amax = np.abs(prob.vals).max()
     g = np.random.default_rng(case)
-    for trial in range(2):
-        order = _random_topo(d, g)
-        urp, ucol, U = _execute_plan(prob, perm, h, order)
-        # L_ij = U_ji: map the oracle's lower entries onto U positions
-        n = prob.n
-        rows = np.repeat(np.arange(n), np.diff(lrp))
-        upos = urp[lci] + np.array([np.searchsorted(ucol[urp[c]:urp[c + 1]], r) for r, c in zip(rows, lci)])
-        assert np.array_equal(U[upos], lref), (case, trial)
+    for exact in (1, 0):
+        h = ick.ic_symbolic(prob.rowptr, prob.colind, k, perm, ranges, block_rows=br, host_only=1, exact=exact)
+        d = ick.ic_get_tasks(h)
+        first = None
+        for trial in range(2):
+            order = _random_topo(d, g)
+            urp, ucol, U = _execute_plan(prob, perm, h, order)
+            # L_ij = U_ji: map the oracle's lower entries onto U positions
+            n = prob.n
+            rows = np.repeat(np.arange(n), np.diff(lrp))
+            upos = urp[lci] + np.array([np.searchsorted(ucol[urp[c]:urp[c + 1]], r) for r, c in zip(rows, lci)])
+            if exact:
+                # the task generator's k order per block: the oracle's operation sequence
+                assert np.array_equal(U[upos], lref), (case, trial)
+            else:
+                # chains ordered by readiness: the same sums in another order, and one
+                # fixed order per entry whatever the topological order of the run
+                assert np.abs(U[upos] - lref).max() <= 1e-12 * amax, (case, trial)
+                if first is None:
+                    first = U.copy()
+                assert np.array_equal(U, first), (case, trial)
+
+
+def _chains(d):
+    """Per written block: (Chol/Trsm task, updates in generation order); pred sets."""
+    nt = len(d["type"])
+    pp, pr = d["pred_ptr"], d["pred"]
+    preds = [set(pr[pp[t]:pp[t + 1]].tolist()) for t in range(nt)]
+    ups, final = {}, {}
+    for t in range(nt):
+        ty, k, i, j = (int(d[x][t]) for x in ("type", "k", "i", "j"))
+        if ty >= 2:
+            ups.setdefault((i, j), []).append(t)
+        else:
+            final[(k, k) if ty == 0 else (k, j)] = t
+    return preds, ups, final
+
+
+def test_fma_plan_reorders_update_chains():
+    """Without exact, the updates into a block form one chain in the order of their
+    inputs' estimated readiness: the same tasks and data dependencies as the task
+    generator's plan, each block's updates a permutation of its k-ordered chain, ending
+    in the block's Chol/Trsm; on an ND-ordered grid some chains leave k order."""
+    prob = synth.laplace3d_27pt(12)
+    perm, ranges = ick.ic_nd_grid(12, 12, 12, 1, 60)
+    he = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=64, host_only=1, exact=1)
+    hf = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=64, host_only=1)
+    de, df = ick.ic_get_tasks(he), ick.ic_get_tasks(hf)
+    for x in ("type", "k", "i", "j"):
+        assert np.array_equal(de[x], df[x])
+    nt = len(df["type"])
+    _random_topo(df, np.random.default_rng(0))  # acyclic, every task reachable
+    preds, ups, final = _chains(df)
+    trsm = {(int(df["k"][t]), int(df["j"][t])): t for t in range(nt) if df["type"][t] == 1}
+    chol = {int(df["k"][t]): t for t in range(nt) if df["type"][t] == 0}
+    moved = 0
+    for blk, us in ups.items():
+        inset = set(us)
+        # each update: its inputs Trsm(k,i), Trsm(k,j) and at most one update of the block
+        prev = {}
+        for u in us:
+            k, i, j = (int(df[x][u]) for x in ("k", "i", "j"))
+            src = {trsm[(k, i)], trsm[(k, j)]}
+            assert src <= preds[u]
+            rest = preds[u] - src
+            assert rest <= inset and len(rest) <= 1
+            prev[u] = next(iter(rest)) if rest else None
+        # one chain through all of them, ending in the block's Chol/Trsm
+        heads = [u for u in us if prev[u] is None]
+        assert len(heads) == 1
+        nxt = {p: u for u, p in prev.items() if p is not None}
+        chain = [heads[0]]
+        while chain[-1] in nxt:
+            chain.append(nxt[chain[-1]])
+        assert sorted(chain) == sorted(us)
+        f = final[blk]
+        assert preds[f] & inset == {chain[-1]}
+        moved += chain != sorted(us)
+    for t in range(nt):
+        if df["type"][t] == 1:
+            assert chol[int(df["k"][t])] in preds[t]
+    assert moved > 0
+    s_e, s_f = ick.ic_stats(he), ick.ic_stats(hf)
+    assert s_e["ntasks"] == s_f["ntasks"] and s_e["nitems"] == s_f["nitems"]
+    assert 1 <= s_f["critical_path"] <= nt
 
 
 # ------------------------------------------------------------------ batches (block-diagonal unions)
@@ -362,7 +457,8 @@ def test_batch_plan_executes_bitwise_per_system(orc):
     union = synth.matrices._from_coo("union", off, np.concatenate(rows), np.concatenate(cols),
                                      np.concatenate(vals), 0)
     uperm = np.concatenate([pm + o for pm, o in zip(perms, np.cumsum([0] + [p.n for p in probs])[:-1])])
-    h = ick.ic_symbolic_batch([(p.rowptr, p.colind) for p in probs], 1, perms, host_only=1, block_rows=48)
+    h = ick.ic_symbolic_batch([(p.rowptr, p.colind) for p in probs], 1, perms, host_only=1, block_rows=48,
+                              exact=1)
     d = ick.ic_get_tasks(h)
     urp, ucol, U = _execute_plan(union, uperm, h, _random_topo(d, np.random.default_rng(5)))
     offs = ick.ic_batch_info(h)
