@@ -216,11 +216,98 @@ int check_pattern(const ic_csr_pattern* A, std::string& err) {
     return IC_OK;
 }
 
+// Order of the updates into each block (FMA mode).  The task generator serialises the
+// Herk/Gemm updates of block (i,j) in ascending k, so an update whose inputs are ready
+// early waits behind every earlier-k update, however late their inputs come; with a
+// geometric ND ordering the updates from one half's top separator hold back those from
+// the other half's whole subtree.  Any order of the chain gives a correct factor (the
+// same sums, rounded in another order), so the chain is rebuilt in the order of its
+// inputs' estimated readiness: an ASAP schedule of the graph under a rough cost model
+// (a fixed cost per task plus a cost per pivot application, Chol/Trsm rows spread over
+// a CTA's warps, Herk/Gemm rows over CTAs), computed in task generation order, which
+// settles every chain before its consumer (the Chol or Trsm of that block) is reached.
+// Dependencies otherwise stay those of the task generator: Trsm(k,j) after Chol(k) and
+// the last update of (k,j); an update after Trsm(k,i) and Trsm(k,j).
+void order_updates(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
+    constexpr double kTaskCost = 3.0, kPivotCost = 0.7, kRowsInParallel = 32.0;
+    const int64_t nt = int64_t(P.task.size());
+    auto block_id = [&](int64_t i, int64_t j) -> int64_t {
+        auto b = P.bcol.begin() + P.bptr[i], e = P.bcol.begin() + P.bptr[i + 1];
+        auto it = std::lower_bound(b, e, int32_t(j));
+        return (it != e && *it == j) ? int64_t(it - P.bcol.begin()) : -1;
+    };
+    std::vector<double> cost(nt), fin(nt, 0.0);
+    for (int64_t t = 0; t < nt; ++t) {
+        double sum = 0.0, mx = 0.0;
+        for (const int4& g : ttgt[t]) {
+            sum += double(g.z - g.y);
+            mx = std::max(mx, double(g.z - g.y));
+        }
+        const int type = P.task[t].x;
+        cost[t] = kTaskCost + kPivotCost * ((type == T_CHOL || type == T_TRSM) ? sum / kRowsInParallel : mx);
+    }
+    const size_t nblk = P.bcol.size();
+    std::vector<int32_t> writer(nblk, -1);             // Chol/Trsm task that produced a block
+    std::vector<std::vector<int32_t>> upd(nblk);       // updates into a block, generation order
+    std::vector<std::vector<int32_t>> pred(nt);
+    std::vector<std::pair<double, int32_t>> key;
+    for (int64_t t = 0; t < nt; ++t) {
+        const int4 T = P.task[t];
+        if (T.x == T_HERK || T.x == T_GEMM) {
+            upd[block_id(T.z, T.w)].push_back(int32_t(t));
+            continue;
+        }
+        const int64_t b = block_id(T.y, T.x == T_CHOL ? T.y : T.w);
+        key.clear();
+        for (int32_t u : upd[b]) {
+            const int4 Uu = P.task[u];
+            const int32_t si = writer[block_id(Uu.y, Uu.z)], sj = writer[block_id(Uu.y, Uu.w)];
+            pred[u].assign({si});
+            if (sj != si) pred[u].push_back(sj);
+            key.emplace_back(std::max(fin[si], fin[sj]), u);
+        }
+        std::stable_sort(key.begin(), key.end(),
+                         [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& c) {
+                             return a.first < c.first;
+                         });
+        int32_t prev = -1;
+        for (const auto& ku : key) {
+            const int32_t u = ku.second;
+            double start = ku.first;
+            if (prev >= 0) {
+                pred[u].push_back(prev);
+                start = std::max(start, fin[prev]);
+            }
+            fin[u] = start + cost[u];
+            prev = u;
+        }
+        double start = 0.0;
+        if (T.x == T_TRSM) {
+            const int32_t c = writer[block_id(T.y, T.y)];
+            pred[t].push_back(c);
+            start = fin[c];
+        }
+        if (prev >= 0) {
+            pred[t].push_back(prev);
+            start = std::max(start, fin[prev]);
+        }
+        fin[t] = start + cost[t];
+        writer[b] = int32_t(t);
+    }
+    P.pred_ptr.assign(1, 0);
+    P.pred.clear();
+    for (int64_t t = 0; t < nt; ++t) {
+        std::sort(pred[t].begin(), pred[t].end());
+        P.pred.insert(P.pred.end(), pred[t].begin(), pred[t].end());
+        P.pred_ptr.push_back(int64_t(P.pred.size()));
+    }
+}
+
 }  // namespace
 
 int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
-               int64_t nranges, int block_rows, int rows_per_item, int threads, HostPlan& P,
-               std::string& err) {
+               int64_t nranges, int block_rows, int rows_per_item, int threads, bool k_order,
+               HostPlan& P, std::string& err) {
     if (!A) { err = "NULL pattern"; return IC_ERR_ARG; }
     if (k < 0) { err = "k < 0"; return IC_ERR_ARG; }
     if (block_rows <= 0 || block_rows > kMaxBlockRows) { err = "block_rows out of range"; return IC_ERR_ARG; }
@@ -517,6 +604,8 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
         std::copy(tend[t].begin(), tend[t].end(), P.tgt_end.begin() + P.tgt_ptr[t]);
     }
 
+    if (!k_order) order_updates(P, ttgt);
+
     // items, successors, in-degrees, seeds, critical path, type counts
     P.nitems.resize(nt);
     P.indeg0.resize(nt);
@@ -546,13 +635,25 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
         if (P.indeg0[t] == 0)
             for (int32_t c = 0; c < P.nitems[t]; ++c) P.seeds.push_back(make_int2(int(t), c));
     {
+        // longest chain of tasks, over a topological order (in FMA mode an update's
+        // predecessor in its block's chain can have a larger index)
         std::vector<int64_t> depth(nt, 1);
-        int64_t best = nt ? 1 : 0;
-        for (int64_t t = 0; t < nt; ++t) {
-            for (int64_t e = P.pred_ptr[t]; e < P.pred_ptr[t + 1]; ++e)
-                depth[t] = std::max(depth[t], depth[P.pred[e]] + 1);
+        std::vector<int32_t> left(P.indeg0), ready;
+        for (int64_t t = 0; t < nt; ++t)
+            if (left[t] == 0) ready.push_back(int32_t(t));
+        int64_t best = nt ? 1 : 0, seen = 0;
+        while (!ready.empty()) {
+            const int32_t t = ready.back();
+            ready.pop_back();
+            ++seen;
             best = std::max(best, depth[t]);
+            for (int64_t e = P.succ_ptr[t]; e < P.succ_ptr[t + 1]; ++e) {
+                const int32_t s = P.succ[e];
+                depth[s] = std::max(depth[s], depth[t] + 1);
+                if (--left[s] == 0) ready.push_back(s);
+            }
         }
+        if (seen != nt) { err = "task graph has a cycle"; return IC_ERR_ARG; }
         P.critical_path = best;
     }
 

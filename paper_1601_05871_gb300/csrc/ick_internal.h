@@ -277,9 +277,11 @@ cudaError_t launch_mlp_grad(const MlpDev& M, const float* X, const float* t, lon
 cudaError_t launch_mlp_adam(const MlpDev& M, float lr, int step, cudaStream_t s);
 
 // Host symbolic phase (host.cpp).
+// k_order: updates into each block applied in ascending k (the task generator's order,
+// which exact mode needs); otherwise ordered by the estimated readiness of their inputs.
 int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
-               int64_t nranges, int block_rows, int rows_per_item, int threads, HostPlan& P,
-               std::string& err);
+               int64_t nranges, int block_rows, int rows_per_item, int threads, bool k_order,
+               HostPlan& P, std::string& err);
 void build_solve_dag(HostPlan& P, int threads);
 int block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, std::vector<int4>& task,
               std::vector<int64_t>& pred_ptr, std::vector<int32_t>& pred);
