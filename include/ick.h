@@ -103,6 +103,9 @@ typedef struct {
     int64_t solve_depth[2];/* levels of the forward / backward solve's row DAG        */
     int64_t warps_per_cta;/* warps per CTA of the persistent kernel (defaults resolved) */
     int64_t rows_per_item;/* target rows per Herk/Gemm work item (defaults resolved)    */
+    int64_t nsplit;       /* Chol/Trsm tasks spread over several CTAs (expected to run
+                             with little else in flight; their row flags in global
+                             memory)                                                  */
 } ic_stats_t;
 
 typedef struct ic_handle ic_handle;

@@ -182,6 +182,10 @@ int upload_plan(ic_handle* h) {
     if ((st = h->upload(&D.succ, P.succ))) return st;
     if ((st = h->upload(&D.indeg0, P.indeg0))) return st;
     if ((st = h->upload(&D.seeds, P.seeds))) return st;
+    if ((st = h->upload(&D.flag_off, P.flag_off))) return st;
+    D.nflags = int(P.nflags);
+    if ((st = h->alloc(&D.gflag, size_t(P.nflags > 0 ? P.nflags : 1)))) return st;
+    if ((st = h->alloc(&D.row_next, P.task.size()))) return st;
     // factor values (FP64, or FP32 plus FP64 pivots), padded by 16 bytes
     const bool f32 = h->opts.dtype == IC_F32;
     double* uval = nullptr;
@@ -893,6 +897,7 @@ int ic_stats(const ic_handle* h, ic_stats_t* out) {
     out->solve_depth[1] = P.bwd_depth;
     out->warps_per_cta = h->opts.warps_per_cta;
     out->rows_per_item = h->opts.rows_per_item;
+    out->nsplit = P.nsplit;
     return IC_OK;
 }
 

@@ -216,27 +216,13 @@ int check_pattern(const ic_csr_pattern* A, std::string& err) {
     return IC_OK;
 }
 
-// Order of the updates into each block (FMA mode).  The task generator serialises the
-// Herk/Gemm updates of block (i,j) in ascending k, so an update whose inputs are ready
-// early waits behind every earlier-k update, however late their inputs come; with a
-// geometric ND ordering the updates from one half's top separator hold back those from
-// the other half's whole subtree.  Any order of the chain gives a correct factor (the
-// same sums, rounded in another order), so the chain is rebuilt in the order of its
-// inputs' estimated readiness: an ASAP schedule of the graph under a rough cost model
-// (a fixed cost per task plus a cost per pivot application, Chol/Trsm rows spread over
-// a CTA's warps, Herk/Gemm rows over CTAs), computed in task generation order, which
-// settles every chain before its consumer (the Chol or Trsm of that block) is reached.
-// Dependencies otherwise stay those of the task generator: Trsm(k,j) after Chol(k) and
-// the last update of (k,j); an update after Trsm(k,i) and Trsm(k,j).
-void order_updates(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
+// Rough duration of every task for the host's ASAP estimates: a fixed cost per task
+// plus a cost per pivot application, a Chol/Trsm task's rows spread over one CTA's
+// warps, a Herk/Gemm task's rows over CTAs (so its slowest row counts).
+std::vector<double> task_costs(const HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
     constexpr double kTaskCost = 3.0, kPivotCost = 0.7, kRowsInParallel = 32.0;
     const int64_t nt = int64_t(P.task.size());
-    auto block_id = [&](int64_t i, int64_t j) -> int64_t {
-        auto b = P.bcol.begin() + P.bptr[i], e = P.bcol.begin() + P.bptr[i + 1];
-        auto it = std::lower_bound(b, e, int32_t(j));
-        return (it != e && *it == j) ? int64_t(it - P.bcol.begin()) : -1;
-    };
-    std::vector<double> cost(nt), fin(nt, 0.0);
+    std::vector<double> cost(nt);
     for (int64_t t = 0; t < nt; ++t) {
         double sum = 0.0, mx = 0.0;
         for (const int4& g : ttgt[t]) {
@@ -246,6 +232,29 @@ void order_updates(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
         const int type = P.task[t].x;
         cost[t] = kTaskCost + kPivotCost * ((type == T_CHOL || type == T_TRSM) ? sum / kRowsInParallel : mx);
     }
+    return cost;
+}
+
+// Order of the updates into each block (FMA mode).  The task generator serialises the
+// Herk/Gemm updates of block (i,j) in ascending k, so an update whose inputs are ready
+// early waits behind every earlier-k update, however late their inputs come; with a
+// geometric ND ordering the updates from one half's top separator hold back those from
+// the other half's whole subtree.  Any order of the chain gives a correct factor (the
+// same sums, rounded in another order), so the chain is rebuilt in the order of its
+// inputs' estimated readiness: an ASAP schedule of the graph under task_costs,
+// computed in task generation order, which settles every chain before its consumer
+// (the Chol or Trsm of that block) is reached.
+// Dependencies otherwise stay those of the task generator: Trsm(k,j) after Chol(k) and
+// the last update of (k,j); an update after Trsm(k,i) and Trsm(k,j).
+void order_updates(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
+    const int64_t nt = int64_t(P.task.size());
+    auto block_id = [&](int64_t i, int64_t j) -> int64_t {
+        auto b = P.bcol.begin() + P.bptr[i], e = P.bcol.begin() + P.bptr[i + 1];
+        auto it = std::lower_bound(b, e, int32_t(j));
+        return (it != e && *it == j) ? int64_t(it - P.bcol.begin()) : -1;
+    };
+    const std::vector<double> cost = task_costs(P, ttgt);
+    std::vector<double> fin(nt, 0.0);
     const size_t nblk = P.bcol.size();
     std::vector<int32_t> writer(nblk, -1);             // Chol/Trsm task that produced a block
     std::vector<std::vector<int32_t>> upd(nblk);       // updates into a block, generation order
@@ -300,6 +309,71 @@ void order_updates(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
         std::sort(pred[t].begin(), pred[t].end());
         P.pred.insert(P.pred.end(), pred[t].begin(), pred[t].end());
         P.pred_ptr.push_back(int64_t(P.pred.size()));
+    }
+}
+
+// Chol and Trsm tasks that would run nearly alone get several CTAs.  Such a task's rows
+// form dependence levels inside its block; one CTA works through them with per-row
+// flags in shared memory, and at the end of the factorization (the top separators) it
+// is the only work on the GPU, bound by one SM's issue rate.  Split into kSplitItems
+// items, the task's rows are claimed from a counter in global memory by every CTA that
+// holds one of its items, and row completion flags live in global memory.  The
+// estimate: an ASAP schedule of the final graph under task_costs; a Chol/Trsm task of
+// at least kSplitMinRows target rows whose start finds fewer than kSplitIdle other
+// work items in flight is split.
+void split_tail_tasks(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
+    constexpr int kSplitItems = 4, kSplitMinRows = 512;
+    constexpr int64_t kSplitIdle = 64;
+    const int64_t nt = int64_t(P.task.size());
+    P.flag_off.assign(nt, -1);
+    P.nflags = 0;
+    P.nsplit = 0;
+    if (nt == 0) return;
+    const std::vector<double> cost = task_costs(P, ttgt);
+    // ASAP over a topological order of the graph
+    std::vector<int32_t> left(nt), order;
+    std::vector<std::vector<int32_t>> succ(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        left[t] = int32_t(P.pred_ptr[t + 1] - P.pred_ptr[t]);
+        for (int64_t e = P.pred_ptr[t]; e < P.pred_ptr[t + 1]; ++e) succ[P.pred[e]].push_back(int32_t(t));
+        if (left[t] == 0) order.push_back(int32_t(t));
+    }
+    std::vector<double> start(nt, 0.0), fin(nt, 0.0);
+    for (size_t q = 0; q < order.size(); ++q) {
+        const int32_t t = order[q];
+        fin[t] = start[t] + cost[t];
+        for (int32_t s : succ[t]) {
+            start[s] = std::max(start[s], fin[t]);
+            if (--left[s] == 0) order.push_back(s);
+        }
+    }
+    if (int64_t(order.size()) != nt) return;  // not a DAG: reported by the caller
+    // items in flight at each task's start: sweep over (time, +-items) events
+    std::vector<std::pair<double, int64_t>> ev;
+    ev.reserve(2 * nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        ev.emplace_back(fin[t], -int64_t(P.nitems[t]));  // ends sort before starts at equal times
+        ev.emplace_back(start[t], int64_t(P.nitems[t]));
+    }
+    std::sort(ev.begin(), ev.end());
+    std::vector<std::pair<double, int32_t>> starts;
+    for (int64_t t = 0; t < nt; ++t) {
+        const int type = P.task[t].x;
+        if ((type == T_CHOL || type == T_TRSM) && int64_t(ttgt[t].size()) >= kSplitMinRows)
+            starts.emplace_back(start[t], int32_t(t));
+    }
+    std::sort(starts.begin(), starts.end());
+    int64_t live = 0;
+    size_t e = 0;
+    for (const auto& st : starts) {
+        while (e < ev.size() && ev[e].first <= st.first) live += ev[e++].second;
+        const int32_t t = st.second;
+        if (live - P.nitems[t] >= kSplitIdle) continue;
+        const int32_t blk = P.task[t].y;
+        P.flag_off[t] = int32_t(P.nflags);
+        P.nflags += P.ranges[blk + 1] - P.ranges[blk];
+        P.nitems[t] = kSplitItems;
+        ++P.nsplit;
     }
 }
 
@@ -616,10 +690,12 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
         const int32_t cnt = P.tgt_ptr[t + 1] - P.tgt_ptr[t];
         P.nitems[t] = (T.x == T_CHOL || T.x == T_TRSM) ? 1
                       : std::max<int32_t>(1, (cnt + rows_per_item - 1) / rows_per_item);
-        P.total_items += P.nitems[t];
         P.indeg0[t] = int32_t(P.pred_ptr[t + 1] - P.pred_ptr[t]);
         ++P.ntype[T.x];
     }
+    split_tail_tasks(P, ttgt);
+    if (P.nflags > INT32_MAX / 2) { err = "too many split rows"; return IC_ERR_ARG; }
+    for (int64_t t = 0; t < nt; ++t) P.total_items += P.nitems[t];
     if (P.total_items > INT32_MAX / 2) { err = "too many work items"; return IC_ERR_ARG; }
     P.succ_ptr.assign(nt + 1, 0);
     for (int32_t d : P.pred) ++P.succ_ptr[d + 1];

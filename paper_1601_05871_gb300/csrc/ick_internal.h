@@ -66,6 +66,10 @@ struct HostPlan {
     std::vector<int32_t> pred;
     std::vector<int32_t> succ_ptr, succ;
     std::vector<int32_t> indeg0, nitems;
+    // Chol/Trsm tasks spread over several CTAs (nitems > 1): offset of their rows'
+    // completion flags in global memory, -1 for the others (flags in shared memory)
+    std::vector<int32_t> flag_off;
+    int64_t nflags = 0, nsplit = 0;
     std::vector<int32_t> tgt_ptr;   // ntasks + 1
     std::vector<int4> tgt;          // (r, csc_a, csc_b, seg_begin)
     std::vector<int32_t> tgt_end;   // seg_end
@@ -112,6 +116,8 @@ struct DevPlan {
     const int* succ;
     const int* indeg0;
     const int2* seeds;
+    const int* flag_off;   // per task: rows' flags in gflag (split Chol/Trsm) or -1
+    int nflags;
     // mutable state
     void* uval;            // factor values (double for IC_F64)
     int* indeg;
@@ -126,6 +132,8 @@ struct DevPlan {
     double* udiag;         // IC_F32: FP64 diagonal pivots (U_ii) of the factor
     const int* diag_src;   // IC_F32: index of A's diagonal value of each row
     int* epoch_dev;        // queue epoch, advanced on the device before each numeric phase
+    unsigned char* gflag;  // completion flags of the rows of split Chol/Trsm tasks
+    int* row_next;         // per task: next target to claim (split Chol/Trsm)
 };
 
 // Status bits written by the kernels into counters[2].

@@ -95,7 +95,9 @@ __device__ __forceinline__ void note_breakdown(const DevPlan& P, int r) {
     atomicMin(P.brk_row, (long long)r);
 }
 
-// Wait until done[local] is set by another warp of this CTA; false on timeout/abort.
+// Wait until done[local] is set by another warp (of this CTA, flags in shared memory;
+// GF: of any CTA, flags in global memory); false on timeout/abort.
+template <bool GF>
 __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int local,
                          unsigned long long deadline) {
     unsigned spins = 0;
@@ -106,7 +108,8 @@ __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int loc
         }
         __nanosleep(20);
     }
-    __threadfence_block();
+    if (GF) __threadfence();
+    else __threadfence_block();
     return true;
 }
 
@@ -171,20 +174,23 @@ __device__ __forceinline__ void apply_staged(WarpBuf<T>& W, const int* cols, con
 
 // Issue the copies of pivot q's source segment into ring slot q % kRing.  Returns 1
 // when the slot will hold the data (or the segment is empty), 0 when the pivot row is
-// not complete yet (Chol/Trsm): then the consumer waits and loads it directly.
-template <int MODE, typename T>
+// not complete yet (Chol/Trsm): then the consumer waits and loads it directly.  Bit q
+// of seen: pivot q's row was already seen complete (then no flag is read again).
+template <int MODE, bool GF, typename T>
 __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf<T>& W, int q,
-                                           bool start_at_r, int rbase, volatile unsigned char* done) {
+                                           bool start_at_r, int rbase, volatile unsigned char* done,
+                                           unsigned seen) {
     constexpr int EPC = 16 / sizeof(T);  // elements per 16-byte chunk
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const int4 pi = W.piv[q];
     if (pi.w == 0) return 1;
-    if (MODE != M_UPDATE) {
+    if (MODE != M_UPDATE && !((seen >> q) & 1u)) {
         int f = 0;
         if (lane == 0) f = done[pi.x - rbase];
         if (!__shfl_sync(full, f, 0)) return 0;
-        __threadfence_block();
+        if (GF) __threadfence();
+        else __threadfence_block();
     }
     Slot<T>& S = W.ring[q % kRing];
     const int n = min(pi.w, kSegStage);
@@ -218,7 +224,7 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf
 // shared-memory slots while the current one is applied.  For Chol and Trsm a copy is
 // issued only once the pivot row's completion flag is seen; a pivot that was not
 // complete at issue time is waited for and loaded directly when its turn comes.
-template <int MODE, bool EXACT, typename T>
+template <int MODE, bool EXACT, bool GF, typename T>
 __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, int tb, int te,
                                int srcblk, bool start_at_r, int rbase,
                                volatile unsigned char* done, WarpBuf<T>& W,
@@ -266,6 +272,7 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
         __syncwarp();
         for (int q0 = ca; q0 < cb; q0 += 32) {
             const int nq = min(32, cb - q0);
+            int dn = 1;
             if (lane < nq) {
                 const int2 pe = __ldg(P.csc + q0 + lane);
                 int sb, len;
@@ -278,18 +285,27 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                     len = s.y - s.x;
                 }
                 W.piv[lane] = make_int4(pe.x, pe.y, sb, len);
+                // Chol/Trsm: the completion flags of the whole batch, one per lane
+                if (MODE != M_UPDATE && len > 0) dn = done[pe.x - rbase];
+            }
+            const unsigned seen = __ballot_sync(full, dn != 0);
+            if (MODE != M_UPDATE) {
+                if (GF) __threadfence();
+                else __threadfence_block();
             }
             __syncwarp();
             unsigned issued = 0;
 #pragma unroll
             for (int s = 0; s < kRing - 1; ++s) {
-                if (s < nq) issued |= unsigned(issue_pivot<MODE>(P, U, W, s, start_at_r, rbase, done)) << s;
+                if (s < nq)
+                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, W, s, start_at_r, rbase, done, seen)) << s;
                 cp_async_commit();
             }
             for (int q = 0; q < nq; ++q) {
                 const int nxt = q + kRing - 1;
                 if (nxt < nq)
-                    issued |= unsigned(issue_pivot<MODE>(P, U, W, nxt, start_at_r, rbase, done)) << nxt;
+                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, W, nxt, start_at_r, rbase, done, seen))
+                              << nxt;
                 cp_async_commit();
                 cp_async_wait<kRing - 1>();
                 __syncwarp();
@@ -306,11 +322,12 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                         first_direct = n;
                     } else {
                         int ok = 1;
-                        if (lane == 0) ok = wait_row(P, done, pi.x - rbase, deadline);
+                        if (lane == 0) ok = wait_row<GF>(P, done, pi.x - rbase, deadline);
                         if (!__shfl_sync(full, ok, 0)) {
                             cp_async_wait<0>();
                             return;
                         }
+                        if (GF) __threadfence();
                         a = ld_cg(U + pi.y);
                     }
                     for (int o = first_direct + lane; o < pi.w; o += 32)
@@ -416,7 +433,31 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
         const int4 Tk = __ldg(P.task + task);
         const int t0 = __ldg(P.tgt_ptr + task), nt = __ldg(P.tgt_ptr + task + 1) - t0;
 
-        if (Tk.x == T_CHOL || Tk.x == T_TRSM) {
+        if ((Tk.x == T_CHOL || Tk.x == T_TRSM) && __ldg(P.flag_off + task) >= 0) {
+            // a split task: every CTA holding one of its items claims rows from the
+            // task's counter; completion flags in global memory
+            const int blk = Tk.y;
+            const int rbase = __ldg(P.ranges + blk);
+            volatile unsigned char* gdone = P.gflag + __ldg(P.flag_off + task);
+            for (;;) {
+                int idx = 0;
+                if (lane == 0) idx = atomicAdd(P.row_next + task, 1);
+                idx = __shfl_sync(0xffffffffu, idx, 0);
+                if (idx >= nt) break;
+                const int4 g = __ldg(P.tgt + t0 + idx);
+                const int gend = __ldg(P.tgt_end + t0 + idx);
+                if (Tk.x == T_CHOL)
+                    process_target<M_CHOL, EXACT, true, T>(P, U, g.x, g.y, g.z, g.w, gend, blk, true, rbase,
+                                                           gdone, W, deadline);
+                else
+                    process_target<M_TRSM, EXACT, true, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, false,
+                                                           rbase, gdone, W, deadline);
+                // every lane's stores of the row, then the flag
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) gdone[g.x - rbase] = 1;
+            }
+        } else if (Tk.x == T_CHOL || Tk.x == T_TRSM) {
             const int blk = Tk.y;
             const int rbase = __ldg(P.ranges + blk), nrows = __ldg(P.ranges + blk + 1) - rbase;
             for (int i = threadIdx.x; i < nrows; i += WARPS * 32) s_done[i] = 0;
@@ -430,11 +471,11 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
                 const int4 g = __ldg(P.tgt + t0 + idx);
                 const int gend = __ldg(P.tgt_end + t0 + idx);
                 if (Tk.x == T_CHOL)
-                    process_target<M_CHOL, EXACT, T>(P, U, g.x, g.y, g.z, g.w, gend, blk, true, rbase,
-                                                     done, W, deadline);
+                    process_target<M_CHOL, EXACT, false, T>(P, U, g.x, g.y, g.z, g.w, gend, blk, true,
+                                                            rbase, done, W, deadline);
                 else
-                    process_target<M_TRSM, EXACT, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, false, rbase,
-                                                     done, W, deadline);
+                    process_target<M_TRSM, EXACT, false, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, false,
+                                                            rbase, done, W, deadline);
                 __threadfence_block();
                 __syncwarp();
                 if (lane == 0) done[g.x - rbase] = 1;
@@ -447,11 +488,11 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
                 const int4 g = __ldg(P.tgt + t0 + idx);
                 const int gend = __ldg(P.tgt_end + t0 + idx);
                 if (herk)
-                    process_target<M_UPDATE, EXACT, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, true, 0, done,
-                                                       W, deadline);
+                    process_target<M_UPDATE, EXACT, false, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, true, 0,
+                                                              done, W, deadline);
                 else
-                    process_target<M_UPDATE, EXACT, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, false, 0, done,
-                                                       W, deadline);
+                    process_target<M_UPDATE, EXACT, false, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, false, 0,
+                                                              done, W, deadline);
             }
         }
         __threadfence();
@@ -522,7 +563,9 @@ __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double
     for (int t = tid; t < P.ntasks; t += stride) {
         P.indeg[t] = __ldg(P.indeg0 + t);
         P.items_left[t] = __ldg(P.nitems + t);
+        P.row_next[t] = 0;
     }
+    for (int i = tid; i < P.nflags; i += stride) P.gflag[i] = 0;
     for (int s = tid; s < P.nseeds; s += stride) {
         P.queue[s] = __ldg(P.seeds + s);
         P.qstamp[s] = epoch;

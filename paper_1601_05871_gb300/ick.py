@@ -45,7 +45,7 @@ class ic_stats_t(C.Structure):
                 ("nitems", C.c_int64), ("critical_path", C.c_int64), ("max_level", C.c_int64),
                 ("flops", C.c_double), ("bytes", C.c_double), ("symbolic_s", C.c_double),
                 ("grid_ctas", C.c_int64), ("solve_depth", C.c_int64 * 2), ("warps_per_cta", C.c_int64),
-                ("rows_per_item", C.c_int64)]
+                ("rows_per_item", C.c_int64), ("nsplit", C.c_int64)]
 
 
 def load():

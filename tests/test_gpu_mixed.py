@@ -71,6 +71,14 @@ def test_f32_factor_within_bound(ick, orc, case):
     assert err <= F32_TOL, err
 
 
+def test_f32_tasks_split_over_ctas(ick, orc):
+    prob = synth.laplace3d_27pt(24)
+    perm, ranges = ick.ic_nd_grid(24, 24, 24, 1, 1024)
+    h, o, err = mixed_vs_oracle(ick, orc, prob, perm, ranges, 2, block_rows=1024)
+    assert ick.ic_stats(h)["nsplit"] > 0
+    assert err <= F32_TOL, err
+
+
 def test_f32_long_rows(ick, orc):
     prob = synth.random_spd(300, 1.0, 12, kind="dense_spd")
     h, o, err = mixed_vs_oracle(ick, orc, prob, None, None, 300, block_rows=100)

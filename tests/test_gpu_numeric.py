@@ -85,6 +85,19 @@ def test_27pt_ic2(ick, orc, warps):
     check_parity(ick, orc, prob, perm, ranges, 2, exact=0, block_rows=300, warps_per_cta=warps)
 
 
+@pytest.mark.parametrize("warps", [16, 32])
+def test_tasks_split_over_ctas(ick, orc, warps):
+    """Chol/Trsm tasks expected to run with little else in flight are spread over
+    several CTAs, rows claimed from a global counter and their flags in global memory:
+    the factor is the one CTA would give (bit-exact in exact mode)."""
+    prob = synth.laplace3d_27pt(24)
+    perm, ranges = ick.ic_nd_grid(24, 24, 24, 1, 1024)
+    for exact in (1, 0):
+        h, o, lv = check_parity(ick, orc, prob, perm, ranges, 2, exact=exact, block_rows=1024,
+                                warps_per_cta=warps)
+        assert ick.ic_stats(h)["nsplit"] > 0
+
+
 def test_rows_wider_than_the_column_map(ick, orc):
     """Natural order of a 5000 x 3 grid in two 7500-row blocks: a row's segment in a
     block reaches 5000 columns past its diagonal, so a target row is cut into chunks

@@ -196,6 +196,27 @@ def test_launch_shape_defaults():
     assert only_warps["rows_per_item"] == 16
 
 
+def test_split_tasks_plan():
+    """Only Chol/Trsm tasks of at least 512 target rows are split (several work items);
+    their blocks' row-flag ranges are disjoint; the item total adds up."""
+    prob = synth.laplace3d_27pt(24)
+    perm, ranges = ick.ic_nd_grid(24, 24, 24, 1, 1024)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=1024, host_only=1)
+    s = ick.ic_stats(h)
+    d = ick.ic_get_tasks(h)
+    nt = len(d["type"])
+    items = 0
+    split = 0
+    for t in range(nt):
+        ntg = len(ick.ic_get_task_targets(h, t))
+        if d["type"][t] >= 2:
+            items += max(1, -(-ntg // s["rows_per_item"]))
+        elif ntg >= 512:
+            split += 1
+    assert 0 < s["nsplit"] <= split
+    assert s["nitems"] == items + (sum(d["type"] < 2) - s["nsplit"]) + 4 * s["nsplit"]
+
+
 def test_empty_matrix():
     h = ick.ic_symbolic(np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), 2, host_only=1)
     s = ick.ic_stats(h)
