@@ -322,7 +322,7 @@ void order_updates(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
 // at least kSplitMinRows target rows whose start finds fewer than kSplitIdle other
 // work items in flight is split.
 void split_tail_tasks(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
-    constexpr int kSplitItems = 4, kSplitMinRows = 512;
+    constexpr int kSplitItems = 8, kSplitMinRows = 512;
     constexpr int64_t kSplitIdle = 64;
     const int64_t nt = int64_t(P.task.size());
     P.flag_off.assign(nt, -1);

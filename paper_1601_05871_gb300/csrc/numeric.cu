@@ -96,7 +96,8 @@ __device__ __forceinline__ void note_breakdown(const DevPlan& P, int r) {
 }
 
 // Wait until done[local] is set by another warp (of this CTA, flags in shared memory;
-// GF: of any CTA, flags in global memory); false on timeout/abort.
+// GF: of any CTA, flags in global memory); false on timeout/abort.  The caller fences
+// before it reads the row.
 template <bool GF>
 __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int local,
                          unsigned long long deadline) {
@@ -108,8 +109,6 @@ __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int loc
         }
         __nanosleep(20);
     }
-    if (GF) __threadfence();
-    else __threadfence_block();
     return true;
 }
 
@@ -175,22 +174,28 @@ __device__ __forceinline__ void apply_staged(WarpBuf<T>& W, const int* cols, con
 // Issue the copies of pivot q's source segment into ring slot q % kRing.  Returns 1
 // when the slot will hold the data (or the segment is empty), 0 when the pivot row is
 // not complete yet (Chol/Trsm): then the consumer waits and loads it directly.  Bit q
-// of seen: pivot q's row was already seen complete (then no flag is read again).
+// of seen: pivot q's row was seen complete.  When pivot q has not been, the flags of
+// all the batch's pivots not seen yet are read again, one per lane, so that rows
+// completed meanwhile cost one round trip together, not one each.
 template <int MODE, bool GF, typename T>
-__device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf<T>& W, int q,
+__device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf<T>& W, int q, int nq,
                                            bool start_at_r, int rbase, volatile unsigned char* done,
-                                           unsigned seen) {
+                                           unsigned& seen) {
     constexpr int EPC = 16 / sizeof(T);  // elements per 16-byte chunk
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const int4 pi = W.piv[q];
     if (pi.w == 0) return 1;
     if (MODE != M_UPDATE && !((seen >> q) & 1u)) {
-        int f = 0;
-        if (lane == 0) f = done[pi.x - rbase];
-        if (!__shfl_sync(full, f, 0)) return 0;
-        if (GF) __threadfence();
-        else __threadfence_block();
+        int dn = 1;
+        if (lane < nq && !((seen >> lane) & 1u)) dn = done[W.piv[lane].x - rbase];
+        const unsigned now = __ballot_sync(full, dn != 0);
+        if (now & ~seen) {
+            if (GF) __threadfence();
+            else __threadfence_block();
+        }
+        seen |= now;
+        if (!((seen >> q) & 1u)) return 0;
     }
     Slot<T>& S = W.ring[q % kRing];
     const int n = min(pi.w, kSegStage);
@@ -288,7 +293,7 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                 // Chol/Trsm: the completion flags of the whole batch, one per lane
                 if (MODE != M_UPDATE && len > 0) dn = done[pe.x - rbase];
             }
-            const unsigned seen = __ballot_sync(full, dn != 0);
+            unsigned seen = __ballot_sync(full, dn != 0);
             if (MODE != M_UPDATE) {
                 if (GF) __threadfence();
                 else __threadfence_block();
@@ -298,13 +303,13 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
 #pragma unroll
             for (int s = 0; s < kRing - 1; ++s) {
                 if (s < nq)
-                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, W, s, start_at_r, rbase, done, seen)) << s;
+                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, W, s, nq, start_at_r, rbase, done, seen)) << s;
                 cp_async_commit();
             }
             for (int q = 0; q < nq; ++q) {
                 const int nxt = q + kRing - 1;
                 if (nxt < nq)
-                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, W, nxt, start_at_r, rbase, done, seen))
+                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, W, nxt, nq, start_at_r, rbase, done, seen))
                               << nxt;
                 cp_async_commit();
                 cp_async_wait<kRing - 1>();
@@ -328,6 +333,8 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                             return;
                         }
                         if (GF) __threadfence();
+                        else __threadfence_block();
+                        seen |= 1u << q;
                         a = ld_cg(U + pi.y);
                     }
                     for (int o = first_direct + lane; o < pi.w; o += 32)

@@ -214,7 +214,7 @@ def test_split_tasks_plan():
         elif ntg >= 512:
             split += 1
     assert 0 < s["nsplit"] <= split
-    assert s["nitems"] == items + (sum(d["type"] < 2) - s["nsplit"]) + 4 * s["nsplit"]
+    assert s["nitems"] == items + (sum(d["type"] < 2) - s["nsplit"]) + 8 * s["nsplit"]
 
 
 def test_empty_matrix():
