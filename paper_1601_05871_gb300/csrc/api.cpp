@@ -201,6 +201,7 @@ int upload_plan(ic_handle* h) {
         CK(cudaMemset(uval, 0, (size_t(P.nnz_u) + 2) * sizeof(double)));
         D.uval = uval;
     }
+    if ((st = h->alloc(&D.urcp, size_t(P.n)))) return st;
     if ((st = h->alloc(&D.indeg, P.task.size()))) return st;
     if ((st = h->alloc(&D.items_left, P.task.size()))) return st;
     if ((st = h->alloc(&D.queue, size_t(P.total_items)))) return st;

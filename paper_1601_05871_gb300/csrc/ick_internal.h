@@ -130,6 +130,7 @@ struct DevPlan {
     unsigned long long* trace;  // NULL, or 4 words per queue slot: start ns, end ns,
                                 // task | chunk << 32, SM id
     double* udiag;         // IC_F32: FP64 diagonal pivots (U_ii) of the factor
+    double* urcp;          // FMA mode: 1/U_ii of every row, kept by its Chol for Trsm
     const int* diag_src;   // IC_F32: index of A's diagonal value of each row
     int* epoch_dev;        // queue epoch, advanced on the device before each numeric phase
     unsigned char* gflag;  // completion flags of the rows of split Chol/Trsm tasks

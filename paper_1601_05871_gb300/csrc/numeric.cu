@@ -71,6 +71,22 @@ __device__ __forceinline__ float sub_product(float acc, float a, float b) {
 
 enum Mode { M_CHOL = 0, M_TRSM = 1, M_UPDATE = 2 };
 
+// 1/sqrt(d) by Newton's iteration for the reciprocal square root,
+// y <- y + y (1 - d y^2) / 2, started from the single-precision estimate: each step
+// about doubles the number of correct bits, so two reach double precision.  Outside
+// the single-precision exponent range (and for d <= 0 or NaN) the library's square
+// root and division are used.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    if (!(d >= 1e-30 && d <= 1e30)) return 1.0 / sqrt(d);
+    double y = double(rsqrtf(float(d)));
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const double e = fma(-(d * y), y, 1.0);
+        y = fma(0.5 * y, e, y);
+    }
+    return y;
+}
+
 struct Smem {
     int task, chunk, next, slot;
     unsigned long long t0;
@@ -112,6 +128,9 @@ __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int loc
     return true;
 }
 
+constexpr int kLenBits = 14;    // pivot descriptor: segment length in the low bits, then
+constexpr int kLenMask = (1 << kLenBits) - 1;  // the staged part's value and column chunk counts
+static_assert(kMaxBlockRows <= kLenMask, "a segment length must fit the descriptor");
 constexpr int kMapWords = 128;  // per-warp column map: 4096 column offsets
 constexpr int kMapBits = 32 * kMapWords;
 constexpr int kRing = 4;        // staging slots per warp: kRing - 1 pivots in flight
@@ -185,7 +204,7 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const int4 pi = W.piv[q];
-    if (pi.w == 0) return 1;
+    if ((pi.w & kLenMask) == 0) return 1;
     if (MODE != M_UPDATE && !((seen >> q) & 1u)) {
         int dn = 1;
         if (lane < nq && !((seen >> lane) & 1u)) dn = done[W.piv[lane].x - rbase];
@@ -198,9 +217,8 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf
         if (!((seen >> q) & 1u)) return 0;
     }
     Slot<T>& S = W.ring[q % kRing];
-    const int n = min(pi.w, kSegStage);
-    const int vb = pi.z & ~(EPC - 1), nv = (((pi.z + n + EPC - 1) & ~(EPC - 1)) - vb) / EPC;
-    const int cb = pi.z & ~3, nc = (((pi.z + n + 3) & ~3) - cb) >> 2;
+    const int vb = pi.z & ~(EPC - 1), nv = (pi.w >> kLenBits) & 63;
+    const int cb = pi.z & ~3, nc = (pi.w >> (kLenBits + 6)) & 63;
     const int total = nv + nc + (start_at_r ? 0 : 1);
     for (int t = lane; t < total; t += 32) {
         const bool isv = t < nv, isc = !isv && t < nv + nc;
@@ -238,12 +256,12 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
     constexpr int EPC = 16 / sizeof(T);
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    // Trsm: FP32 multiplies by the rounded reciprocal of the FP64 pivot; FP64 divides
-    // by the pivot itself (the operation of the definition)
+    // Trsm: exact mode divides by the pivot itself (the operation of the definition);
+    // otherwise the row is multiplied by the pivot's reciprocal, kept by its Chol
     T scale = T(1);
     if (MODE == M_TRSM) {
-        if (MIXED) scale = T(1.0 / __ldcg(P.udiag + r));
-        else scale = ld_cg(U + __ldg(P.urp + r));
+        if (EXACT) scale = ld_cg(U + __ldg(P.urp + r));
+        else scale = T(__ldcg(P.urcp + r));
     }
     int m = 0;
     for (int c0 = tb; c0 < te; c0 += m) {
@@ -289,7 +307,11 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                     sb = s.x;
                     len = s.y - s.x;
                 }
-                W.piv[lane] = make_int4(pe.x, pe.y, sb, len);
+                // copy counts of the staged part: 16-byte chunks of values and of columns
+                const int n = min(len, kSegStage);
+                const int nv = (((sb + n + EPC - 1) & ~(EPC - 1)) - (sb & ~(EPC - 1))) / EPC;
+                const int nc = (((sb + n + 3) & ~3) - (sb & ~3)) >> 2;
+                W.piv[lane] = make_int4(pe.x, pe.y, sb, len | (nv << kLenBits) | (nc << (kLenBits + 6)));
                 // Chol/Trsm: the completion flags of the whole batch, one per lane
                 if (MODE != M_UPDATE && len > 0) dn = done[pe.x - rbase];
             }
@@ -315,12 +337,13 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                 cp_async_wait<kRing - 1>();
                 __syncwarp();
                 const int4 pi = W.piv[q];
-                if (pi.w > 0) {
+                const int len = pi.w & kLenMask;
+                if (len > 0) {
                     int first_direct = 0;
                     T a;
                     if ((issued >> q) & 1u) {
                         const Slot<T>& S = W.ring[q % kRing];
-                        const int n = min(pi.w, kSegStage);
+                        const int n = min(len, kSegStage);
                         const int vo = pi.z - (pi.z & ~(EPC - 1)), co = pi.z - (pi.z & ~3);
                         a = start_at_r ? S.vals[vo] : S.aval[pi.y & (EPC - 1)];
                         apply_staged<EXACT>(W, S.cols + co, S.vals + vo, n, c_0, span, a);
@@ -337,7 +360,7 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                         seen |= 1u << q;
                         a = ld_cg(U + pi.y);
                     }
-                    for (int o = first_direct + lane; o < pi.w; o += 32)
+                    for (int o = first_direct + lane; o < len; o += 32)
                         apply_one<EXACT>(W, __ldg(P.ucol + pi.z + o), c_0, span, a, ld_cg(U + pi.z + o));
                     if (dchunk && lane == 0) W.dacc = fma(-double(a), double(a), W.dacc);
                 }
@@ -351,26 +374,32 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                 if (lane == 0) {
                     const double d = MIXED ? W.dacc : double(W.tval[0]);
                     if (!(d > 0.0) || !isfinite(d)) note_breakdown(P, r);
-                    const double piv = sqrt(d);
-                    if (MIXED) __stcg(P.udiag + r, piv);
-                    W.tval[0] = T(piv);
-                    W.dacc = MIXED ? 1.0 / piv : piv;
+                    if (EXACT) {
+                        // IEEE square root, then the row divided by the pivot
+                        const double piv = sqrt(d);
+                        W.tval[0] = T(piv);
+                        W.dacc = piv;
+                    } else {
+                        // the reciprocal pivot first; the row is multiplied by it
+                        const double y = rsqrt_newton(d);
+                        const double piv = d * y;
+                        if (MIXED) __stcg(P.udiag + r, piv);
+                        __stcg(P.urcp + r, y);
+                        W.tval[0] = T(piv);
+                        W.dacc = y;
+                    }
                 }
                 __syncwarp();
-                if (MIXED) {
-                    scale = T(W.dacc);
-                    for (int x = 1 + lane; x < m; x += 32) W.tval[x] = W.tval[x] * scale;
-                } else {
-                    scale = T(W.dacc);  // the pivot itself: FP64 divides as in the definition
-                    for (int x = 1 + lane; x < m; x += 32) W.tval[x] = W.tval[x] / scale;
-                }
+                scale = T(W.dacc);
+                if (EXACT) for (int x = 1 + lane; x < m; x += 32) W.tval[x] = W.tval[x] / scale;
+                else for (int x = 1 + lane; x < m; x += 32) W.tval[x] = W.tval[x] * scale;
             } else {
-                if (MIXED) for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] * scale;
-                else for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / scale;
+                if (EXACT) for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / scale;
+                else for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] * scale;
             }
         } else if (MODE == M_TRSM) {
-            if (MIXED) for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] * scale;
-            else for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / scale;
+            if (EXACT) for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] / scale;
+            else for (int x = lane; x < m; x += 32) W.tval[x] = W.tval[x] * scale;
         } else if (dchunk && lane == 0) {
             __stcg(P.udiag + r, W.dacc);  // Herk: the updated FP64 diagonal
         }
