@@ -1,26 +1,32 @@
 // Numeric phase of IC(k) by blocks (Section 3.3) on sm_103a.
 //
 // One persistent kernel drains a device ready queue of work items.  A work item is a
-// block task of the Cholesky-by-blocks DAG (Chol, Trsm, Herk, Gemm) or, for Herk and
-// Gemm, a chunk of its target rows.  A task's in-degree counter is decremented by
-// each finishing predecessor; the predecessor that brings it to zero pushes the
-// task's items onto the queue (the scheduler duties of Section 2.2: track ready and
-// waiting tasks, run ready ones, release dependents on completion).
+// block task of the Cholesky-by-blocks DAG (Chol, Trsm, Herk, Gemm), a chunk of a
+// Herk/Gemm task's target rows, or one of the CTAs that share a split Chol/Trsm task.
+// A task's in-degree counter is decremented by each finishing predecessor; the
+// predecessor that brings it to zero pushes the task's items onto the queue (the
+// scheduler duties of Section 2.2: track ready and waiting tasks, run ready ones,
+// release dependents on completion).
 //
 // Inside a task every target row r is owned by one warp (data parallelism within a
 // task, the remedy Section 6 plans for task granularity).  The warp stages the
-// target segment of row r in shared memory and applies, pivot by pivot in ascending
-// order, U_rc -= U_pr * U_pc for the columns c of the pivot row's source segment
-// that belong to the target segment; other contributions fall outside the IC(k)
-// pattern S and are discarded.  Chol and Trsm rows depend on earlier rows of the
-// same diagonal block; those waits use per-row completion flags in shared memory.
-// Every wait is bounded by a %globaltimer deadline and ends in a status bit.
+// target segment of row r in shared memory, with a bit map of its columns, and
+// applies, pivot by pivot in ascending order, U_rc -= U_pr * U_pc for the columns c
+// of the pivot row's source segment that belong to the target segment; other
+// contributions fall outside the IC(k) pattern S and are discarded.  Chol and Trsm
+// rows depend on earlier rows of the same diagonal block: a task on one CTA keeps
+// their completion flags in shared memory; a split task (several CTAs claiming its
+// rows from a global counter) keeps them in global memory.  Every wait is bounded by
+// a %globaltimer deadline and ends in a status bit.
 //
 // Precision: T = double is the FP64 factorization.  T = float keeps the off-diagonal
 // factor values in FP32 while every diagonal pivot is accumulated, square-rooted and
 // tested for breakdown in FP64 (array udiag): in Chol and Herk each pivot row's source
 // segment starts at column r, so its contribution to U_rr is exactly U_pr^2, which the
-// owning warp subtracts in FP64.
+// owning warp subtracts in FP64.  EXACT (FP64 only) rounds every multiply and
+// subtract separately and finishes a row with the IEEE square root and divisions;
+// otherwise updates are fused multiply-adds and a row is scaled by its reciprocal
+// pivot.
 #include <climits>
 #include <cstdint>
 #include <type_traits>
