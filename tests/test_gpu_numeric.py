@@ -96,6 +96,11 @@ def test_tasks_split_over_ctas(ick, orc, warps):
         h, o, lv = check_parity(ick, orc, prob, perm, ranges, 2, exact=exact, block_rows=1024,
                                 warps_per_cta=warps)
         assert ick.ic_stats(h)["nsplit"] > 0
+        # whichever CTA takes a row, every entry sees the same operations: same bits
+        v = dev(prob.vals)
+        for _ in range(2):
+            ick.ic_numeric(h, v)
+            assert np.array_equal(ick.ic_get_factor(h)[2], lv)
 
 
 def test_rows_wider_than_the_column_map(ick, orc):
