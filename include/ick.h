@@ -104,8 +104,8 @@ typedef struct {
     int64_t warps_per_cta;/* warps per CTA of the persistent kernel (defaults resolved) */
     int64_t rows_per_item;/* target rows per Herk/Gemm work item (defaults resolved)    */
     int64_t nsplit;       /* Chol/Trsm tasks spread over several CTAs (expected to run
-                             with little else in flight; their row flags in global
-                             memory)                                                  */
+                             with little else in flight; their finished rows published
+                             in a shadow array read with no completion flags)          */
 } ic_stats_t;
 
 typedef struct ic_handle ic_handle;

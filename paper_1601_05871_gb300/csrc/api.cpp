@@ -183,8 +183,17 @@ int upload_plan(ic_handle* h) {
     if ((st = h->upload(&D.indeg0, P.indeg0))) return st;
     if ((st = h->upload(&D.seeds, P.seeds))) return st;
     if ((st = h->upload(&D.flag_off, P.flag_off))) return st;
-    D.nflags = int(P.nflags);
-    if ((st = h->alloc(&D.gflag, size_t(P.nflags > 0 ? P.nflags : 1)))) return st;
+    if ((st = h->upload(&D.soff, P.soff))) return st;
+    D.nshadow = P.nshadow;
+    if (h->opts.dtype == IC_F32) {
+        float* sh = nullptr;
+        if ((st = h->alloc(&sh, size_t(P.nshadow)))) return st;
+        D.shadow = sh;
+    } else {
+        double* sh = nullptr;
+        if ((st = h->alloc(&sh, size_t(P.nshadow)))) return st;
+        D.shadow = sh;
+    }
     if ((st = h->alloc(&D.row_next, P.task.size()))) return st;
     // factor values (FP64, or FP32 plus FP64 pivots), padded by 16 bytes
     const bool f32 = h->opts.dtype == IC_F32;

@@ -317,17 +317,21 @@ void order_updates(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
 // flags in shared memory, and at the end of the factorization (the top separators) it
 // is the only work on the GPU, bound by one SM's issue rate.  Split into kSplitItems
 // items, the task's rows are claimed from a counter in global memory by every CTA that
-// holds one of its items, and row completion flags live in global memory.  The
-// estimate: an ASAP schedule of the final graph under task_costs; a Chol/Trsm task of
-// at least kSplitMinRows target rows whose start finds fewer than kSplitIdle other
-// work items in flight is split.
-void split_tail_tasks(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
+// holds one of its items, and each finished row is published in a shadow array whose
+// entries hold a sentinel until written, so a reader knows every value it uses is
+// final without a flag.  The estimate: an ASAP schedule of the final graph under
+// task_costs; a Chol/Trsm task of at least kSplitMinRows target rows whose start finds
+// fewer than kSplitIdle other work items in flight is split.
+void split_tail_tasks(HostPlan& P, const std::vector<std::vector<int4>>& ttgt,
+                      const std::vector<std::vector<int32_t>>& tend) {
     constexpr int kSplitItems = 8, kSplitMinRows = 512;
-    constexpr int64_t kSplitIdle = 64;
+    constexpr int64_t kSplitIdle = 64, kShadowPad = 4;
     const int64_t nt = int64_t(P.task.size());
     P.flag_off.assign(nt, -1);
+    P.soff.clear();
     P.nflags = 0;
     P.nsplit = 0;
+    P.nshadow = kShadowPad;  // 16-byte copies may reach up to 3 values past either end
     if (nt == 0) return;
     const std::vector<double> cost = task_costs(P, ttgt);
     // ASAP over a topological order of the graph
@@ -369,12 +373,20 @@ void split_tail_tasks(HostPlan& P, const std::vector<std::vector<int4>>& ttgt) {
         while (e < ev.size() && ev[e].first <= st.first) live += ev[e++].second;
         const int32_t t = st.second;
         if (live - P.nitems[t] >= kSplitIdle) continue;
-        const int32_t blk = P.task[t].y;
+        const int32_t blk = P.task[t].y, rbase = P.ranges[blk];
         P.flag_off[t] = int32_t(P.nflags);
-        P.nflags += P.ranges[blk + 1] - P.ranges[blk];
+        P.nflags += P.ranges[blk + 1] - rbase;
+        P.soff.resize(size_t(P.nflags), 0);
+        for (size_t i = 0; i < ttgt[t].size(); ++i) {
+            const int64_t r = ttgt[t][i].x, tb = ttgt[t][i].w, te = tend[t][i];
+            const int64_t pos = P.nshadow + (((tb - P.nshadow) % 4) + 4) % 4;
+            P.soff[size_t(P.flag_off[t] + (r - rbase))] = int32_t(pos - tb);
+            P.nshadow = pos + (te - tb);
+        }
         P.nitems[t] = kSplitItems;
         ++P.nsplit;
     }
+    P.nshadow += kShadowPad;
 }
 
 }  // namespace
@@ -693,8 +705,8 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
         P.indeg0[t] = int32_t(P.pred_ptr[t + 1] - P.pred_ptr[t]);
         ++P.ntype[T.x];
     }
-    split_tail_tasks(P, ttgt);
-    if (P.nflags > INT32_MAX / 2) { err = "too many split rows"; return IC_ERR_ARG; }
+    split_tail_tasks(P, ttgt, tend);
+    if (P.nflags > INT32_MAX / 2 || P.nshadow > INT32_MAX / 2) { err = "too many split rows"; return IC_ERR_ARG; }
     for (int64_t t = 0; t < nt; ++t) P.total_items += P.nitems[t];
     if (P.total_items > INT32_MAX / 2) { err = "too many work items"; return IC_ERR_ARG; }
     P.succ_ptr.assign(nt + 1, 0);

@@ -66,10 +66,12 @@ struct HostPlan {
     std::vector<int32_t> pred;
     std::vector<int32_t> succ_ptr, succ;
     std::vector<int32_t> indeg0, nitems;
-    // Chol/Trsm tasks spread over several CTAs (nitems > 1): offset of their rows'
-    // completion flags in global memory, -1 for the others (flags in shared memory)
-    std::vector<int32_t> flag_off;
-    int64_t nflags = 0, nsplit = 0;
+    // Chol/Trsm tasks spread over several CTAs (nitems > 1): offset of their block's
+    // rows in soff, -1 for the others (completion flags in shared memory).  A split
+    // task's finished rows are published in a shadow array: row r's target segment
+    // [tb, te) sits at shadow positions tb + soff[...], congruent to tb modulo 4
+    std::vector<int32_t> flag_off, soff;
+    int64_t nflags = 0, nsplit = 0, nshadow = 0;
     std::vector<int32_t> tgt_ptr;   // ntasks + 1
     std::vector<int4> tgt;          // (r, csc_a, csc_b, seg_begin)
     std::vector<int32_t> tgt_end;   // seg_end
@@ -116,8 +118,9 @@ struct DevPlan {
     const int* succ;
     const int* indeg0;
     const int2* seeds;
-    const int* flag_off;   // per task: rows' flags in gflag (split Chol/Trsm) or -1
-    int nflags;
+    const int* flag_off;   // per task: its block's rows in soff (split Chol/Trsm) or -1
+    const int* soff;       // per row of a split task's block: shadow position - U position
+    long long nshadow;
     // mutable state
     void* uval;            // factor values (double for IC_F64)
     int* indeg;
@@ -133,7 +136,7 @@ struct DevPlan {
     double* urcp;          // FMA mode: 1/U_ii of every row, kept by its Chol for Trsm
     const int* diag_src;   // IC_F32: index of A's diagonal value of each row
     int* epoch_dev;        // queue epoch, advanced on the device before each numeric phase
-    unsigned char* gflag;  // completion flags of the rows of split Chol/Trsm tasks
+    void* shadow;          // finished rows of split Chol/Trsm tasks, else the sentinel
     int* row_next;         // per task: next target to claim (split Chol/Trsm)
 };
 

@@ -16,8 +16,9 @@
 // contributions fall outside the IC(k) pattern S and are discarded.  Chol and Trsm
 // rows depend on earlier rows of the same diagonal block: a task on one CTA keeps
 // their completion flags in shared memory; a split task (several CTAs claiming its
-// rows from a global counter) keeps them in global memory.  Every wait is bounded by
-// a %globaltimer deadline and ends in a status bit.
+// rows from a global counter) publishes each finished row in a shadow array that
+// holds a sentinel until written, and readers take a value once it is not the
+// sentinel.  Every wait is bounded by a %globaltimer deadline and ends in a status bit.
 //
 // Precision: T = double is the FP64 factorization.  T = float keeps the off-diagonal
 // factor values in FP32 while every diagonal pivot is accumulated, square-rooted and
@@ -160,6 +161,7 @@ template <typename T>
 struct WarpBuf {
     Slot<T> ring[kRing];
     int4 piv[32];          // pivot row, position of U_pr, source segment start, length
+    int psoff[32];         // split tasks: the pivot row's shadow offset
     double dacc;           // FP64 diagonal accumulator (T = float)
     double pad;
     uint2 cmap[kMapWords]; // (bits, rank) per 32 column offsets
@@ -196,6 +198,66 @@ __device__ __forceinline__ void apply_staged(WarpBuf<T>& W, const int* cols, con
     if (i1 >= 0) W.tval[i1] = sub_product<EXACT>(t1, a, v1);
 }
 
+// Split tasks publish finished rows in a shadow array that holds a signalling NaN
+// with a fixed payload until each value is written.  Arithmetic never produces that
+// bit pattern (a NaN result is the quiet canonical one), and an aligned 8- or 4-byte
+// store is seen whole or not at all, so a value read that is not the sentinel is final.
+constexpr unsigned long long kSentinel64 = 0x7FF00000DEADBEEFull;
+constexpr unsigned kSentinel32 = 0x7F80BEEFu;
+__device__ __forceinline__ bool is_sentinel(double v) {
+    return (unsigned long long)__double_as_longlong(v) == kSentinel64;
+}
+__device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == kSentinel32; }
+__device__ __forceinline__ double ld_vol(const double* p) { return *reinterpret_cast<const volatile double*>(p); }
+__device__ __forceinline__ float ld_vol(const float* p) { return *reinterpret_cast<const volatile float*>(p); }
+
+// The n <= 64 staged values vals[0, n) of a split task's pivot segment, copied from
+// src: any still holding the sentinel are read again (bounded) until published.
+// False on timeout or abort.
+template <typename T>
+__device__ bool await_published(const DevPlan& P, T* vals, int n, const T* src,
+                                unsigned long long deadline) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    bool v0 = lane >= n || !is_sentinel(vals[lane]);
+    bool v1 = lane + 32 >= n || !is_sentinel(vals[lane + 32]);
+    unsigned spins = 0;
+    while (!__all_sync(full, v0 && v1)) {
+        if (!v0) {
+            const T t = ld_vol(src + lane);
+            if (!is_sentinel(t)) { vals[lane] = t; v0 = true; }
+        }
+        if (!v1) {
+            const T t = ld_vol(src + lane + 32);
+            if (!is_sentinel(t)) { vals[lane + 32] = t; v1 = true; }
+        }
+        int stop = 0;
+        if (lane == 0 && (++spins & 63) == 0) {
+            if (ld_volatile(P.counters + 3)) stop = 1;
+            else if (gtimer() > deadline) { set_timeout(P, 3); stop = 1; }
+        }
+        if (__shfl_sync(full, stop, 0)) return false;
+        __nanosleep(20);
+    }
+    __syncwarp();
+    return true;
+}
+
+// One published value of a split task's pivot row (per lane, bounded).
+template <typename T>
+__device__ T await_value(const DevPlan& P, const T* src, unsigned long long deadline) {
+    unsigned spins = 0;
+    for (;;) {
+        const T t = ld_vol(src);
+        if (!is_sentinel(t)) return t;
+        if ((++spins & 63) == 0 && (ld_volatile(P.counters + 3) || gtimer() > deadline)) {
+            if (!ld_volatile(P.counters + 3)) set_timeout(P, 4);
+            return t;
+        }
+        __nanosleep(20);
+    }
+}
+
 // Issue the copies of pivot q's source segment into ring slot q % kRing.  Returns 1
 // when the slot will hold the data (or the segment is empty), 0 when the pivot row is
 // not complete yet (Chol/Trsm): then the consumer waits and loads it directly.  Bit q
@@ -203,32 +265,31 @@ __device__ __forceinline__ void apply_staged(WarpBuf<T>& W, const int* cols, con
 // all the batch's pivots not seen yet are read again, one per lane, so that rows
 // completed meanwhile cost one round trip together, not one each.
 template <int MODE, bool GF, typename T>
-__device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, WarpBuf<T>& W, int q, int nq,
-                                           bool start_at_r, int rbase, volatile unsigned char* done,
-                                           unsigned& seen) {
+__device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, const T* shadow, WarpBuf<T>& W,
+                                           int q, int nq, bool start_at_r, int rbase,
+                                           volatile unsigned char* done, unsigned& seen) {
     constexpr int EPC = 16 / sizeof(T);  // elements per 16-byte chunk
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const int4 pi = W.piv[q];
     if ((pi.w & kLenMask) == 0) return 1;
-    if (MODE != M_UPDATE && !((seen >> q) & 1u)) {
+    if (!GF && MODE != M_UPDATE && !((seen >> q) & 1u)) {
         int dn = 1;
         if (lane < nq && !((seen >> lane) & 1u)) dn = done[W.piv[lane].x - rbase];
         const unsigned now = __ballot_sync(full, dn != 0);
-        if (now & ~seen) {
-            if (GF) __threadfence();
-            else __threadfence_block();
-        }
+        if (now & ~seen) __threadfence_block();
         seen |= now;
         if (!((seen >> q) & 1u)) return 0;
     }
+    // split task: the values from the pivot row's published copy (checked on use)
+    const T* V = GF ? shadow + W.psoff[q] : U;
     Slot<T>& S = W.ring[q % kRing];
     const int vb = pi.z & ~(EPC - 1), nv = (pi.w >> kLenBits) & 63;
     const int cb = pi.z & ~3, nc = (pi.w >> (kLenBits + 6)) & 63;
     const int total = nv + nc + (start_at_r ? 0 : 1);
     for (int t = lane; t < total; t += 32) {
         const bool isv = t < nv, isc = !isv && t < nv + nc;
-        const void* src = isv ? static_cast<const void*>(U + vb + EPC * t)
+        const void* src = isv ? static_cast<const void*>(V + vb + EPC * t)
                         : isc ? static_cast<const void*>(P.ucol + cb + 4 * (t - nv))
                               : static_cast<const void*>(U + (pi.y & ~(EPC - 1)));
         void* dst = isv ? static_cast<void*>(&S.vals[EPC * t])
@@ -257,7 +318,8 @@ template <int MODE, bool EXACT, bool GF, typename T>
 __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, int tb, int te,
                                int srcblk, bool start_at_r, int rbase,
                                volatile unsigned char* done, WarpBuf<T>& W,
-                               unsigned long long deadline) {
+                               unsigned long long deadline, const int* soffs = nullptr,
+                               T* shadow = nullptr) {
     constexpr bool MIXED = std::is_same<T, float>::value;
     constexpr int EPC = 16 / sizeof(T);
     const int lane = threadIdx.x & 31;
@@ -318,27 +380,26 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                 const int nv = (((sb + n + EPC - 1) & ~(EPC - 1)) - (sb & ~(EPC - 1))) / EPC;
                 const int nc = (((sb + n + 3) & ~3) - (sb & ~3)) >> 2;
                 W.piv[lane] = make_int4(pe.x, pe.y, sb, len | (nv << kLenBits) | (nc << (kLenBits + 6)));
-                // Chol/Trsm: the completion flags of the whole batch, one per lane
-                if (MODE != M_UPDATE && len > 0) dn = done[pe.x - rbase];
+                if (GF) W.psoff[lane] = len > 0 ? __ldg(soffs + pe.x - rbase) : 0;
+                // one CTA's Chol/Trsm: the completion flags of the whole batch, one per lane
+                else if (MODE != M_UPDATE && len > 0) dn = done[pe.x - rbase];
             }
             unsigned seen = __ballot_sync(full, dn != 0);
-            if (MODE != M_UPDATE) {
-                if (GF) __threadfence();
-                else __threadfence_block();
-            }
+            if (!GF && MODE != M_UPDATE) __threadfence_block();
             __syncwarp();
             unsigned issued = 0;
 #pragma unroll
             for (int s = 0; s < kRing - 1; ++s) {
                 if (s < nq)
-                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, W, s, nq, start_at_r, rbase, done, seen)) << s;
+                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, shadow, W, s, nq, start_at_r, rbase, done,
+                                                             seen)) << s;
                 cp_async_commit();
             }
             for (int q = 0; q < nq; ++q) {
                 const int nxt = q + kRing - 1;
                 if (nxt < nq)
-                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, W, nxt, nq, start_at_r, rbase, done, seen))
-                              << nxt;
+                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, shadow, W, nxt, nq, start_at_r, rbase,
+                                                             done, seen)) << nxt;
                 cp_async_commit();
                 cp_async_wait<kRing - 1>();
                 __syncwarp();
@@ -348,9 +409,13 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                     int first_direct = 0;
                     T a;
                     if ((issued >> q) & 1u) {
-                        const Slot<T>& S = W.ring[q % kRing];
+                        Slot<T>& S = W.ring[q % kRing];
                         const int n = min(len, kSegStage);
                         const int vo = pi.z - (pi.z & ~(EPC - 1)), co = pi.z - (pi.z & ~3);
+                        if (GF && !await_published(P, S.vals + vo, n, shadow + W.psoff[q] + pi.z, deadline)) {
+                            cp_async_wait<0>();
+                            return;
+                        }
                         a = start_at_r ? S.vals[vo] : S.aval[pi.y & (EPC - 1)];
                         apply_staged<EXACT>(W, S.cols + co, S.vals + vo, n, c_0, span, a);
                         first_direct = n;
@@ -366,8 +431,11 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                         seen |= 1u << q;
                         a = ld_cg(U + pi.y);
                     }
-                    for (int o = first_direct + lane; o < len; o += 32)
-                        apply_one<EXACT>(W, __ldg(P.ucol + pi.z + o), c_0, span, a, ld_cg(U + pi.z + o));
+                    for (int o = first_direct + lane; o < len; o += 32) {
+                        const T v = GF ? await_value(P, shadow + W.psoff[q] + pi.z + o, deadline)
+                                       : ld_cg(U + pi.z + o);
+                        apply_one<EXACT>(W, __ldg(P.ucol + pi.z + o), c_0, span, a, v);
+                    }
                     if (dchunk && lane == 0) W.dacc = fma(-double(a), double(a), W.dacc);
                 }
                 __syncwarp();
@@ -411,6 +479,11 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
         }
         __syncwarp();
         for (int x = lane; x < m; x += 32) __stcg(U + c0 + x, W.tval[x]);
+        if (GF) {
+            // publish the finished chunk for the split task's other rows
+            T* pub = shadow + __ldg(soffs + r - rbase);
+            for (int x = lane; x < m; x += 32) __stcg(pub + c0 + x, W.tval[x]);
+        }
         __syncwarp();
     }
 }
@@ -480,7 +553,8 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
             // task's counter; completion flags in global memory
             const int blk = Tk.y;
             const int rbase = __ldg(P.ranges + blk);
-            volatile unsigned char* gdone = P.gflag + __ldg(P.flag_off + task);
+            const int* soffs = P.soff + __ldg(P.flag_off + task);
+            T* shadow = static_cast<T*>(P.shadow);
             for (;;) {
                 int idx = 0;
                 if (lane == 0) idx = atomicAdd(P.row_next + task, 1);
@@ -490,14 +564,10 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
                 const int gend = __ldg(P.tgt_end + t0 + idx);
                 if (Tk.x == T_CHOL)
                     process_target<M_CHOL, EXACT, true, T>(P, U, g.x, g.y, g.z, g.w, gend, blk, true, rbase,
-                                                           gdone, W, deadline);
+                                                           nullptr, W, deadline, soffs, shadow);
                 else
                     process_target<M_TRSM, EXACT, true, T>(P, U, g.x, g.y, g.z, g.w, gend, Tk.w, false,
-                                                           rbase, gdone, W, deadline);
-                // every lane's stores of the row, then the flag
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) gdone[g.x - rbase] = 1;
+                                                           rbase, nullptr, W, deadline, soffs, shadow);
             }
         } else if (Tk.x == T_CHOL || Tk.x == T_TRSM) {
             const int blk = Tk.y;
@@ -607,7 +677,13 @@ __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double
         P.items_left[t] = __ldg(P.nitems + t);
         P.row_next[t] = 0;
     }
-    for (int i = tid; i < P.nflags; i += stride) P.gflag[i] = 0;
+    if (MIXED) {
+        unsigned* sh = static_cast<unsigned*>(P.shadow);
+        for (long long i = tid; i < P.nshadow; i += stride) sh[i] = kSentinel32;
+    } else {
+        unsigned long long* sh = static_cast<unsigned long long*>(P.shadow);
+        for (long long i = tid; i < P.nshadow; i += stride) sh[i] = kSentinel64;
+    }
     for (int s = tid; s < P.nseeds; s += stride) {
         P.queue[s] = __ldg(P.seeds + s);
         P.qstamp[s] = epoch;
