@@ -118,10 +118,8 @@ __device__ __forceinline__ void note_breakdown(const DevPlan& P, int r) {
     atomicMin(P.brk_row, (long long)r);
 }
 
-// Wait until done[local] is set by another warp (of this CTA, flags in shared memory;
-// GF: of any CTA, flags in global memory); false on timeout/abort.  The caller fences
-// before it reads the row.
-template <bool GF>
+// Wait until done[local] is set by another warp of this CTA (flags in shared memory);
+// false on timeout/abort.  The caller fences before it reads the row.
 __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int local,
                          unsigned long long deadline) {
     unsigned spins = 0;
@@ -208,8 +206,12 @@ __device__ __forceinline__ bool is_sentinel(double v) {
     return (unsigned long long)__double_as_longlong(v) == kSentinel64;
 }
 __device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == kSentinel32; }
-__device__ __forceinline__ double ld_vol(const double* p) { return *reinterpret_cast<const volatile double*>(p); }
-__device__ __forceinline__ float ld_vol(const float* p) { return *reinterpret_cast<const volatile float*>(p); }
+__device__ __forceinline__ double ld_vol(const double* p) {
+    return *reinterpret_cast<const volatile double*>(p);
+}
+__device__ __forceinline__ float ld_vol(const float* p) {
+    return *reinterpret_cast<const volatile float*>(p);
+}
 
 // The n <= 64 staged values vals[0, n) of a split task's pivot segment, copied from
 // src: any still holding the sentinel are read again (bounded) until published.
@@ -263,8 +265,9 @@ __device__ T await_value(const DevPlan& P, const T* src, unsigned long long dead
 // not complete yet (Chol/Trsm): then the consumer waits and loads it directly.  Bit q
 // of seen: pivot q's row was seen complete.  When pivot q has not been, the flags of
 // all the batch's pivots not seen yet are read again, one per lane, so that rows
-// completed meanwhile cost one round trip together, not one each.
-template <int MODE, bool GF, typename T>
+// completed meanwhile cost one round trip together, not one each.  SPLIT: no flags;
+// the values come from the published copy and are checked by the consumer.
+template <int MODE, bool SPLIT, typename T>
 __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, const T* shadow, WarpBuf<T>& W,
                                            int q, int nq, bool start_at_r, int rbase,
                                            volatile unsigned char* done, unsigned& seen) {
@@ -273,7 +276,7 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, const T
     const unsigned full = 0xffffffffu;
     const int4 pi = W.piv[q];
     if ((pi.w & kLenMask) == 0) return 1;
-    if (!GF && MODE != M_UPDATE && !((seen >> q) & 1u)) {
+    if (!SPLIT && MODE != M_UPDATE && !((seen >> q) & 1u)) {
         int dn = 1;
         if (lane < nq && !((seen >> lane) & 1u)) dn = done[W.piv[lane].x - rbase];
         const unsigned now = __ballot_sync(full, dn != 0);
@@ -282,7 +285,7 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, const T
         if (!((seen >> q) & 1u)) return 0;
     }
     // split task: the values from the pivot row's published copy (checked on use)
-    const T* V = GF ? shadow + W.psoff[q] : U;
+    const T* V = SPLIT ? shadow + W.psoff[q] : U;
     Slot<T>& S = W.ring[q % kRing];
     const int vb = pi.z & ~(EPC - 1), nv = (pi.w >> kLenBits) & 63;
     const int cb = pi.z & ~3, nc = (pi.w >> (kLenBits + 6)) & 63;
@@ -311,10 +314,14 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, const T
 // the chunk's bit map and word ranks with no probing.  Pivots are applied one at a
 // time in ascending order, lane l taking source elements l, l+32, ...  The source
 // segments of the next kRing-1 pivots are copied asynchronously into a ring of
-// shared-memory slots while the current one is applied.  For Chol and Trsm a copy is
-// issued only once the pivot row's completion flag is seen; a pivot that was not
-// complete at issue time is waited for and loaded directly when its turn comes.
-template <int MODE, bool EXACT, bool GF, typename T>
+// shared-memory slots while the current one is applied.  For Chol and Trsm on one CTA
+// a copy is issued only once the pivot row's completion flag is seen; a pivot that was
+// not complete at issue time is waited for and loaded directly when its turn comes.
+// SPLIT (a Chol/Trsm task shared by several CTAs): there are no flags; the copies come
+// from the pivot rows' published copies (shadow, offsets soffs per row of the block),
+// every value is checked against the sentinel on use, and the finished row is
+// published in turn.
+template <int MODE, bool EXACT, bool SPLIT, typename T>
 __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, int tb, int te,
                                int srcblk, bool start_at_r, int rbase,
                                volatile unsigned char* done, WarpBuf<T>& W,
@@ -380,26 +387,26 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                 const int nv = (((sb + n + EPC - 1) & ~(EPC - 1)) - (sb & ~(EPC - 1))) / EPC;
                 const int nc = (((sb + n + 3) & ~3) - (sb & ~3)) >> 2;
                 W.piv[lane] = make_int4(pe.x, pe.y, sb, len | (nv << kLenBits) | (nc << (kLenBits + 6)));
-                if (GF) W.psoff[lane] = len > 0 ? __ldg(soffs + pe.x - rbase) : 0;
+                if (SPLIT) W.psoff[lane] = len > 0 ? __ldg(soffs + pe.x - rbase) : 0;
                 // one CTA's Chol/Trsm: the completion flags of the whole batch, one per lane
                 else if (MODE != M_UPDATE && len > 0) dn = done[pe.x - rbase];
             }
             unsigned seen = __ballot_sync(full, dn != 0);
-            if (!GF && MODE != M_UPDATE) __threadfence_block();
+            if (!SPLIT && MODE != M_UPDATE) __threadfence_block();
             __syncwarp();
             unsigned issued = 0;
 #pragma unroll
             for (int s = 0; s < kRing - 1; ++s) {
                 if (s < nq)
-                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, shadow, W, s, nq, start_at_r, rbase, done,
-                                                             seen)) << s;
+                    issued |= unsigned(issue_pivot<MODE, SPLIT>(P, U, shadow, W, s, nq, start_at_r, rbase,
+                                                                done, seen)) << s;
                 cp_async_commit();
             }
             for (int q = 0; q < nq; ++q) {
                 const int nxt = q + kRing - 1;
                 if (nxt < nq)
-                    issued |= unsigned(issue_pivot<MODE, GF>(P, U, shadow, W, nxt, nq, start_at_r, rbase,
-                                                             done, seen)) << nxt;
+                    issued |= unsigned(issue_pivot<MODE, SPLIT>(P, U, shadow, W, nxt, nq, start_at_r,
+                                                                rbase, done, seen)) << nxt;
                 cp_async_commit();
                 cp_async_wait<kRing - 1>();
                 __syncwarp();
@@ -412,7 +419,8 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                         Slot<T>& S = W.ring[q % kRing];
                         const int n = min(len, kSegStage);
                         const int vo = pi.z - (pi.z & ~(EPC - 1)), co = pi.z - (pi.z & ~3);
-                        if (GF && !await_published(P, S.vals + vo, n, shadow + W.psoff[q] + pi.z, deadline)) {
+                        if (SPLIT &&
+                            !await_published(P, S.vals + vo, n, shadow + W.psoff[q] + pi.z, deadline)) {
                             cp_async_wait<0>();
                             return;
                         }
@@ -421,18 +429,17 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                         first_direct = n;
                     } else {
                         int ok = 1;
-                        if (lane == 0) ok = wait_row<GF>(P, done, pi.x - rbase, deadline);
+                        if (lane == 0) ok = wait_row(P, done, pi.x - rbase, deadline);
                         if (!__shfl_sync(full, ok, 0)) {
                             cp_async_wait<0>();
                             return;
                         }
-                        if (GF) __threadfence();
-                        else __threadfence_block();
+                        __threadfence_block();
                         seen |= 1u << q;
                         a = ld_cg(U + pi.y);
                     }
                     for (int o = first_direct + lane; o < len; o += 32) {
-                        const T v = GF ? await_value(P, shadow + W.psoff[q] + pi.z + o, deadline)
+                        const T v = SPLIT ? await_value(P, shadow + W.psoff[q] + pi.z + o, deadline)
                                        : ld_cg(U + pi.z + o);
                         apply_one<EXACT>(W, __ldg(P.ucol + pi.z + o), c_0, span, a, v);
                     }
@@ -479,7 +486,7 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
         }
         __syncwarp();
         for (int x = lane; x < m; x += 32) __stcg(U + c0 + x, W.tval[x]);
-        if (GF) {
+        if (SPLIT) {
             // publish the finished chunk for the split task's other rows
             T* pub = shadow + __ldg(soffs + r - rbase);
             for (int x = lane; x < m; x += 32) __stcg(pub + c0 + x, W.tval[x]);
