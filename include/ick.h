@@ -272,6 +272,17 @@ int ic_get_solve_tasks(const ic_handle* h, int backward, int64_t* ntasks, int32_
  * Errors: IC_ERR_ARG. */
 int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t* j, int32_t* pos);
 
+/* Layout of the split Chol/Trsm tasks (ic_stats nsplit), for inspection.  A split
+ * task's finished rows are published in a shadow array of *nshadow values: the target
+ * segment [tb, te) of row r of such a task (ic_get_task_targets) sits at shadow
+ * positions [tb + soff[flag_off[t] + r - ranges[k]], te + ...), k the task's block
+ * row, at a position congruent to tb modulo 4.  flag_off (ntasks): the task's first
+ * entry in soff, -1 for tasks that are not split.  soff (*nsoff): one per row of each
+ * split task's block.  Call with NULL arrays to get *nsoff and *nshadow.
+ * Errors: IC_ERR_ARG. */
+int ic_get_split_layout(const ic_handle* h, int32_t* flag_off, int32_t* soff, int64_t* nsoff,
+                        int64_t* nshadow);
+
 /* Kernel timing of the handle's calls, from CUDA events recorded on the launching
  * stream while timing is on (ic_set_timing(h, 1); it adds no synchronisation beyond
  * what the calls already do).  launches counts the library's own kernel launches

@@ -1036,6 +1036,18 @@ int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t
     return IC_OK;
 }
 
+int ic_get_split_layout(const ic_handle* h, int32_t* flag_off, int32_t* soff, int64_t* nsoff,
+                        int64_t* nshadow) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    const HostPlan& P = h->hp;
+    if (nsoff) *nsoff = int64_t(P.soff.size());
+    if (nshadow) *nshadow = P.nshadow;
+    if (flag_off && !P.flag_off.empty())
+        std::memcpy(flag_off, P.flag_off.data(), P.flag_off.size() * sizeof(int32_t));
+    if (soff && !P.soff.empty()) std::memcpy(soff, P.soff.data(), P.soff.size() * sizeof(int32_t));
+    return IC_OK;
+}
+
 int ic_set_timing(ic_handle* h, int on) {
     if (!h) return fail(IC_ERR_ARG, "NULL handle");
     if (h->device < 0) return fail(IC_ERR_STATE, "host-only handle");

@@ -87,6 +87,7 @@ def load():
         "ic_get_trace": (I, [P, P]),
         "ic_get_solve_trace": (I, [P, I, P]),
         "ic_get_solve_entries": (I, [P, I, P, P, P]),
+        "ic_get_split_layout": (I, [P, P, P, P, P]),
         "ic_shift_features": (I, [P, P, D, P, P]),
         "ic_numeric_shifted": (I, [P, P, D, D, I, P, P, P]),
         "ic_mlp_n_params": (I, []),
@@ -369,6 +370,20 @@ def ic_get_solve_entries(h, backward=False):
     pos = np.empty(max(1, m), dtype=np.int32)
     _check(L.ic_get_solve_entries(h.ptr, int(bool(backward)), None, _p(j), _p(pos)))
     return {"ptr": ptr, "j": j[:m], "pos": pos[:m]}
+
+
+def ic_get_split_layout(h):
+    """Split Chol/Trsm tasks' published-row layout: dict with flag_off (ntasks), soff,
+    nshadow."""
+    L = load()
+    nt = ic_stats(h)["ntasks"]
+    ns = np.zeros(1, dtype=np.int64)
+    nsh = np.zeros(1, dtype=np.int64)
+    _check(L.ic_get_split_layout(h.ptr, None, None, _p(ns), _p(nsh)))
+    fo = np.empty(max(1, nt), dtype=np.int32)
+    so = np.empty(max(1, int(ns[0])), dtype=np.int32)
+    _check(L.ic_get_split_layout(h.ptr, _p(fo), _p(so), None, None))
+    return {"flag_off": fo[:nt], "soff": so[:int(ns[0])], "nshadow": int(nsh[0])}
 
 
 def ic_get_solve_trace(h, backward=False):

@@ -217,6 +217,39 @@ def test_split_tasks_plan():
     assert s["nitems"] == items + (sum(d["type"] < 2) - s["nsplit"]) + 8 * s["nsplit"]
 
 
+def test_split_tasks_shadow_layout():
+    """The published copy of every target segment of a split task lies inside the
+    shadow array with 4 values of margin (16-byte copies may reach 3 past either end),
+    is congruent to its U position modulo 4 (so the copies stay 16-byte aligned), and
+    no two overlap."""
+    prob = synth.laplace3d_27pt(24)
+    perm, ranges = ick.ic_nd_grid(24, 24, 24, 1, 1024)
+    for dtype in (ick.IC_F64, ick.IC_F32):
+        h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=1024, host_only=1,
+                            dtype=dtype)
+        lay = ick.ic_get_split_layout(h)
+        rng, _, _ = ick.ic_get_blocks(h)
+        d = ick.ic_get_tasks(h)
+        fo, so, nsh = lay["flag_off"], lay["soff"], lay["nshadow"]
+        split = np.nonzero(fo >= 0)[0]
+        assert len(split) == ick.ic_stats(h)["nsplit"] > 0
+        assert all(d["type"][t] in (0, 1) for t in split)
+        spans = []
+        for t in split:
+            k = int(d["k"][t])
+            for r, ca, cb, tb, te in ick.ic_get_task_targets(h, t):
+                off = int(so[fo[t] + r - rng[k]])
+                assert (tb + off) % 4 == tb % 4
+                spans.append((tb + off, te + off))
+        spans.sort()
+        assert spans[0][0] >= 4 and spans[-1][1] <= nsh - 4
+        assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
+    # no split tasks: an empty layout
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=300, host_only=1)
+    lay = ick.ic_get_split_layout(h)
+    assert (lay["flag_off"] < 0).all() == (ick.ic_stats(h)["nsplit"] == 0)
+
+
 def test_empty_matrix():
     h = ick.ic_symbolic(np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), 2, host_only=1)
     s = ick.ic_stats(h)
