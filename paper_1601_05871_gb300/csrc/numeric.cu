@@ -557,7 +557,7 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
 
         if ((Tk.x == T_CHOL || Tk.x == T_TRSM) && __ldg(P.flag_off + task) >= 0) {
             // a split task: every CTA holding one of its items claims rows from the
-            // task's counter; completion flags in global memory
+            // task's counter; finished rows are published in the shadow array
             const int blk = Tk.y;
             const int rbase = __ldg(P.ranges + blk);
             const int* soffs = P.soff + __ldg(P.flag_off + task);

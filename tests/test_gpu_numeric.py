@@ -88,7 +88,7 @@ def test_27pt_ic2(ick, orc, warps):
 @pytest.mark.parametrize("warps", [16, 32])
 def test_tasks_split_over_ctas(ick, orc, warps):
     """Chol/Trsm tasks expected to run with little else in flight are spread over
-    several CTAs, rows claimed from a global counter and their flags in global memory:
+    several CTAs, rows claimed from a global counter and published in a shadow array:
     the factor is the one CTA would give (bit-exact in exact mode)."""
     prob = synth.laplace3d_27pt(24)
     perm, ranges = ick.ic_nd_grid(24, 24, 24, 1, 1024)
