@@ -13,8 +13,14 @@ events on the launching stream).  e2e repeats the step through the C ABI from pi
 host buffers, with the host-to-device copies of A's values and b and the
 device-to-host copy of x inside the timed region.
 
+With one GPU the line also carries, outside the timed region, the other workloads of
+the method (each with a few fixed repetitions): c4_shift (Q1 elasticity, FP32 +
+learned shift vs plain FP64, time to 1e-8), c3_batch (512 diffusion cubes in one
+launch) and c5 (160^3 7-point diffusion IC(3), FP32 vs FP64 time to 1e-8).  --shift,
+--c3 and --c5 print each of them as a line of its own instead.
+
 --impl reference times the CPU oracle (the single-threaded FP64 reference the
-parity tests use) on a bounded sample of the same workload.
+parity tests use): one numeric factorization of the same workload per step.
 """
 from __future__ import annotations
 
@@ -33,12 +39,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "IC(k) factor GFLOP/s & HBM GB/s; PCG time-to-1e-8 vs plain FP64 on GB300"
-FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (see the alu roofline in the design notes)
-# DRAM bytes (read + write) per launch of a solve kernel, keyed by (side, k, kernel):
-# ncu captures at 48^3 and 64^3 give 14.95 / 14.83 (forward) and 15.51 / 15.18
-# (backward) bytes per factor entry; the 64^3 figures are scaled here to the 96^3
-# factor (57,510,348 entries); profiles/ holds the captures' summary
-SOLVE_TRAFFIC = {(96, 2, "forward_dag"): 14.83 * 57510348, (96, 2, "backward_dag"): 15.18 * 57510348}
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300's nominal FP64 rate, used only if the probe cannot run
+# DRAM bytes (read + write) per launch of a solve kernel of the 27-point IC(2) problem,
+# per factor entry: ncu captures (dram__bytes_read.sum + dram__bytes_write.sum, one
+# launch each) of the 48^3 and 64^3 problems gave 14.95 / 14.83 (forward) and 15.51 /
+# 15.18 (backward) bytes per entry; the 64^3 figures are scaled to the factor at hand
+SOLVE_TRAFFIC_PER_ENTRY = {(2, "forward_dag"): 14.83, (2, "backward_dag"): 15.18}
+# DRAM bytes (read + write) per factor entry of one numeric factorization (scatter +
+# task kernel) of the 27-point IC(k) problem, by k; filled from ncu captures
+NUMERIC_TRAFFIC_PER_ENTRY = {}
 
 
 def parse():
@@ -66,11 +75,19 @@ def parse():
                     help="batch workload instead: 512 7-point diffusion cubes, IC(1), FP32, one launch")
     ap.add_argument("--c5", action="store_true",
                     help="7-point diffusion workload instead: 160^3 (--side), sigma 2, z faces x100, IC(3)")
-    return ap.parse_args()
+    ap.add_argument("--leaf-rows", type=int, default=0,
+                    help="nested-dissection leaf size (the pruning of the ND tree); 0: --block-rows")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="leave the C4 / C3 / C5 workloads out of the default line")
+    a = ap.parse_args()
+    if a.leaf_rows <= 0:
+        a.leaf_rows = a.block_rows
+    return a
 
 
 def workload_name(a):
-    return (f"27-point Laplacian {a.side}^3 (n={a.side ** 3}), geometric ND, 2D blocks <= "
+    leaf = "" if a.leaf_rows == a.block_rows else f" (ND leaves <= {a.leaf_rows} rows)"
+    return (f"27-point Laplacian {a.side}^3 (n={a.side ** 3}), geometric ND{leaf}, 2D blocks <= "
             f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}, "
             f"{'block-DAG' if a.solve_mode == 0 else 'row-level'} triangular solves")
 
@@ -142,20 +159,22 @@ class ClockSampler:
                 "samples": len(loaded), "reasons": sorted(reasons)}
 
 
-def run_oracle_sample(side, k, reps=1):
-    """Oracle numeric IC(k) on a side^3 27-point problem: (flops, seconds per run)."""
+def oracle_problem(side, k, leaf_rows):
+    """The oracle's symbolic phase of the side^3 27-point problem, as the GPU arm orders
+    it (geometric ND with the same leaf size)."""
     import oracle
     import synth
     prob = synth.laplace3d_27pt(side)
-    perm, _ = oracle.nd_grid(side, side, side, 1, 4096)
-    h = oracle.OracleIC.from_problem(prob, perm, k)
-    times = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        st = h.numeric(prob.vals)
-        times.append(time.perf_counter() - t0)
-        assert st == 0
-    return h.flops, statistics.median(times)
+    perm, _ = oracle.nd_grid(side, side, side, 1, leaf_rows)
+    return prob, oracle.OracleIC.from_problem(prob, perm, k)
+
+
+def time_oracle_numeric(prob, h):
+    t0 = time.perf_counter()
+    st = h.numeric(prob.vals)
+    t = time.perf_counter() - t0
+    assert st == 0
+    return t
 
 
 def max_over_ranks(values, world, device="cuda"):
@@ -179,23 +198,21 @@ def job_rate(units_per_replica, world, seconds):
 def reference_arm(a, rank, world):
     if rank != 0:
         return
-    # bounded sample: a 48^3 sub-problem of the same family (about 1 s per step)
-    side = max(8, a.side // 2)
+    # each step: one oracle numeric factorization of the full workload (single thread)
+    prob, h = oracle_problem(a.side, a.k, a.leaf_rows)
     for _ in range(a.warmup):
-        run_oracle_sample(side, a.k)
-    ts, fl = [], 0.0
-    for _ in range(a.steps):
-        fl, t = run_oracle_sample(side, a.k)
-        ts.append(t)
+        time_oracle_numeric(prob, h)
+    ts = [time_oracle_numeric(prob, h) for _ in range(a.steps)]
     t = sum(ts) / len(ts)
+    fl = h.flops
     v = fl / t / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "sample": f"{side}^3 sub-problem, IC({a.k})"},
+            "config": {"workload": workload_name(a), "sample": f"the full {a.side}^3 workload, IC({a.k})"},
             "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": f"oracle numeric IC({a.k}) of the {side}^3 27-point problem "
-                                       f"per step ({fl:.3g} flops)"},
+                             "sample": f"one oracle numeric IC({a.k}) of the full {a.side}^3 27-point "
+                                       f"problem per step ({fl:.4g} flops)"},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -206,7 +223,7 @@ SHIFT_ALPHAS = [0.0] + [1e-3 * 2 ** j for j in range(13)]
 SHIFT_NE_TRAIN = (6, 8, 12, 16, 24)
 
 
-def shift_workload(a):
+def shift_workload(a, steps):
     """Q1 hex elasticity (ne^3 elements, clamped face, IC(0), geometric ND): time to a
     relative residual of 1e-8, all factorization attempts included, for the plain FP64
     form (FP64 factor, shift 0 then 1e-3 doubling) and the FP32 + learned-shift form
@@ -248,7 +265,7 @@ def shift_workload(a):
             h = ick.ic_symbolic(p.rowptr, p.colind, 0, perm, ranges, block_rows=4096, dtype=dtype,
                                warps_per_cta=a.warps)
             T.solve(h, av, b, x, mlp=model, nu=nu)  # warm-up
-            runs = [T.solve(h, av, b, x, mlp=model, nu=nu) for _ in range(max(1, a.steps))]
+            runs = [T.solve(h, av, b, x, mlp=model, nu=nu) for _ in range(max(1, steps))]
             r = min(runs, key=lambda q: q["seconds"])
             xh = x.cpu().numpy()
             r["true_relres"] = float(np.linalg.norm(p.scipy() @ xh - synth.rhs(p.n, 13)) /
@@ -262,7 +279,7 @@ def shift_workload(a):
     tot32 = sum(r["fp32_learned"]["ms"] for r in rows)
     line = {"metric": "elasticity IC(0) time to PCG relres 1e-8, FP32 + learned shift vs plain FP64",
             "value": tot64 / tot32, "unit": "x (plain FP64 time / FP32 learned-shift time)", "n_gpus": 1,
-            "steps": a.steps, "warmup": 1, "higher_is_better": True, "dtype": "f32 factor, f64 PCG",
+            "steps": steps, "warmup": 1, "higher_is_better": True, "dtype": "f32 factor, f64 PCG",
             "data": "synthetic",
             "config": {"workload": f"Q1 hex elasticity {a.ne}^3 elements (clamped face, 3 dof/node), E = 1, "
                                    f"held-out nu {list(SHIFT_NU_TEST)}, geometric ND, IC(0), b ~ N(0,1)",
@@ -270,10 +287,10 @@ def shift_workload(a):
                                    f"nu {list(SHIFT_NU_TRAIN)}",
                        "train_seconds": train_s, "train_loss": loss},
             "instances": rows, "total_ms_fp64_plain": tot64, "total_ms_fp32_learned": tot32}
-    print(json.dumps(line), flush=True)
+    return line
 
 
-def c3_workload(a):
+def c3_workload(a, warmup, steps):
     """512 independent 7-point diffusion cubes of side U{8..32} (kappa ~ LogNormal(0, 1)),
     IC(1), FP32 factors with FP64 pivots, all factored by one persistent launch, then
     batched FP64 PCG to 1e-8 (one captured CUDA graph iteration replayed).  Each step:
@@ -296,13 +313,13 @@ def c3_workload(a):
     b = torch.from_numpy(b_host).cuda()
     x = torch.empty_like(b)
     ick.ic_set_timing(h, True)
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         ick.ic_numeric(h, vals)
         ick.pcg_solve_batch(h, vals, b, x, 1e-8, 1000)
     torch.cuda.synchronize()
     fact, tts = [], []
     its = rels = None
-    for _ in range(a.steps):
+    for _ in range(steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         ick.ic_numeric(h, vals)
@@ -314,18 +331,18 @@ def c3_workload(a):
         tts.append(e0.elapsed_time(e1))
     mf = statistics.median(fact)
     line = {"metric": "batched IC(1) factor GFLOP/s and time to 1e-8 of 512 systems (one launch)",
-            "value": st["flops"] / (mf * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1, "steps": a.steps,
-            "warmup": a.warmup, "higher_is_better": True, "dtype": "f32 factor, f64 PCG", "data": "synthetic",
+            "value": st["flops"] / (mf * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "higher_is_better": True, "dtype": "f32 factor, f64 PCG", "data": "synthetic",
             "config": {"workload": "512 7-point diffusion cubes, side U{8..32}, kappa ~ LogNormal(0, 1), "
                                    "geometric ND, IC(1), one persistent launch",
                        "systems": len(probs), "n": st["n"], "nnz_l": st["nnz_l"], "tasks": st["ntasks"],
                        "flops": st["flops"]},
             "factor_ms": mf, "time_to_solution_ms": statistics.median(tts),
             "pcg_iters_min": int(its.min()), "pcg_iters_max": int(its.max()), "max_relres": float(rels.max())}
-    print(json.dumps(line), flush=True)
+    return line
 
 
-def c5_workload(a):
+def c5_workload(a, side, warmup, steps, densities=True):
     """7-point variable-coefficient diffusion (kappa ~ LogNormal(0, 2), z faces x100),
     geometric ND, 2D blocks <= 4096 rows, IC(3): FP32 factor + FP64 PCG to 1e-8, with
     the FP64 form beside it.  Reports the largest block density of the factor (the
@@ -337,7 +354,6 @@ def c5_workload(a):
 
     build()
     ick.load()
-    side = a.side if a.side != 96 else 160
     p = synth.config_problem(5, scale=side)
     perm, ranges = ick.ic_nd_grid(side, side, side, 1, a.block_rows)
     av = torch.from_numpy(p.vals).cuda()
@@ -351,12 +367,12 @@ def c5_workload(a):
                             warps_per_cta=a.warps)
         st = ick.ic_stats(h)
         ick.ic_set_timing(h, True)
-        for _ in range(a.warmup):
+        for _ in range(warmup):
             ick.ic_numeric(h, av)
             ick.pcg_solve(h, av, b, x, 1e-8, 5000)
         torch.cuda.synchronize()
         fact, tts, its = [], [], 0
-        for _ in range(a.steps):
+        for _ in range(steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             ick.ic_numeric(h, av)
@@ -372,6 +388,17 @@ def c5_workload(a):
                      "time_to_solution_ms": statistics.median(tts), "pcg_iters": int(its), "relres": float(rel),
                      "true_relres": true_rel}
         del h
+    line = {"metric": "IC(3) FP32 factor + FP64 PCG time to 1e-8 (7-point diffusion)",
+            "value": out["fp32"]["time_to_solution_ms"], "unit": "ms", "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "higher_is_better": False, "dtype": "f32 factor, f64 PCG", "data": "synthetic",
+            "config": {"workload": f"7-point diffusion {side}^3, kappa ~ LogNormal(0, 2), z faces x100, "
+                                   f"geometric ND, 2D blocks <= {a.block_rows} rows, IC(3)",
+                       "n": st["n"], "nnz_a": st["nnz_a"], "nnz_l": st["nnz_l"], "blocks": st["nblocks"],
+                       "tasks": st["ntasks"], "flops": st["flops"]},
+            **out,
+            "speedup_fp32_vs_fp64": out["fp64"]["time_to_solution_ms"] / out["fp32"]["time_to_solution_ms"]}
+    if not densities:
+        return line
     # largest block density: entries of each (row range, column range) block over its area
     hh = ick.ic_symbolic(p.rowptr, p.colind, 3, perm, ranges, block_rows=a.block_rows, host_only=1)
     urp, ucol, _, _, _ = ick.ic_get_upper(hh)
@@ -384,28 +411,21 @@ def c5_workload(a):
     area = np.outer(sz, sz)
     area[np.diag_indices(nb)] = sz * (sz + 1) / 2
     dens = np.where(cnt > 0, cnt / area, 0.0)
-    line = {"metric": "IC(3) FP32 factor + FP64 PCG time to 1e-8 (7-point diffusion)",
-            "value": out["fp32"]["time_to_solution_ms"], "unit": "ms", "n_gpus": 1, "steps": a.steps,
-            "warmup": a.warmup, "higher_is_better": False, "dtype": "f32 factor, f64 PCG", "data": "synthetic",
-            "config": {"workload": f"7-point diffusion {side}^3, kappa ~ LogNormal(0, 2), z faces x100, "
-                                   f"geometric ND, 2D blocks <= {a.block_rows} rows, IC(3)",
-                       "n": st["n"], "nnz_a": st["nnz_a"], "nnz_l": st["nnz_l"], "blocks": st["nblocks"],
-                       "tasks": st["ntasks"], "flops": st["flops"]},
-            "max_block_density": float(dens.max()), "blocks_denser_than_5pct": int((dens >= 0.05).sum()),
-            **out}
-    print(json.dumps(line), flush=True)
+    line["max_block_density"] = float(dens.max())
+    line["blocks_denser_than_5pct"] = int((dens >= 0.05).sum())
+    return line
 
 
 def main():
     a = parse()
     if a.shift:
-        shift_workload(a)
+        print(json.dumps(shift_workload(a, a.steps)), flush=True)
         return
     if a.c5:
-        c5_workload(a)
+        print(json.dumps(c5_workload(a, a.side if a.side != 96 else 160, a.warmup, a.steps)), flush=True)
         return
     if a.c3:
-        c3_workload(a)
+        print(json.dumps(c3_workload(a, a.warmup, a.steps)), flush=True)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -430,7 +450,7 @@ def main():
     ick.load()
 
     prob = synth.laplace3d_27pt(a.side)
-    perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.block_rows)
+    perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.leaf_rows)
     h = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
                         warps_per_cta=a.warps, solve_mode=a.solve_mode)
     st = ick.ic_stats(h)
@@ -452,6 +472,14 @@ def main():
     if a.numeric_only:
         a.no_e2e = True
         a.no_cpu_baseline = True
+
+    # arithmetic roofs of the numeric phase, measured on this GPU by the library's FMA
+    # throughput kernel (before the timed region)
+    try:
+        fp64_peak, fp64_src = ick.ic_fma_peak(ick.IC_F64), "measured (ic_fma_peak, FP64 FMA chains)"
+        fp32_peak = ick.ic_fma_peak(ick.IC_F32)
+    except ick.IckError:
+        fp64_peak, fp64_src, fp32_peak = FP64_NOMINAL_GFLOPS, "nominal GB300 FP64 rate", None
 
     for _ in range(a.warmup):
         step()
@@ -502,11 +530,20 @@ def main():
     # one solve launch reads every factor entry once (8-byte value + 4-byte index) and
     # four row vectors (row pointer, right-hand side, reciprocal diagonal, result)
     solve_bytes = nnz_l * 12 + n * 8 * 4
+    # the FP64 factor's arithmetic floor (flops / FP64 peak) lies above its HBM floor
+    # (compulsory bytes / bandwidth), so the FP64 FMA rate is its roof; the FP32 factor
+    # takes the same time, so what limits the kernel is instruction issue while every
+    # CTA is busy and the dependence chain of the top separators at the end
+    traffic_entry = NUMERIC_TRAFFIC_PER_ENTRY.get(a.k) if a.leaf_rows == a.block_rows else None
     roof_numeric = {"kernel": "numeric_persistent (+ numeric_prepare scatter)",
                     "bound": "alu", "achieved": st["flops"] / (mean_fact * 1e-3) / 1e9,
-                    "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "peak_source": "nominal FP64",
+                    "peak": fp64_peak, "unit": "GFLOP/s", "peak_source": fp64_src,
+                    "fp32_fma_peak_gflops": fp32_peak,
+                    "limiter": "instruction issue while all CTAs are busy, then the top separators' "
+                               "dependence chain (the FP32 factor takes as long)",
                     "hbm_achieved_gbs": st["bytes"] / (mean_fact * 1e-3) / 1e9,
-                    "hbm_peak_gbs": peak_hbm, "traffic": None}
+                    "hbm_peak_gbs": peak_hbm, "algorithmic_bytes": st["bytes"],
+                    "traffic": traffic_entry * nnz_l if traffic_entry else None}
     roof_numeric["frac"] = roof_numeric["achieved"] / roof_numeric["peak"]
     calls = max(1, tim["apply_calls"])
     roofs = {"numeric": (mean_fact, roof_numeric)}
@@ -517,7 +554,8 @@ def main():
              "achieved": solve_bytes / (per * 1e-3) / 1e9 if per > 0 else 0.0,
              "peak": peak_hbm, "unit": "GB/s", "peak_source": peak_src,
              "launch_ms": per, "algorithmic_bytes": solve_bytes,
-             "traffic": SOLVE_TRAFFIC.get((a.side, a.k, name))}
+             "traffic": (SOLVE_TRAFFIC_PER_ENTRY[(a.k, name)] * nnz_l
+                         if (a.k, name) in SOLVE_TRAFFIC_PER_ENTRY else None)}
         r["frac"] = r["achieved"] / r["peak"]
         roofs[name] = (tim[key] / a.steps, r)
     dominant = max(roofs.values(), key=lambda v: v[0])[1]
@@ -624,6 +662,17 @@ def main():
             parity[name] = {"pattern_equal": bool(np.array_equal(rp, orp) and np.array_equal(ci, oci)),
                             "max_abs_err_over_max_A": float(np.abs(lv - ref).max() / amax)}
         line["parity_vs_oracle"] = parity
+
+    # the method's other workloads, outside the timed region, a few fixed repetitions
+    # each (one GPU only: the replicas of a multi-GPU run measure the default workload)
+    if world == 1 and not a.no_sub and not a.numeric_only:
+        del h, h32
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        line["c4_shift"] = shift_workload(a, steps=1)
+        line["c3_batch"] = c3_workload(a, warmup=2, steps=3)
+        line["c5"] = c5_workload(a, 160, warmup=1, steps=2, densities=False)
+        line["sub_workloads_wall_s"] = time.perf_counter() - t0
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:

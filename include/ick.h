@@ -159,27 +159,45 @@ int ic_numeric(ic_handle* h, const void* values, void* stream, int64_t* breakdow
  * handle's work vector and completion stamps, so calls on one handle must not overlap
  * on the GPU (issue them on one stream).  Their row dependences are acyclic, so the
  * bounded waits can only expire if the GPU stops the kernel for longer than
- * opts.timeout_s; z is then undefined and the next pcg_solve reports IC_ERR_TIMEOUT.
+ * opts.timeout_s; z is then undefined and the timeout is recorded on the handle:
+ * ic_apply_status reports it (and pcg_solve reports a timeout of its own
+ * applications).  Each call starts afresh, so one expired wait does not stop later
+ * calls.
  * Errors: IC_ERR_ARG, IC_ERR_STATE (no successful ic_numeric yet), IC_ERR_CUDA. */
 int ic_apply(ic_handle* h, const void* r, void* z, void* stream);
 
+/* Synchronises stream, then reports whether a triangular-solve wait of an ic_apply on
+ * this handle expired since the last ic_apply_status or pcg_solve (IC_ERR_TIMEOUT),
+ * and clears that record.  Errors: IC_ERR_ARG, IC_ERR_TIMEOUT, IC_ERR_CUDA. */
+int ic_apply_status(ic_handle* h, void* stream);
+
 /* The same preconditioner application as ic_apply, for callers that cannot allocate
- * GPU memory where they apply it: code running while a stream is captured into a CUDA
- * graph (cudaMalloc is not allowed during capture), code whose device memory is owned
- * by another framework's allocator, or loops that must never reach the allocator.
- * The paper has no counterpart; this is an interface convenience of this library.
- * The call allocates nothing and calls no allocating routine: the solves' scratch (the
- * permuted work vector, per-row completion stamps and claim counters) lives in one
- * file-scope device array for at most 1,048,576 rows (about 12 MB), which every GPU
- * that loads the library keeps until the process exits.  The first call on a device
- * looks up that array's device address (once per device, with the device current),
- * so make it before any stream capture begins.  All calls share the array and it keeps
- * the last call's contents (counters are cleared at the start of each call): calls
- * that overlap on the GPU -- on different streams or from different threads, for any
- * handle -- race, and the caller must serialise them.  r and z: as for ic_apply.
- * Errors: IC_ERR_ARG (NULL or aliased vectors, or n above 1,048,576 rows),
- * IC_ERR_STATE (no successful ic_numeric yet), IC_ERR_CUDA. */
+ * GPU memory where they apply it: a plugin running inside another framework that owns
+ * the device's memory budget and gives its plugins no allocator, or a loop with a hard
+ * latency limit in which a cudaMalloc (which may synchronise the device) is not
+ * allowed.  The paper has no counterpart; this is an interface convenience of this
+ * library.  The call allocates nothing and calls no allocating routine: the solves'
+ * scratch (the permuted work vector, per-row completion stamps, claim counters, abort
+ * word and timeout record) lives in one file-scope device array for at most 1,048,576
+ * rows (about 12 MB), which every GPU that loads the library keeps until the process
+ * exits.  It runs the row-level solves (every row a unit, ic_opts.solve_mode = 1),
+ * whatever the handle's solve_mode: they need no per-handle task state, and they are
+ * 1.3-1.7x slower than the default block-DAG solves of ic_apply on large 3D problems.
+ * The first call on a device looks up that array's device address (once per device,
+ * with the device current), so make it before any stream capture begins.  All calls
+ * share the array and it keeps the last call's contents (counters are cleared at the
+ * start of each call): calls that overlap on the GPU -- on different streams or from
+ * different threads, for any handle -- race, and the caller must serialise them.  A
+ * wait that expires leaves z undefined; the call cannot report it (it does not wait
+ * for the GPU), ic_apply_static_status does.  r and z: as for ic_apply.
+ * Errors: IC_ERR_ARG (NULL or aliased vectors, n above 1,048,576 rows, or an IC_F32
+ * factor), IC_ERR_STATE (no successful ic_numeric yet), IC_ERR_CUDA. */
 int ic_apply_static(ic_handle* h, const void* r, void* z, void* stream);
+
+/* Synchronises stream, then reports whether a solve wait of an ic_apply_static call on
+ * the current device expired since the last ic_apply_static_status (IC_ERR_TIMEOUT),
+ * and clears that record.  Allocates nothing.  Errors: IC_ERR_TIMEOUT, IC_ERR_CUDA. */
+int ic_apply_static_status(void* stream);
 
 /* Preconditioned conjugate gradients on A x = b with M = L L^T (textbook PCG, x0 = 0,
  * stop when ||r||_2 / ||b||_2 <= tol).  A's pattern is the one given to ic_symbolic.
@@ -300,11 +318,27 @@ int ic_set_timing(ic_handle* h, int on);
 int ic_reset_timing(ic_handle* h);
 int ic_get_timing(const ic_handle* h, ic_timing_t* out);
 
+/* Fused multiply-add throughput of the current GPU in GFLOP/s for dtype IC_F64 or
+ * IC_F32 (2 flops per FMA): a kernel of independent register FMA chains, 8 CTAs of 256
+ * threads per SM, best of three timed launches (CUDA events on stream, which is
+ * synchronised).  It is the arithmetic roof against which the numeric factorization's
+ * GFLOP/s (Section 3.3's Chol/Trsm/Herk/Gemm flops) is compared; the paper has no
+ * counterpart.  Allocates and frees a buffer of 8 bytes per thread.
+ * Errors: IC_ERR_ARG, IC_ERR_CUDA. */
+int ic_fma_peak(int dtype, double* gflops, void* stream);
+
 /* Fault injection for tests, done on the host: adds `extra` to task t's initial
  * in-degree, so with extra = 1 the task is never released and the next ic_numeric
  * ends in IC_ERR_TIMEOUT once opts.timeout_s has passed (every device wait is
  * bounded; nothing traps).  extra = 0 restores the plan.  Errors: IC_ERR_ARG, IC_ERR_CUDA. */
 int ic_test_hold_task(ic_handle* h, int64_t t, int extra);
+
+/* The same for the block-DAG solves (solve_mode 0): adds `extra` to the initial
+ * in-degree of task t (claim order of ic_get_solve_tasks) of the forward (backward = 0)
+ * or backward (1) solve, so with extra = 1 every later ic_apply gives up that task's
+ * wait after opts.timeout_s and records a timeout (ic_apply_status, pcg_solve report
+ * it).  extra = 0 restores the plan.  Errors: IC_ERR_ARG, IC_ERR_STATE, IC_ERR_CUDA. */
+int ic_test_hold_solve_task(ic_handle* h, int backward, int64_t t, int extra);
 
 /* Batched symbolic factorization: count independent SPD matrices (different sizes
  * allowed) become one block-diagonal system whose task DAG is the union of the

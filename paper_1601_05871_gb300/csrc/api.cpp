@@ -647,6 +647,20 @@ int ic_apply(ic_handle* h, const void* r, void* z, void* stream) {
     return IC_OK;
 }
 
+int ic_apply_status(ic_handle* h, void* stream) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    if (h->opts.host_only || h->hp.n == 0) return IC_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rec = 0;
+    CK(cudaMemcpyAsync(&rec, h->sp.counter + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!rec) return IC_OK;
+    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
+}
+
 int ic_apply_static(ic_handle* h, const void* r, void* z, void* stream) {
     if (!h || ((!r || !z) && h->hp.n > 0)) return fail(IC_ERR_ARG, "NULL argument");
     if (r == z && h->hp.n > 0) return fail(IC_ERR_ARG, "r and z may not alias");
@@ -658,13 +672,17 @@ int ic_apply_static(ic_handle* h, const void* r, void* z, void* stream) {
                                     std::to_string(static_apply_max_rows()) + " rows; use ic_apply");
     if (h->hp.n == 0) return IC_OK;
     DeviceGuard g(h->device);
-    // process-wide call counter: completion stamps 2*epoch and 2*epoch+1 never repeat
-    // (the stamps are cleared and the count restarts long before int overflow)
-    static std::atomic<int> calls{0};
-    int epoch = ++calls;
+    // one call counter per device (each device has its own scratch array and stamps):
+    // completion stamps 2*epoch and 2*epoch+1 never repeat on that device; the stamps
+    // are cleared and its count restarts long before int overflow
+    static std::atomic<int> calls[kStaticApplyDevices];
+    if (h->device < 0 || h->device >= kStaticApplyDevices)
+        return fail(IC_ERR_ARG, "ic_apply_static: device index above the supported range");
+    int epoch = ++calls[h->device];
     bool clear = false;
     if (epoch >= (1 << 29)) {
-        calls = 1;
+        int expect = epoch;
+        calls[h->device].compare_exchange_strong(expect, 1);
         epoch = 1;
         clear = true;
     }
@@ -673,6 +691,12 @@ int ic_apply_static(ic_handle* h, const void* r, void* z, void* stream) {
                            tmo, h->grid_apply, static_cast<cudaStream_t>(stream), clear));
     h->tm.launches += 2;
     return IC_OK;
+}
+
+int ic_apply_static_status(void* stream) {
+    int rec = 0;
+    CK(static_apply_timeout(&rec, static_cast<cudaStream_t>(stream)));
+    return rec ? fail(IC_ERR_TIMEOUT, "ic_apply_static: triangular solve wait timed out") : IC_OK;
 }
 
 int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, double tol, int maxit,
@@ -691,7 +715,7 @@ int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, doub
     const int parts = pcg_parts(n);
     int st = 0;
     int64_t& nl = h->tm.launches;
-    CK(cudaMemsetAsync(h->sp.counter + 2, 0, sizeof(int), s));  // solve abort word
+    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s));  // solve timeout record
     ++nl;
     CK(pcg_init(n, b, x, h->r, s));
     ++nl;
@@ -740,7 +764,7 @@ int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, doub
     {
         int ctr[4];
         CK(cudaMemcpy(ctr, h->sp.counter, sizeof(ctr), cudaMemcpyDeviceToHost));
-        if (ctr[2]) return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
+        if (ctr[3]) return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
     }
     if (iters) *iters = it;
     if (relres) *relres = rel;
@@ -792,7 +816,7 @@ int pcg_solve_batch(ic_handle* h, const void* A_vals, const double* b, double* x
     const double* av = static_cast<const double*>(A_vals);
     BatchScalars& B = h->bs;
     const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
-    CK(cudaMemsetAsync(h->sp.counter + 2, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s));  // solve timeout record
     CK(pcg_init(n, b, x, h->r, s));
     CK(batch_dot(h->d_row_off, count, b, b, B.tmp, s));
     CK(batch_scalars(B, count, 4, tol, s));
@@ -833,7 +857,7 @@ int pcg_solve_batch(ic_handle* h, const void* A_vals, const double* b, double* x
     CK(cudaMemcpy(its.data(), B.iters, count * sizeof(int), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(rel.data(), B.relres, count * sizeof(double), cudaMemcpyDeviceToHost));
     int abort_word = 0;
-    CK(cudaMemcpy(&abort_word, h->sp.counter + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&abort_word, h->sp.counter + 3, sizeof(int), cudaMemcpyDeviceToHost));
     CK(cudaEventRecord(h->cap_ev[1], s));
     CK(cudaStreamWaitEvent(us, h->cap_ev[1], 0));
     if (iters) std::memcpy(iters, its.data(), count * sizeof(int));
@@ -1116,6 +1140,26 @@ int ic_get_trace(const ic_handle* h, uint64_t* out) {
     if (!h->trace_buf) return fail(IC_ERR_STATE, "tracing was never enabled");
     DeviceGuard g(h->device);
     CK(cudaMemcpy(out, h->trace_buf, 4 * size_t(h->hp.total_items) * 8, cudaMemcpyDeviceToHost));
+    return IC_OK;
+}
+
+int ic_fma_peak(int dtype, double* gflops, void* stream) {
+    if (!gflops || (dtype != IC_F64 && dtype != IC_F32)) return fail(IC_ERR_ARG, "bad argument");
+    *gflops = 0.0;
+    CK(measure_fma_peak(dtype, gflops, static_cast<cudaStream_t>(stream)));
+    return IC_OK;
+}
+
+int ic_test_hold_solve_task(ic_handle* h, int backward, int64_t t, int extra) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    if (h->device < 0) return fail(IC_ERR_STATE, "host-only handle");
+    if (h->opts.solve_mode != 0) return fail(IC_ERR_STATE, "the handle's solves are not block-DAG solves");
+    const SolveTasks& ST = backward ? h->hp.bs : h->hp.fs;
+    if (t < 0 || t >= int64_t(ST.task.size()) || extra < 0) return fail(IC_ERR_ARG, "task out of range");
+    DeviceGuard g(h->device);
+    const int v = ST.indeg0[t] + extra;
+    const size_t off = (backward ? h->hp.fs.task.size() : 0) + size_t(t);
+    CK(cudaMemcpy(const_cast<int*>(h->sp.dag_indeg0) + off, &v, sizeof(int), cudaMemcpyHostToDevice));
     return IC_OK;
 }
 

@@ -38,13 +38,21 @@ __device__ __forceinline__ bool aborted(const int* abort_word) {
     return *reinterpret_cast<const volatile int*>(abort_word) != 0;
 }
 
+// Ends the solve after a wait gave up: the abort word stops every other waiting CTA
+// of this launch (it is cleared when the next application starts); the word after it
+// records the timeout until the host reads it.
+__device__ __forceinline__ void raise_abort(int* abort_word) {
+    atomicExch(abort_word, 1);
+    atomicOr(abort_word + 1, 1);
+}
+
 // Thread 0: wait until *c is zero; false on abort or timeout.
 __device__ bool await_zero(const int* c, int* abort_word, unsigned long long deadline) {
     const volatile int* p = c;
     unsigned spins = 0;
     while (*p != 0) {
         if ((++spins & 63) == 0 && (aborted(abort_word) || gclock() > deadline)) {
-            atomicExch(abort_word, 1);
+            raise_abort(abort_word);
             return false;
         }
         __nanosleep(64);
@@ -61,7 +69,7 @@ __device__ bool await_count(const int* done, int need, int* abort_word, unsigned
     int d;
     while ((d = *p) < need) {
         if ((++spins & 255) == 0 && (aborted(abort_word) || gclock() > deadline)) {
-            atomicExch(abort_word, 1);
+            raise_abort(abort_word);
             return false;
         }
         (void)d;
@@ -480,7 +488,7 @@ cudaError_t launch_apply_dag(const SolvePlan& S, const double* r, double* z, uns
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(S.dag_taken, 0, size_t(S.nftask + S.nbtask) * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(S.counter, 0, 2 * sizeof(int), s);
+    e = cudaMemsetAsync(S.counter, 0, 3 * sizeof(int), s);  // claims and the abort word
     if (e != cudaSuccess) return e;
     if (t0) cudaEventRecord(t0, s);
     if (S.dtype == IC_F32)

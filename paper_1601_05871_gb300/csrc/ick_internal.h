@@ -158,7 +158,9 @@ struct SolvePlan {
     const int* acol;
     double* y;       // permuted work vector
     int* flag;       // per-row completion stamps of the solves
-    int* counter;    // [0] forward row claim, [1] backward row claim, [2] abort/timeout
+    int* counter;    // [0] forward row claim, [1] backward row claim, [2] abort word of the
+                     // running application (cleared when each one starts), [3] timeout
+                     // record (set with the abort word, cleared by the host when read)
     const int* fwd_order;  // rows in forward claim order (by dependence depth)
     const int* bwd_order;  // rows in backward claim order
     const int* fwd_pad;    // padded claim orders (-1: empty slot) and their lengths
@@ -232,7 +234,11 @@ cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, d
 cudaError_t apply_blocks_per_sm(int* blocks);
 cudaError_t launch_solve_prepare(const SolvePlan& S, cudaStream_t s);
 // Allocation-free application (solve.cu): scratch in a file-scope device array.
+constexpr int kStaticApplyDevices = 64;  // devices whose scratch address is cached
 int static_apply_max_rows();
+// Reads and clears the timeout record of the current device's scratch (*timed_out = 0
+// or 1); synchronises the stream.
+cudaError_t static_apply_timeout(int* timed_out, cudaStream_t s);
 cudaError_t launch_apply_static(const SolvePlan& S, const double* r, double* z, int epoch,
                                 unsigned long long timeout_ns, int grid, cudaStream_t s,
                                 bool clear_stamps);
@@ -287,6 +293,9 @@ size_t features_scratch_bytes();
 cudaError_t launch_mlp_forward(const MlpDev& M, const float* X, long long n, float* y, cudaStream_t s);
 cudaError_t launch_mlp_grad(const MlpDev& M, const float* X, const float* t, long long n, cudaStream_t s);
 cudaError_t launch_mlp_adam(const MlpDev& M, float lr, int step, cudaStream_t s);
+
+// FMA throughput of the current GPU in GFLOP/s (probe.cu); synchronises the stream.
+cudaError_t measure_fma_peak(int dtype, double* gflops, cudaStream_t s);
 
 // Host symbolic phase (host.cpp).
 // k_order: updates into each block applied in ascending k (the task generator's order,

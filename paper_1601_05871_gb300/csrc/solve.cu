@@ -11,6 +11,7 @@
 // waits on a row that no running warp owns; rows of equal depth (independent ND
 // subtrees, wavefronts inside a part) run concurrently.
 #include <cstdint>
+#include <mutex>
 
 #include "ick_internal.h"
 
@@ -30,6 +31,15 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Ends a solve whose wait gave up: the abort word (stops every other waiting warp of
+// this launch; cleared when the next application starts) and, in the word after it, the
+// timeout record, which stays set until the host reads it (pcg_solve, ic_apply_status,
+// ic_apply_static_status).
+__device__ __forceinline__ void raise_abort(int* abort_word) {
+    atomicExch(abort_word, 1);
+    atomicOr(abort_word + 1, 1);
+}
+
 // Spin until flag[i] == want; false on timeout or abort.
 __device__ __forceinline__ bool wait_flag(const int* flag, int i, int want, int* abort_word,
                                           unsigned long long deadline) {
@@ -38,7 +48,7 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int i, int want, int*
     while (*f != want) {
         if ((++spins & 255) == 0) {
             if (*(volatile int*)abort_word) return false;
-            if (gtimer() > deadline) { atomicExch(abort_word, 1); return false; }
+            if (gtimer() > deadline) { raise_abort(abort_word); return false; }
         }
         __nanosleep(32);
     }
@@ -125,7 +135,7 @@ __device__ __forceinline__ double await_value(const double* x, int i, int* abort
     while (b == kUnset) {
         if ((++spins & 255) == 0) {
             if (*(volatile int*)abort_word || gtimer() > deadline) {
-                atomicExch(abort_word, 1);
+                raise_abort(abort_word);
                 ok = false;
                 return 0.0;
             }
@@ -164,7 +174,7 @@ __device__ __forceinline__ float await_value(const float* x, int i, int* abort_w
     while (b == -1) {
         if ((++spins & 255) == 0) {
             if (*(volatile int*)abort_word || gtimer() > deadline) {
-                atomicExch(abort_word, 1);
+                raise_abort(abort_word);
                 ok = false;
                 return 0.f;
             }
@@ -419,7 +429,7 @@ cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epo
     const size_t bytes = 2 * size_t(S.n) * (S.dtype == IC_F32 ? sizeof(float) : sizeof(double));
     cudaError_t e = cudaMemsetAsync(S.y, 0xff, bytes, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(S.counter, 0, 2 * sizeof(int), s);
+    e = cudaMemsetAsync(S.counter, 0, 3 * sizeof(int), s);  // claims and the abort word
     if (e != cudaSuccess) return e;
     if (S.dtype == IC_F32)
         return launch_solves<float>(S, S.uval32, S.rdiag32, r, z, reinterpret_cast<float*>(S.y), grid,
@@ -439,19 +449,20 @@ cudaError_t launch_solve_prepare(const SolvePlan& S, cudaStream_t s) {
 // ---------------------------------------------------------------------------------
 // Allocation-free variant of the preconditioner application (ic_apply_static).
 //
-// Some callers cannot call cudaMalloc where they apply the preconditioner: code that
-// runs while a stream is being captured into a CUDA graph (allocation is not
-// permitted during capture), code inside frameworks that own the whole device memory
-// budget through their own allocator, or latency-critical loops that must not touch
-// the allocator.  For them the solve's scratch -- the permuted work vector, the
-// per-row completion stamps and the two row-claim counters plus the abort word --
-// lives in one file-scope device array, sized for at most kStaticApplyRows rows.
-// Every GPU that loads the library keeps this array until the process exits; all
-// calls share it, so calls that overlap on the GPU (on different streams, or from
-// different threads) race and must be serialised by the caller.  The array keeps the
-// contents of the last call: the claim counters and the abort word are cleared at the
-// start of every call, and the completion stamps never need clearing because each
-// call uses stamps no earlier call has written (a process-wide call counter).
+// Some callers cannot call cudaMalloc where they apply the preconditioner: a plugin
+// that runs inside another framework which owns the device's memory budget and hands
+// its plugins no allocator, or a loop with a hard latency limit in which a cudaMalloc
+// (which may synchronise the device) is not allowed.  For them the solve's scratch --
+// the permuted work vector, the per-row completion stamps, the two row-claim counters,
+// the abort word and the timeout record -- lives in one file-scope device array, sized
+// for at most kStaticApplyRows rows.  Every GPU that loads the library keeps this array
+// until the process exits; all calls share it, so calls that overlap on the GPU (on
+// different streams, or from different threads) race and must be serialised by the
+// caller.  The array keeps the contents of the last call: the claim counters and the
+// abort word are cleared at the start of every call, and the completion stamps never
+// need clearing because each call on a device uses stamps that no earlier call on that
+// device has written (a per-device call counter).  The solves are the row-level
+// kernels above (their scratch is one work vector and one stamp per row).
 constexpr int kStaticApplyRows = 1 << 20;
 constexpr size_t kStaticApplyBytes =
     size_t(kStaticApplyRows) * sizeof(double) + size_t(kStaticApplyRows) * sizeof(int) + 16;
@@ -460,47 +471,75 @@ static __device__ __align__(256) unsigned char g_apply_scratch[kStaticApplyBytes
 
 int static_apply_max_rows() { return kStaticApplyRows; }
 
+namespace {
+
 // Device address of g_apply_scratch on the current device (the symbol's name is only
-// a host-side stand-in).  Looked up once per device, with that device current.
-cudaError_t static_apply_scratch(void** out) {
-    static void* addr[64] = {};
+// a host-side stand-in).  Looked up once per device, with that device current; the
+// lookup of each device runs once even when several threads make their first call
+// together.
+cudaError_t static_apply_scratch(unsigned char** out) {
+    static std::once_flag once[kStaticApplyDevices];
+    static void* addr[kStaticApplyDevices] = {};
+    static cudaError_t err[kStaticApplyDevices] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!addr[dev]) {
+    if (dev < 0 || dev >= kStaticApplyDevices) return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [dev] {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_apply_scratch);
-        if (e != cudaSuccess) return e;
+        err[dev] = cudaGetSymbolAddress(&p, g_apply_scratch);
         addr[dev] = p;
-    }
-    *out = addr[dev];
+    });
+    if (err[dev] != cudaSuccess) return err[dev];
+    *out = static_cast<unsigned char*>(addr[dev]);
     return cudaSuccess;
 }
+
+int* static_counters(unsigned char* base) {
+    return reinterpret_cast<int*>(base + size_t(kStaticApplyRows) * (sizeof(double) + sizeof(int)));
+}
+
+}  // namespace
 
 cudaError_t launch_apply_static(const SolvePlan& H, const double* r, double* z, int epoch,
                                 unsigned long long timeout_ns, int grid, cudaStream_t s,
                                 bool clear_stamps) {
     if (H.n == 0) return cudaSuccess;
     if (H.n > kStaticApplyRows) return cudaErrorInvalidValue;
-    void* base = nullptr;
+    unsigned char* base = nullptr;
     cudaError_t e = static_apply_scratch(&base);
     if (e != cudaSuccess) return e;
     SolvePlan S = H;
-    S.y = static_cast<double*>(base);
-    S.flag = reinterpret_cast<int*>(static_cast<unsigned char*>(base) + size_t(kStaticApplyRows) * sizeof(double));
-    S.counter = reinterpret_cast<int*>(static_cast<unsigned char*>(base) +
-                                       size_t(kStaticApplyRows) * (sizeof(double) + sizeof(int)));
+    S.y = reinterpret_cast<double*>(base);
+    S.flag = reinterpret_cast<int*>(base + size_t(kStaticApplyRows) * sizeof(double));
+    S.counter = static_counters(base);
     if (clear_stamps) {
         e = cudaMemsetAsync(S.flag, 0, size_t(kStaticApplyRows) * sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
-    e = cudaMemsetAsync(S.counter, 0, 3 * sizeof(int), s);
+    e = cudaMemsetAsync(S.counter, 0, 3 * sizeof(int), s);  // claims and the abort word
     if (e != cudaSuccess) return e;
     forward_solve<<<grid, kApplyThreads, 0, s>>>(S, r, 2 * epoch, timeout_ns);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     backward_solve<<<grid, kApplyThreads, 0, s>>>(S, z, 2 * epoch + 1, timeout_ns);
     return cudaGetLastError();
+}
+
+cudaError_t static_apply_timeout(int* timed_out, cudaStream_t s) {
+    *timed_out = 0;
+    unsigned char* base = nullptr;
+    cudaError_t e = static_apply_scratch(&base);
+    if (e != cudaSuccess) return e;
+    int* rec = static_counters(base) + 3;
+    int v = 0;
+    if ((e = cudaMemcpyAsync(&v, rec, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (v) {
+        if ((e = cudaMemsetAsync(rec, 0, sizeof(int), s)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    }
+    *timed_out = v != 0;
+    return cudaSuccess;
 }
 
 cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, double* y,

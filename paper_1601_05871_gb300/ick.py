@@ -63,7 +63,9 @@ def load():
         "ic_symbolic": (I, [P, I, P, P, I64, P, P]),
         "ic_numeric": (I, [P, P, P, P]),
         "ic_apply": (I, [P, P, P, P]),
+        "ic_apply_status": (I, [P, P]),
         "ic_apply_static": (I, [P, P, P, P]),
+        "ic_apply_static_status": (I, [P]),
         "pcg_solve": (I, [P, P, P, P, D, I, P, P, P]),
         "ic_get_factor": (I, [P, P, P, P, P]),
         "ic_stats": (I, [P, P]),
@@ -76,7 +78,9 @@ def load():
         "ic_set_timing": (I, [P, I]),
         "ic_reset_timing": (I, [P]),
         "ic_get_timing": (I, [P, P]),
+        "ic_fma_peak": (I, [I, P, P]),
         "ic_test_hold_task": (I, [P, I64, I]),
+        "ic_test_hold_solve_task": (I, [P, I, I64, I]),
         "ic_symbolic_batch": (I, [I64, P, I, P, P, P, P, P]),
         "ic_batch_info": (I, [P, P, P]),
         "pcg_solve_batch": (I, [P, P, P, P, D, I, P, P, P]),
@@ -232,6 +236,18 @@ def ic_numeric(h, values, stream=None):
 
 def ic_apply(h, r, z, stream=None):
     _check(load().ic_apply(h.ptr, _p(r), _p(z), _stream(stream)))
+
+
+def ic_apply_status(h, stream=None):
+    """Raises IckError(IC_ERR_TIMEOUT) if a solve wait of an earlier ic_apply expired
+    (synchronises the stream; clears the record)."""
+    _check(load().ic_apply_status(h.ptr, _stream(stream)))
+
+
+def ic_apply_static_status(stream=None):
+    """Raises IckError(IC_ERR_TIMEOUT) if a solve wait of an earlier ic_apply_static on
+    the current device expired (synchronises the stream; clears the record)."""
+    _check(load().ic_apply_static_status(_stream(stream)))
 
 
 def ic_apply_static(h, r, z, stream=None):
@@ -415,6 +431,17 @@ def ic_get_timing(h):
     t = ic_timing_t()
     _check(load().ic_get_timing(h.ptr, C.byref(t)))
     return {f: getattr(t, f) for f, _ in t._fields_}
+
+
+def ic_fma_peak(dtype=IC_F64, stream=None):
+    """Measured FMA throughput (GFLOP/s) of the current GPU for IC_F64 or IC_F32."""
+    g = np.zeros(1, dtype=np.float64)
+    _check(load().ic_fma_peak(int(dtype), _p(g), _stream(stream)))
+    return float(g[0])
+
+
+def ic_test_hold_solve_task(h, t, extra=1, backward=False):
+    _check(load().ic_test_hold_solve_task(h.ptr, int(bool(backward)), int(t), int(extra)))
 
 
 def ic_test_hold_task(h, t, extra=1):

@@ -210,7 +210,7 @@ def test_timeout_when_a_task_is_never_released(ick, orc):
     ick.ic_numeric(h, v)
     o = orc.OracleIC.from_problem(prob, perm, 1)
     o.numeric(prob.vals)
-    assert np.abs(ick.ic_get_factor(h)[2] - o.values()).max() <= TOL * 4
+    assert np.abs(ick.ic_get_factor(h)[2] - o.values()).max() <= TOL * np.abs(prob.vals).max()
 
 
 def test_apply_matches_oracle(ick, orc):
@@ -229,6 +229,45 @@ def test_apply_matches_oracle(ick, orc):
     assert np.abs(z.cpu().numpy() - zr).max() <= 1e-11 * np.abs(zr).max()
     with pytest.raises(ick.IckError):
         ick.ic_apply(h, z, z)
+
+
+def test_solve_timeout_is_reported_and_later_applies_recover(ick, orc):
+    """Host-side fault injection into the block-DAG solve: one forward task's in-degree
+    is raised so that nothing releases it.  The wait gives up after timeout_s; the
+    timeout is recorded, ic_apply_status and pcg_solve report it, and once the plan is
+    restored the next applications are correct again (each one clears the abort word
+    of the previous)."""
+    import torch
+    prob = synth.diffusion3d_7pt(14, sigma=1.0, seed=3002)
+    perm, ranges = ick.ic_nd_grid(14, 14, 14, 1, 256)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 1, perm, ranges, block_rows=256, timeout_s=0.5)
+    av = dev(prob.vals)
+    ick.ic_numeric(h, av)
+    o = orc.OracleIC.from_problem(prob, perm, 1)
+    o.numeric(prob.vals)
+    nt = len(ick.ic_get_solve_tasks(h)["tasks"])
+    rh = np.random.default_rng(4).standard_normal(prob.n)
+    r = dev(rh)
+    z = torch.empty_like(r)
+    ick.ic_test_hold_solve_task(h, nt // 2, 1)
+    ick.ic_apply(h, r, z)
+    with pytest.raises(ick.IckError) as e:
+        ick.ic_apply_status(h)
+    assert e.value.status == 4
+    ick.ic_apply_status(h)  # the record was cleared by the read
+    b = dev(synth.rhs(prob.n, 5))
+    x = torch.empty_like(b)
+    with pytest.raises(ick.IckError) as e:
+        ick.pcg_solve(h, av, b, x, 1e-8, 3)
+    assert e.value.status == 4
+    ick.ic_test_hold_solve_task(h, nt // 2, 0)
+    zr = o.apply(rh)
+    for _ in range(2):
+        ick.ic_apply(h, r, z)
+        ick.ic_apply_status(h)
+        assert np.abs(z.cpu().numpy() - zr).max() <= 1e-11 * np.abs(zr).max()
+    it, rel = ick.pcg_solve(h, av, b, x, 1e-8, 500)
+    assert rel <= 1e-8
 
 
 @pytest.mark.parametrize("dtype", [0, 1])

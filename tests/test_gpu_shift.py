@@ -79,6 +79,20 @@ def test_mlp_forward_matches_oracle(ick):
     assert np.array_equal(ick.ic_mlp_get_params(m), theta)
 
 
+def test_mlp_forward_hand_derived_golden(ick):
+    """The hand-derived 2-unit network of tests/golden/mlp_forward_h2.txt, embedded in
+    the library's 32-unit layout with zero extra units: every value is a short dyadic
+    fraction, so the FP32 kernel must give the derived outputs exactly."""
+    import torch
+    from test_shift_oracle import pad_network, read_mlp_golden
+    H, theta, mean, std, X, y = read_mlp_golden()
+    m = ick.Mlp(pad_network(theta, H, 32).astype(np.float32))
+    ick.ic_mlp_set_scaling(m, mean.astype(np.float32), std.astype(np.float32))
+    out = torch.empty(len(X), dtype=torch.float32, device="cuda")
+    ick.ic_mlp_forward(m, dev(X.astype(np.float32)), out)
+    assert np.array_equal(out.cpu().numpy(), y.astype(np.float32))
+
+
 @pytest.mark.parametrize("n", [1, 7, 300, 5000])
 def test_mlp_gradient_matches_oracle(ick, n):
     theta, X, t, mean, std = _net(2 + n, n)

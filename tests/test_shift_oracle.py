@@ -149,3 +149,107 @@ def test_retry_rule_resolves_the_golden_breakdown(orc):
     a, tries = S.first_success(lambda x: o.numeric(vals, x) != 0, 0.0)
     assert tries > 1 and a > 0.0
     assert o.numeric(vals, a) == 0 and o.numeric(vals, 0.0) != 0
+
+
+# ------------------------------------------------ the shifted factorization
+
+
+def _csr_from_dense(A):
+    rows, cols = np.nonzero(A)
+    rp = np.zeros(A.shape[0] + 1, dtype=np.int64)
+    np.add.at(rp, rows + 1, 1)
+    return np.cumsum(rp), cols.astype(np.int32), A[rows, cols]
+
+
+def test_shifted_factor_hand_derived_3x3(orc):
+    """B = [[2,2,4],[2,5,0],[4,0,4]], identity order, IC(0): the fill (2,1) has level 1
+    and is dropped.  The shift multiplies the diagonal of B by (1 + alpha) before any
+    elimination.  alpha = 1: B_00 -> 4, L_00 = 2, L_10 = 1, L_20 = 2, L_11 = sqrt(10 - 1)
+    = 3, L_22 = sqrt(8 - 4) = 2 (the dropped fill is discarded, not added to the
+    diagonal).  alpha = 0: L_22^2 = 4 - 8 < 0, so row 2 breaks down.  An additive
+    shift, a shift applied after elimination or a compensated drop all give other
+    numbers."""
+    A = np.array([[2.0, 2.0, 4.0], [2.0, 5.0, 0.0], [4.0, 0.0, 4.0]])
+    rp, ci, v = _csr_from_dense(A)
+    o = orc.OracleIC(3, rp, ci, None, 0)
+    lptr, lcol, _ = o.pattern()
+    assert list(lptr) == [0, 1, 3, 5] and list(lcol) == [0, 0, 1, 0, 2]
+    assert o.numeric(v, 1.0) == 0
+    assert list(o.values()) == [2.0, 1.0, 3.0, 2.0, 2.0]
+    assert o.numeric(v, 0.0) == orc.ERR_BREAKDOWN and o.breakdown_row == 2
+    # with the fill kept (k = 1): L_21 = (0 - L_20 L_10) / L_11 = -2/3 and
+    # L_22 = sqrt(8 - 4 - 4/9) = sqrt(32)/3
+    o1 = orc.OracleIC(3, rp, ci, None, 1)
+    assert o1.numeric(v, 1.0) == 0
+    assert np.allclose(o1.values(), [2.0, 1.0, 3.0, 2.0, -2.0 / 3.0, np.sqrt(32.0) / 3.0], rtol=1e-15, atol=0)
+
+
+def test_shifted_diagonal_matrix_closed_form(orc):
+    d = np.array([1.0, 2.0, 0.5, 7.0, 3.25])
+    n = len(d)
+    rp = np.arange(n + 1, dtype=np.int64)
+    o = orc.OracleIC(n, rp, np.arange(n, dtype=np.int32), None, 2)
+    for alpha in (0.0, 1e-3, 0.3, 5.0):
+        assert o.numeric(d, alpha) == 0
+        assert np.allclose(o.values(), np.sqrt((1.0 + alpha) * d), rtol=2e-16, atol=0), alpha
+
+
+@pytest.mark.parametrize("alpha,k", [(1e-3, 0), (0.05, 1), (0.4, 2)])
+def test_shift_equals_factor_of_preshifted_matrix(orc, alpha, k):
+    """Shifting inside the factorization gives the factor of the matrix whose diagonal
+    was scaled beforehand, under a nested-dissection order (the shift lands on B_ii =
+    A_perm(i),perm(i), whichever row that is in A's order)."""
+    p = synth.laplace3d_27pt(9)
+    perm, _ = orc.nd_grid(9, 9, 9, 1, 100)
+    diag = np.zeros(len(p.vals), dtype=bool)
+    for i in range(p.n):
+        s, e = p.rowptr[i], p.rowptr[i + 1]
+        diag[s:e] = p.colind[s:e] == i
+    pre = p.vals.copy()
+    pre[diag] = pre[diag] + alpha * pre[diag]
+    o = orc.OracleIC.from_problem(p, perm, k)
+    assert o.numeric(p.vals, alpha) == 0
+    shifted = o.values()
+    assert o.numeric(pre, 0.0) == 0
+    assert np.array_equal(shifted, o.values())
+    assert o.numeric(p.vals, 0.0) == 0
+    assert not np.array_equal(shifted, o.values())
+
+
+# ------------------------------------------------ a hand-derived network
+
+
+def read_mlp_golden():
+    g = {"x": []}
+    for ln in open(os.path.join(GOLD, "mlp_forward_h2.txt")):
+        ln = ln.split("#")[0].split()
+        if not ln:
+            continue
+        if ln[0] == "x":
+            g["x"].append([float(t) for t in ln[1:]])
+        else:
+            g[ln[0]] = [float(t) for t in ln[1:]]
+    H = int(g["hidden"][0])
+    theta = np.concatenate([g["W1"], g["b1"], g["W2"], g["b2"], g["w3"], g["b3"]])
+    return H, theta, np.array(g["mean"]), np.array(g["std"]), np.array(g["x"]), np.array(g["y"])
+
+
+def pad_network(theta, hidden, to):
+    """The same function with `to` hidden units per layer: the extra units have zero
+    weights and biases, so they output ReLU(0) = 0 and feed nothing."""
+    W1, b1, W2, b2, w3, b3 = S.unpack(theta, hidden)
+    P1 = np.zeros((S.NFEAT, to)); P1[:, :hidden] = W1
+    P2 = np.zeros((to, to)); P2[:hidden, :hidden] = W2
+    pad = lambda v: np.concatenate([v, np.zeros(to - hidden)])
+    return np.concatenate([P1.ravel(), pad(b1), P2.ravel(), pad(b2), pad(w3), [b3]])
+
+
+def test_mlp_forward_hand_derived():
+    H, theta, mean, std, X, y = read_mlp_golden()
+    assert len(theta) == S.n_params(H)
+    out, (Z, a1, h1, a2, h2) = S.forward(theta, H, mean, std, X)
+    assert np.array_equal(out, y)
+    # every ReLU unit of both layers is inactive for at least one input
+    assert np.all((a1 <= 0).any(axis=0)) and np.all((a2 <= 0).any(axis=0))
+    padded = pad_network(theta, H, 32)
+    assert np.array_equal(S.forward(padded, 32, mean, std, X)[0], y)
