@@ -66,8 +66,9 @@ def parse():
     ap.add_argument("--numeric-only", action="store_true",
                     help="time only the numeric factorization (for profiling runs)")
     ap.add_argument("--no-f32", action="store_true", help="skip the mixed-precision arm")
-    ap.add_argument("--solve-mode", type=int, default=0, choices=[0, 1],
-                    help="triangular solves: 0 block-DAG, 1 row-level")
+    ap.add_argument("--solve-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="triangular solves: 0 block-DAG, 1 row-level, 2 block-row")
+    ap.add_argument("--solve-lanes", type=int, default=0, help="lanes per row of the solves (0: default)")
     ap.add_argument("--shift", action="store_true",
                     help="learned-shift workload instead: Q1 elasticity, FP32 + learned shift vs plain FP64")
     ap.add_argument("--ne", type=int, default=48, help="elements per side of the --shift workload")
@@ -87,9 +88,9 @@ def parse():
 
 def workload_name(a):
     leaf = "" if a.leaf_rows == a.block_rows else f" (ND leaves <= {a.leaf_rows} rows)"
+    solves = {0: "block-DAG", 1: "row-level", 2: "block-row"}[a.solve_mode]
     return (f"27-point Laplacian {a.side}^3 (n={a.side ** 3}), geometric ND{leaf}, 2D blocks <= "
-            f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}, "
-            f"{'block-DAG' if a.solve_mode == 0 else 'row-level'} triangular solves")
+            f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}, {solves} triangular solves")
 
 
 class ClockSampler:
@@ -452,7 +453,7 @@ def main():
     prob = synth.laplace3d_27pt(a.side)
     perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.leaf_rows)
     h = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
-                        warps_per_cta=a.warps, solve_mode=a.solve_mode)
+                        warps_per_cta=a.warps, solve_mode=a.solve_mode, solve_lanes=a.solve_lanes)
     st = ick.ic_stats(h)
     ick.ic_set_timing(h, True)
     stream = torch.cuda.current_stream()
@@ -547,7 +548,8 @@ def main():
     roof_numeric["frac"] = roof_numeric["achieved"] / roof_numeric["peak"]
     calls = max(1, tim["apply_calls"])
     roofs = {"numeric": (mean_fact, roof_numeric)}
-    names = ("forward_dag", "backward_dag") if a.solve_mode == 0 else ("forward_solve_v", "backward_solve_v")
+    names = {0: ("forward_dag", "backward_dag"), 1: ("forward_solve_v", "backward_solve_v"),
+             2: ("forward_rows", "backward_rows")}[a.solve_mode]
     for name, key in zip(names, ("fwd_ms", "bwd_ms")):
         per = tim[key] / calls
         r = {"kernel": name, "bound": "hbm",
@@ -611,7 +613,8 @@ def main():
     h32 = None
     if not a.numeric_only and not a.no_f32:
         h32 = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
-                              warps_per_cta=a.warps, dtype=ick.IC_F32, solve_mode=a.solve_mode)
+                              warps_per_cta=a.warps, dtype=ick.IC_F32, solve_mode=a.solve_mode,
+                              solve_lanes=a.solve_lanes)
         ick.ic_set_timing(h32, True)
         x32 = torch.empty_like(x)
 
