@@ -45,9 +45,11 @@ FP64_NOMINAL_GFLOPS = 1250.0  # GB300's nominal FP64 rate, used only if the prob
 # launch each) of the 48^3 and 64^3 problems gave 14.95 / 14.83 (forward) and 15.51 /
 # 15.18 (backward) bytes per entry; the 64^3 figures are scaled to the factor at hand
 SOLVE_TRAFFIC_PER_ENTRY = {(2, "forward_dag"): 14.83, (2, "backward_dag"): 15.18}
-# DRAM bytes (read + write) per factor entry of one numeric factorization (scatter +
-# task kernel) of the 27-point IC(k) problem, by k; filled from ncu captures
-NUMERIC_TRAFFIC_PER_ENTRY = {}
+# DRAM bytes (read + write) per factor entry of one launch of the numeric task kernel
+# of the 27-point IC(k) problem, by k: ncu captures of the 48^3, 64^3 and 80^3
+# problems gave 50.7, 59.5 and 56.6 bytes per entry; the 80^3 figure is scaled to the
+# factor at hand
+NUMERIC_TRAFFIC_PER_ENTRY = {2: 56.6}
 
 
 def parse():

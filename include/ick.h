@@ -300,9 +300,12 @@ int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t
  * a holds a source of a row of block row b".  ptr (nranges + 1) and ord (*nord): the
  * rows of each block row in the order its CTA solves them, ascending level in the
  * row dependence DAG (ic_stats solve_depth), each level's run padded with -1 to a
- * multiple of 8.  Any pointer may be NULL.  Errors: IC_ERR_ARG. */
+ * multiple of 8.  need (*nord): per position, the number of the block row's rows in
+ * lower levels; the row there runs once that many rows of its block row are complete
+ * (its sources in other block rows are awaited value by value).  Any pointer may be
+ * NULL.  Errors: IC_ERR_ARG. */
 int ic_get_solve_rows(const ic_handle* h, int backward, int32_t* claim, int32_t* ptr, int32_t* ord,
-                      int64_t* nord);
+                      int32_t* need, int64_t* nord);
 
 /* Layout of the split Chol/Trsm tasks (ic_stats nsplit), for inspection.  A split
  * task's finished rows are published in a shadow array of *nshadow values: the target

@@ -283,6 +283,8 @@ int upload_plan(ic_handle* h) {
     if ((st = h->upload(&S.rb_ord, P.rb_ord))) return st;
     if ((st = h->upload(&S.rf_claim, P.rf_claim))) return st;
     if ((st = h->upload(&S.rb_claim, P.rb_claim))) return st;
+    if ((st = h->upload(&S.rf_need, P.rf_need))) return st;
+    if ((st = h->upload(&S.rb_need, P.rb_need))) return st;
     S.uvt = S.xf_val = S.xb_val = nullptr;
     if (S.solve_mode != 1) {
         const size_t cnt[3] = {size_t(P.nnz_u - P.n) + 4, P.xf.j.size() + 4, P.xb.j.size() + 4};
@@ -1076,16 +1078,18 @@ int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t
 }
 
 int ic_get_solve_rows(const ic_handle* h, int backward, int32_t* claim, int32_t* ptr, int32_t* ord,
-                      int64_t* nord) {
+                      int32_t* need, int64_t* nord) {
     if (!h) return fail(IC_ERR_ARG, "NULL handle");
     const HostPlan& P = h->hp;
     const std::vector<int32_t>& cl = backward ? P.rb_claim : P.rf_claim;
     const std::vector<int32_t>& pt = backward ? P.rb_ptr : P.rf_ptr;
     const std::vector<int32_t>& od = backward ? P.rb_ord : P.rf_ord;
+    const std::vector<int32_t>& nd = backward ? P.rb_need : P.rf_need;
     if (nord) *nord = int64_t(od.size());
     if (claim && !cl.empty()) std::memcpy(claim, cl.data(), cl.size() * sizeof(int32_t));
     if (ptr && !pt.empty()) std::memcpy(ptr, pt.data(), pt.size() * sizeof(int32_t));
     if (ord && !od.empty()) std::memcpy(ord, od.data(), od.size() * sizeof(int32_t));
+    if (need && !nd.empty()) std::memcpy(need, nd.data(), nd.size() * sizeof(int32_t));
     return IC_OK;
 }
 

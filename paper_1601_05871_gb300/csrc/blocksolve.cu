@@ -393,16 +393,17 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
 // One CTA solves a whole range (block row) and then claims the next range of the
 // claim order.  Its rows run in level order (the level of a row in the dependence DAG
 // of the whole solve), R = 32 / G rows of one level per warp group, groups spread over
-// the warps round-robin.  The results are written twice: into shared memory, where
-// the range's own later rows read them, and into the global result vector, where
-// other ranges read them.  Both copies start as the all-ones bit pattern (a NaN that
-// arithmetic never produces, kUnset), and a value that is no longer kUnset is final:
-// a reader spins (bounded) on each of its source values, with no flag, counter or
-// fence between the rows.  A row's sources have lower levels, so they come earlier in
-// its own range's order or lie in ranges claimed before its range; the waits cannot
-// cycle.  Each row sums its entries in a fixed order (the other ranges' entries, then
-// its range's entries sorted by their source's level), so the result does not depend
-// on timing.
+// the warps round-robin.  A row's sources in other ranges are read from the global
+// result vector, which starts as the all-ones bit pattern (a NaN that arithmetic never
+// produces, kUnset): a value that is no longer kUnset is final, and the reader spins
+// (bounded) on it, with no flag, counter or fence between the ranges.  A row's sources
+// inside the range are read from shared memory once the range's count of completed
+// rows reaches the rows of the row's lower levels (one shared word, polled by one lane
+// of each waiting warp).  A row's sources have lower levels, so they come earlier in
+// its range's order or lie in ranges claimed before its range; the waits cannot cycle.
+// Each row sums its entries in a fixed order (the other ranges' entries, then its
+// range's entries sorted by their source's level), so the result does not depend on
+// timing.
 
 template <typename T>
 __device__ __forceinline__ bool unset(T v);
@@ -410,13 +411,6 @@ template <>
 __device__ __forceinline__ bool unset<double>(double v) { return __double_as_longlong(v) == -1LL; }
 template <>
 __device__ __forceinline__ bool unset<float>(float v) { return __float_as_int(v) == -1; }
-
-template <typename T>
-__device__ __forceinline__ T unset_value();
-template <>
-__device__ __forceinline__ double unset_value<double>() { return __longlong_as_double(-1LL); }
-template <>
-__device__ __forceinline__ float unset_value<float>() { return __int_as_float(-1); }
 
 // A result that happens to carry the reserved pattern is published as another NaN.
 template <typename T>
@@ -441,53 +435,67 @@ __device__ __forceinline__ T await_set(const T* p, T v, int* abort_word, unsigne
             ok = false;
             return T(0);
         }
+        __nanosleep(32);
         v = ld_vol(p);
     }
     return v;
 }
 
-// Held internal entries per lane (loaded into registers before the row's waits).
+constexpr int kExtBatch = 4;  // external entries per lane loaded together
+
+// Internal entries per lane held in registers (loaded before the row's wait): 32 per
+// row, fewer than the block-DAG solves hold, so that two CTAs of 16 warps fit on an SM
+// beside the registers of the external sums.
 template <int G>
 struct RowHeld {
     static constexpr int M = 32 / G;
 };
-constexpr int kExtBatch = 4;  // external entries per lane loaded together
 
 // The rows of range k.  Forward (BW false): y_i = (r_perm(i) - sum_p U_pi y_p) / U_ii;
 // backward: z_i = (y_i - sum_c U_ic z_c) / U_ii, also stored to z at perm(i).
 template <int G, typename T, bool BW>
 __device__ void solve_range(const SolvePlan& S, const T* __restrict__ ext_val, const T* __restrict__ int_val,
                             const T* __restrict__ rd_all, const double* __restrict__ r, const T* __restrict__ y,
-                            T* out, double* __restrict__ z, int k, T* sh, unsigned long long deadline) {
+                            T* out, double* __restrict__ z, int k, T* sh, int* done, unsigned long long deadline) {
     constexpr int R = 32 / G, M = RowHeld<G>::M;
     const int lane = threadIdx.x & 31, sl = lane % G;
     const int* ord = BW ? S.rb_ord : S.rf_ord;
+    const int* need_a = BW ? S.rb_need : S.rf_need;
     const int* xptr = BW ? S.xb_ptr : S.xf_ptr;
     const int* xj = BW ? S.xb_j : S.xf_j;
     int* abort_word = S.counter + 2;
     const int base = __ldg((BW ? S.rb_ptr : S.rf_ptr) + k);
     const int len = __ldg((BW ? S.rb_ptr : S.rf_ptr) + k + 1) - base;
-    const int s = __ldg(S.ranges + k), m = __ldg(S.ranges + k + 1) - s;
-    for (int q = threadIdx.x; q < m; q += blockDim.x) sh[q] = unset_value<T>();
+    const int s = __ldg(S.ranges + k);
+    if (threadIdx.x == 0) *done = 0;
     __syncthreads();
     const int nw = blockDim.x >> 5;
     bool ok = true;
     for (int t0 = (threadIdx.x >> 5) * R; t0 < len; t0 += nw * R) {
         const int i = __ldg(ord + base + t0 + lane / G);
+        const int need = __ldg(need_a + base + t0);
         T acc0 = T(0), acc1 = T(0), t = T(0), rd = T(0);
-        int a = 0, c = 0;
-        long long ea = 0, eb = 0;
+        int a = 0, c = 0, cnt = 0;
         int j[M];
         T u[M];
+#pragma unroll
+        for (int x = 0; x < M; ++x) {
+            j[x] = 0;
+            u[x] = T(0);
+        }
         if (i >= 0) {
             a = __ldg(xptr + i);
             c = __ldg(xptr + i + 1);
 #pragma unroll
             for (int x = 0; x < M; ++x) {
                 const int q = a + sl + x * G;
-                j[x] = q < c ? __ldg(xj + q) : 0;
-                u[x] = q < c ? __ldg(int_val + q) : T(0);
+                if (q < c) {
+                    j[x] = __ldg(xj + q);
+                    u[x] = __ldg(int_val + q);
+                    cnt = x + 1;
+                }
             }
+            long long ea, eb;
             if (BW) {
                 ea = __ldg(S.urp + i) + 1 + __ldg(S.sb_nint + i);
                 eb = __ldg(S.urp + i + 1);
@@ -524,34 +532,38 @@ __device__ void solve_range(const SolvePlan& S, const T* __restrict__ ext_val, c
                     }
                 }
             }
-            // entries inside the range, lowest source level first: shared memory
-            T v[M];
+        }
+        const unsigned rows = __ballot_sync(0xffffffffu, sl == 0 && i >= 0);
+        const int most = __reduce_max_sync(0xffffffffu, cnt);
+        // entries inside the range: shared memory, once the lower levels are complete
+        int w_ok = 1;
+        if (lane == 0) w_ok = await_count(done, need, abort_word, deadline);
+        ok = ok && __shfl_sync(0xffffffffu, w_ok, 0);
+        if (ok) {
 #pragma unroll
-            for (int x = 0; x < M; ++x) v[x] = a + sl + x * G < c ? ld_vol(sh + j[x]) : T(0);
-#pragma unroll
-            for (int x = 0; x < M; ++x) {
-                if (a + sl + x * G < c && ok) {
-                    v[x] = await_set(sh + j[x], v[x], abort_word, deadline, ok);
-                    if (x & 1) acc1 = fma(u[x], v[x], acc1);
-                    else acc0 = fma(u[x], v[x], acc0);
-                }
+            for (int x = 0; x < M; x += 2) {
+                if (x >= most) break;
+                if (x < cnt) acc0 = fma(u[x], sh[j[x]], acc0);
+                if (x + 1 < cnt) acc1 = fma(u[x + 1], sh[j[x + 1]], acc1);
             }
-            for (int q = a + sl + M * G; q < c && ok; q += G) {
-                const int jj = __ldg(xj + q);
-                const T vv = await_set(sh + jj, ld_vol(sh + jj), abort_word, deadline, ok);
-                acc0 = fma(__ldg(int_val + q), vv, acc0);
-            }
+            for (int q = a + sl + M * G; q < c; q += G) acc0 = fma(__ldg(int_val + q), sh[__ldg(xj + q)], acc0);
         }
         const T acc = sum_group<G>(acc0 + acc1);
+        T val = T(0);
         if (sl == 0 && i >= 0 && ok) {
-            const T val = fma(-rd, acc, t * rd);
-            st_vol(sh + (i - s), val);
+            val = fma(-rd, acc, t * rd);
+            sh[i - s] = val;
+        }
+        // the count is raised before the global stores, so its fence waits only for the
+        // shared-memory results
+        complete_rows(done, ok ? rows : 0u);
+        if (sl == 0 && i >= 0 && ok) {
             st_vol(out + i, publishable_value(val));
             if (BW) z[__ldg(S.perm + i)] = double(val);
         }
         if (__any_sync(0xffffffffu, !ok)) break;
     }
-    __syncthreads();  // sh is reused by the next range
+    __syncthreads();  // sh and the count are reused by the next range
 }
 
 template <int G, typename T>
@@ -560,7 +572,7 @@ forward_rows(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_al
              T* y, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_claim;
+    __shared__ int s_claim, s_done;
     const unsigned long long deadline = gclock() + timeout_ns;
     for (;;) {
         if (threadIdx.x == 0) s_claim = aborted(S.counter + 2) ? S.nranges : atomicAdd(S.counter + 0, 1);
@@ -570,7 +582,7 @@ forward_rows(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_al
         const int k = __ldg(S.rf_claim + c);  // -1: left out (host-side fault injection)
         if (k >= 0)
             solve_range<G, T, false>(S, uvt, static_cast<const T*>(S.xf_val), rd_all, r, nullptr, y, nullptr, k,
-                                     sh, deadline);
+                                     sh, &s_done, deadline);
         else
             __syncthreads();
     }
@@ -582,7 +594,7 @@ backward_rows(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_al
               double* __restrict__ z, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_claim;
+    __shared__ int s_claim, s_done;
     const unsigned long long deadline = gclock() + timeout_ns;
     for (;;) {
         if (threadIdx.x == 0) s_claim = aborted(S.counter + 2) ? S.nranges : atomicAdd(S.counter + 1, 1);
@@ -592,7 +604,7 @@ backward_rows(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_al
         const int k = __ldg(S.rb_claim + c);
         if (k >= 0)
             solve_range<G, T, true>(S, uv, static_cast<const T*>(S.xb_val), rd_all, nullptr, y, zv, z, k, sh,
-                                    deadline);
+                                    &s_done, deadline);
         else
             __syncthreads();
     }

@@ -281,7 +281,9 @@ void build_solve_dag(HostPlan& P, int nthr) {
 // row's sources -- inside the range or in other ranges -- have lower levels.  A source
 // inside the range is read from shared memory, one in another range from global
 // memory, and each value is its own completion flag, so there is no coarser
-// synchronisation than the rows themselves.  The CTAs claim the ranges in a
+// synchronisation than the rows themselves across ranges; inside a range a row waits,
+// as in the block-DAG solves, for the range's count of completed rows to reach the
+// rows of its lower levels (one shared word polled by one lane per waiting warp).  The CTAs claim the ranges in a
 // topological order of the range graph (range r after every range holding a source of
 // one of its rows), preferring the range whose rows can start first; a CTA waits only
 // for rows of ranges claimed before its own, which are running or finished, so the
@@ -289,22 +291,32 @@ void build_solve_dag(HostPlan& P, int nthr) {
 namespace {
 
 // Rows of each range sorted by lev (ties: ascending row, or descending for the
-// backward solve), each level's run padded with -1 to a multiple of kClaimPad.
+// backward solve), each level's run padded with -1 to a multiple of kClaimPad.  need
+// receives, per position, the number of the range's rows in lower levels: the row
+// there may run once that many rows of the range are complete.
 void level_order(const HostPlan& P, const std::vector<int32_t>& lev, bool descending,
-                 std::vector<int32_t>& ptr, std::vector<int32_t>& ord) {
+                 std::vector<int32_t>& ptr, std::vector<int32_t>& ord, std::vector<int32_t>& need) {
     const int32_t nb = int32_t(P.ranges.size()) - 1;
     ptr.assign(nb + 1, 0);
     ord.clear();
+    need.clear();
     std::vector<int32_t> rows;
     for (int32_t k = 0; k < nb; ++k) {
         const int32_t s = P.ranges[k], e = P.ranges[k + 1];
         rows.resize(e - s);
         for (int32_t q = 0; q < e - s; ++q) rows[q] = descending ? e - 1 - q : s + q;
         std::stable_sort(rows.begin(), rows.end(), [&](int32_t a, int32_t b) { return lev[a] < lev[b]; });
+        int32_t before = 0;
         for (size_t q = 0; q < rows.size(); ++q) {
             ord.push_back(rows[q]);
-            if (q + 1 == rows.size() || lev[rows[q + 1]] != lev[rows[q]])
-                while (ord.size() % kClaimPad) ord.push_back(-1);
+            need.push_back(before);
+            if (q + 1 == rows.size() || lev[rows[q + 1]] != lev[rows[q]]) {
+                while (ord.size() % kClaimPad) {
+                    ord.push_back(-1);
+                    need.push_back(before);
+                }
+                before = int32_t(q) + 1;
+            }
         }
         ptr[k + 1] = int32_t(ord.size());
     }
@@ -375,8 +387,8 @@ void sort_by_source_level(const HostPlan& P, const std::vector<int32_t>& lev, So
 }  // namespace
 
 void build_solve_rows(HostPlan& P) {
-    level_order(P, P.gf, false, P.rf_ptr, P.rf_ord);
-    level_order(P, P.gb, true, P.rb_ptr, P.rb_ord);
+    level_order(P, P.gf, false, P.rf_ptr, P.rf_ord, P.rf_need);
+    level_order(P, P.gb, true, P.rb_ptr, P.rb_ord, P.rb_need);
     // forward: the external sources of row i are the column-list entries before sf_split
     claim_order(P, P.gf, false,
                 [&](int32_t i, auto&& use) {

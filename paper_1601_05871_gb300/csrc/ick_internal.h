@@ -84,6 +84,7 @@ struct HostPlan {
     // level, each level's run padded with -1 to a multiple of kClaimPad (offsets per
     // range in *_ptr), and the order in which CTAs claim the ranges
     std::vector<int32_t> rf_ptr, rf_ord, rb_ptr, rb_ord, rf_claim, rb_claim;
+    std::vector<int32_t> rf_need, rb_need;  // per position: the range's rows of lower levels
     // block-DAG solves (host_solve.cpp): per row the start of the internal entries
     // (forward: absolute column-list index; backward: count after the diagonal), per
     // range the padded local orders, and each direction's tasks
@@ -223,6 +224,8 @@ struct SolvePlan {
     const int* rb_ord;
     const int* rf_claim;
     const int* rb_claim;
+    const int* rf_need;
+    const int* rb_need;
     unsigned long long* trace;  // NULL, or 4 words per task: forward tasks, then backward
 };
 

@@ -65,6 +65,18 @@ def _check(h, backward):
             g = seg[g0:g0 + PAD]
             g = g[g >= 0]
             assert len(set(lev[g])) <= 1, (k, g0)
+        # need: the range's rows of lower levels, so every internal source of a row is
+        # among the rows counted before it may run
+        need = d["need"][ptr[k]:ptr[k + 1]]
+        real_before = np.cumsum(seg >= 0) - (seg >= 0)
+        for q, r in enumerate(seg):
+            if r < 0:
+                continue
+            assert need[q] == np.sum(lev[rows] < lev[r])
+            src = _sources(urp, ucol, cptr, cp, r, backward)
+            inside = src[blk[src] == k]
+            pos = {int(x): qq for qq, x in enumerate(seg) if x >= 0}
+            assert all(real_before[pos[int(x)]] < need[q] for x in inside), (k, r)
     return d
 
 
