@@ -324,8 +324,8 @@ int upload_plan(ic_handle* h) {
     if ((st = h->alloc(&S.y, 2 * size_t(P.n)))) return st;  // forward and backward results
     if ((st = h->alloc(&S.flag, size_t(P.n)))) return st;
     CK(cudaMemset(S.flag, 0, size_t(P.n) * sizeof(int)));
-    if ((st = h->alloc(&S.counter, 4))) return st;
-    CK(cudaMemset(S.counter, 0, 4 * sizeof(int)));
+    if ((st = h->alloc(&S.counter, 8))) return st;
+    CK(cudaMemset(S.counter, 0, 8 * sizeof(int)));
     if ((st = h->alloc(&h->r, size_t(P.n)))) return st;
     if ((st = h->alloc(&h->z, size_t(P.n)))) return st;
     if ((st = h->alloc(&h->p, size_t(P.n)))) return st;
@@ -663,13 +663,17 @@ int ic_apply_status(ic_handle* h, void* stream) {
     if (h->opts.host_only || h->hp.n == 0) return IC_OK;
     DeviceGuard g(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int rec = 0;
-    CK(cudaMemcpyAsync(&rec, h->sp.counter + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int rec[4] = {0, 0, 0, 0};  // timeout record, then where a block-row wait gave up
+    CK(cudaMemcpyAsync(rec, h->sp.counter + 3, sizeof(rec), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (!rec) return IC_OK;
-    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s));
+    if (!rec[0]) return IC_OK;
+    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(rec), s));
     CK(cudaStreamSynchronize(s));
-    return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
+    std::string where;
+    if (rec[1])
+        where = std::string(" (") + (rec[1] == 1 ? "a source in another block row" : "the block row's count") +
+                ", block row " + std::to_string(rec[2]) + ", row " + std::to_string(rec[3]) + ")";
+    return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out" + where);
 }
 
 int ic_apply_static(ic_handle* h, const void* r, void* z, void* stream) {
@@ -726,7 +730,7 @@ int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, doub
     const int parts = pcg_parts(n);
     int st = 0;
     int64_t& nl = h->tm.launches;
-    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s));  // solve timeout record
+    CK(cudaMemsetAsync(h->sp.counter + 3, 0, 4 * sizeof(int), s));  // solve timeout record
     ++nl;
     CK(pcg_init(n, b, x, h->r, s));
     ++nl;
@@ -776,7 +780,7 @@ int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, doub
         int ctr[4];
         CK(cudaMemcpy(ctr, h->sp.counter, sizeof(ctr), cudaMemcpyDeviceToHost));
         if (ctr[3]) {  // reported here, so the record is cleared
-            CK(cudaMemset(h->sp.counter + 3, 0, sizeof(int)));
+            CK(cudaMemset(h->sp.counter + 3, 0, 4 * sizeof(int)));
             return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
         }
     }
@@ -830,7 +834,7 @@ int pcg_solve_batch(ic_handle* h, const void* A_vals, const double* b, double* x
     const double* av = static_cast<const double*>(A_vals);
     BatchScalars& B = h->bs;
     const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
-    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s));  // solve timeout record
+    CK(cudaMemsetAsync(h->sp.counter + 3, 0, 4 * sizeof(int), s));  // solve timeout record
     CK(pcg_init(n, b, x, h->r, s));
     CK(batch_dot(h->d_row_off, count, b, b, B.tmp, s));
     CK(batch_scalars(B, count, 4, tol, s));
@@ -877,7 +881,7 @@ int pcg_solve_batch(ic_handle* h, const void* A_vals, const double* b, double* x
     if (iters) std::memcpy(iters, its.data(), count * sizeof(int));
     if (relres) std::memcpy(relres, rel.data(), count * sizeof(double));
     if (abort_word) {
-        CK(cudaMemset(h->sp.counter + 3, 0, sizeof(int)));
+        CK(cudaMemset(h->sp.counter + 3, 0, 4 * sizeof(int)));
         return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
     }
     for (int s2 = 0; s2 < count; ++s2)

@@ -424,21 +424,53 @@ __device__ __forceinline__ T ld_vol(const T* p) { return *reinterpret_cast<const
 template <typename T>
 __device__ __forceinline__ void st_vol(T* p, T v) { *reinterpret_cast<volatile T*>(p) = v; }
 
+// Every wait of the block-row solves also gives up after kRowSpinCap polls, whatever
+// the clock says, and the first wait to give up records where: counter[4] = site (1:
+// a source in another range, 2: the range's completion count), counter[5] = range,
+// counter[6] = row.
+constexpr unsigned kRowSpinCap = 1u << 24;
+
+__device__ __forceinline__ void record_give_up(int* abort_word, int site, int k, int i) {
+    int* rec = abort_word + 2;  // counter[4..6]
+    if (atomicCAS(rec, 0, site) == 0) {
+        rec[1] = k;
+        rec[2] = i;
+    }
+    raise_abort(abort_word);
+}
+
 // v was loaded from p; while it is still kUnset, reload it (bounded).  ok turns false
-// on timeout or when another CTA has aborted the solve.
+// on timeout, at the poll cap, or when another CTA has aborted the solve.
 template <typename T>
-__device__ __forceinline__ T await_set(const T* p, T v, int* abort_word, unsigned long long deadline, bool& ok) {
+__device__ __forceinline__ T await_set(const T* p, T v, int* abort_word, unsigned long long deadline, bool& ok,
+                                       int k, int i) {
     unsigned spins = 0;
     while (unset(v)) {
-        if ((++spins & 127) == 0 && (aborted(abort_word) || gclock() > deadline)) {
-            raise_abort(abort_word);
+        if ((++spins & 127) == 0 &&
+            (aborted(abort_word) || gclock() > deadline || spins >= kRowSpinCap)) {
+            record_give_up(abort_word, 1, k, i);
             ok = false;
             return T(0);
         }
-        __nanosleep(32);
         v = ld_vol(p);
     }
     return v;
+}
+
+// Lane 0: wait until the range's count of completed rows reaches need (bounded).
+__device__ bool await_rows(const int* done, int need, int* abort_word, unsigned long long deadline, int k,
+                           int i) {
+    const volatile int* p = done;
+    unsigned spins = 0;
+    while (*p < need) {
+        if ((++spins & 255) == 0 &&
+            (aborted(abort_word) || gclock() > deadline || spins >= kRowSpinCap)) {
+            record_give_up(abort_word, 2, k, i);
+            return false;
+        }
+    }
+    __threadfence_block();
+    return true;
 }
 
 constexpr int kExtBatch = 4;  // external entries per lane loaded together
@@ -526,7 +558,7 @@ __device__ void solve_range(const SolvePlan& S, const T* __restrict__ ext_val, c
 #pragma unroll
                 for (int x = 0; x < kExtBatch; ++x) {
                     if (q0 + x * G < eb) {
-                        v[x] = await_set(out + src[x], v[x], abort_word, deadline, ok);
+                        v[x] = await_set(out + src[x], v[x], abort_word, deadline, ok, k, i);
                         if (x & 1) acc1 = fma(w[x], v[x], acc1);
                         else acc0 = fma(w[x], v[x], acc0);
                     }
@@ -537,7 +569,7 @@ __device__ void solve_range(const SolvePlan& S, const T* __restrict__ ext_val, c
         const int most = __reduce_max_sync(0xffffffffu, cnt);
         // entries inside the range: shared memory, once the lower levels are complete
         int w_ok = 1;
-        if (lane == 0) w_ok = await_count(done, need, abort_word, deadline);
+        if (lane == 0) w_ok = await_rows(done, need, abort_word, deadline, k, __ldg(ord + base + t0));
         ok = ok && __shfl_sync(0xffffffffu, w_ok, 0);
         if (ok) {
 #pragma unroll
@@ -555,13 +587,14 @@ __device__ void solve_range(const SolvePlan& S, const T* __restrict__ ext_val, c
             sh[i - s] = val;
         }
         // the count is raised before the global stores, so its fence waits only for the
-        // shared-memory results
-        complete_rows(done, ok ? rows : 0u);
-        if (sl == 0 && i >= 0 && ok) {
+        // shared-memory results; a warp with a failed wait counts none of its rows
+        const bool all_ok = __all_sync(0xffffffffu, ok);
+        complete_rows(done, all_ok ? rows : 0u);
+        if (sl == 0 && i >= 0 && all_ok) {
             st_vol(out + i, publishable_value(val));
             if (BW) z[__ldg(S.perm + i)] = double(val);
         }
-        if (__any_sync(0xffffffffu, !ok)) break;
+        if (!all_ok) break;
     }
     __syncthreads();  // sh and the count are reused by the next range
 }
