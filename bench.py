@@ -68,8 +68,8 @@ def parse():
     ap.add_argument("--numeric-only", action="store_true",
                     help="time only the numeric factorization (for profiling runs)")
     ap.add_argument("--no-f32", action="store_true", help="skip the mixed-precision arm")
-    ap.add_argument("--solve-mode", type=int, default=0, choices=[0, 1, 2],
-                    help="triangular solves: 0 block-DAG, 1 row-level, 2 block-row")
+    ap.add_argument("--solve-mode", type=int, default=0, choices=[0, 1],
+                    help="triangular solves: 0 block-DAG, 1 row-level")
     ap.add_argument("--solve-lanes", type=int, default=0, help="lanes per row of the solves (0: default)")
     ap.add_argument("--shift", action="store_true",
                     help="learned-shift workload instead: Q1 elasticity, FP32 + learned shift vs plain FP64")
@@ -90,7 +90,7 @@ def parse():
 
 def workload_name(a):
     leaf = "" if a.leaf_rows == a.block_rows else f" (ND leaves <= {a.leaf_rows} rows)"
-    solves = {0: "block-DAG", 1: "row-level", 2: "block-row"}[a.solve_mode]
+    solves = {0: "block-DAG", 1: "row-level"}[a.solve_mode]
     return (f"27-point Laplacian {a.side}^3 (n={a.side ** 3}), geometric ND{leaf}, 2D blocks <= "
             f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}, {solves} triangular solves")
 
@@ -550,8 +550,7 @@ def main():
     roof_numeric["frac"] = roof_numeric["achieved"] / roof_numeric["peak"]
     calls = max(1, tim["apply_calls"])
     roofs = {"numeric": (mean_fact, roof_numeric)}
-    names = {0: ("forward_dag", "backward_dag"), 1: ("forward_solve_v", "backward_solve_v"),
-             2: ("forward_rows", "backward_rows")}[a.solve_mode]
+    names = {0: ("forward_dag", "backward_dag"), 1: ("forward_solve_v", "backward_solve_v")}[a.solve_mode]
     for name, key in zip(names, ("fwd_ms", "bwd_ms")):
         per = tim[key] / calls
         r = {"kernel": name, "bound": "hbm",

@@ -77,14 +77,11 @@ typedef struct {
                           needed); such a handle serves the ic_get_* and ic_stats calls   */
     int solve_ctas_per_sm; /* [2 block-DAG, 3 row-level] CTAs per SM for the triangular-
                               solve kernels (capped by occupancy)                    */
-    int solve_lanes;   /* [8 block-DAG and block-row, 32 row-level] lanes per row in the
-                          ic_apply / pcg_solve solves: 4|8|16|32 (block-row: 4|8)         */
+    int solve_lanes;   /* [8 block-DAG, 32 row-level] lanes per row in the ic_apply /
+                          pcg_solve solves: 4|8|16|32                                 */
     int solve_mode;    /* [0] triangular solves of ic_apply / pcg_solve: 0 block-DAG (block
-                        * rows cut into parts of a few local levels, tasks for the parts'
-                        * external sums and local chains), 1 row-level (every row a unit,
-                        * claimed in dependence-level order), 2 block-row (one CTA solves a
-                        * whole block row, its rows in dependence-level order; every row
-                        * waits on its own source values only)                          */
+                        * rows as tasks, one CTA per block row's local chain), 1 row-level
+                        * (every row a unit, claimed in dependence-level order)           */
     int reserved[2];
 } ic_opts;
 
@@ -294,19 +291,6 @@ int ic_get_solve_tasks(const ic_handle* h, int backward, int64_t* ntasks, int32_
  * Errors: IC_ERR_ARG. */
 int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t* j, int32_t* pos);
 
-/* The block-row solves of ic_apply (solve_mode 2), for inspection and tests; every
- * handle has this plan.  backward = 0: L y = r; 1: L^T z = y.  claim (nranges): the
- * order in which CTAs take the block rows, a topological order of the graph "block row
- * a holds a source of a row of block row b".  ptr (nranges + 1) and ord (*nord): the
- * rows of each block row in the order its CTA solves them, ascending level in the
- * row dependence DAG (ic_stats solve_depth), each level's run padded with -1 to a
- * multiple of 8.  need (*nord): per position, the number of the block row's rows in
- * lower levels; the row there runs once that many rows of its block row are complete
- * (its sources in other block rows are awaited value by value).  Any pointer may be
- * NULL.  Errors: IC_ERR_ARG. */
-int ic_get_solve_rows(const ic_handle* h, int backward, int32_t* claim, int32_t* ptr, int32_t* ord,
-                      int32_t* need, int64_t* nord);
-
 /* Layout of the split Chol/Trsm tasks (ic_stats nsplit), for inspection.  A split
  * task's finished rows are published in a shadow array of *nshadow values: the target
  * segment [tb, te) of row r of such a task (ic_get_task_targets) sits at shadow
@@ -350,14 +334,11 @@ int ic_fma_peak(int dtype, double* gflops, void* stream);
  * bounded; nothing traps).  extra = 0 restores the plan.  Errors: IC_ERR_ARG, IC_ERR_CUDA. */
 int ic_test_hold_task(ic_handle* h, int64_t t, int extra);
 
-/* The same for the solves.  Block-DAG solves (solve_mode 0): adds `extra` to the
- * initial in-degree of task t (claim order of ic_get_solve_tasks) of the forward
- * (backward = 0) or backward (1) solve.  Block-row solves (solve_mode 2): with extra > 0
- * the block row at claim position t (ic_get_solve_rows) is left out, so its rows are
- * never solved.  Either way every later ic_apply gives up the waits on them after
- * opts.timeout_s and records a timeout (ic_apply_status, pcg_solve report it).  extra
- * = 0 restores the plan.  Errors: IC_ERR_ARG, IC_ERR_STATE (row-level solves),
- * IC_ERR_CUDA. */
+/* The same for the block-DAG solves (solve_mode 0): adds `extra` to the initial
+ * in-degree of task t (claim order of ic_get_solve_tasks) of the forward (backward = 0)
+ * or backward (1) solve, so with extra = 1 every later ic_apply gives up that task's
+ * wait after opts.timeout_s and records a timeout (ic_apply_status, pcg_solve report
+ * it).  extra = 0 restores the plan.  Errors: IC_ERR_ARG, IC_ERR_STATE, IC_ERR_CUDA. */
 int ic_test_hold_solve_task(ic_handle* h, int backward, int64_t t, int extra);
 
 /* Batched symbolic factorization: count independent SPD matrices (different sizes

@@ -135,8 +135,8 @@ ic_opts normalise(const ic_opts* o, int64_t count) {
     if (r.warps_per_cta == 0) r.warps_per_cta = count > 1 ? 16 : 32;
     if (r.rows_per_item == 0) r.rows_per_item = r.warps_per_cta;
     if (r.timeout_s == 0.0) r.timeout_s = 10.0;
-    if (r.solve_lanes == 0) r.solve_lanes = r.solve_mode == 1 ? 32 : 8;
-    if (r.solve_ctas_per_sm == 0) r.solve_ctas_per_sm = r.solve_mode == 1 ? 3 : 2;
+    if (r.solve_lanes == 0) r.solve_lanes = r.solve_mode == 0 ? 8 : 32;
+    if (r.solve_ctas_per_sm == 0) r.solve_ctas_per_sm = r.solve_mode == 0 ? 2 : 3;
     return r;
 }
 
@@ -277,16 +277,8 @@ int upload_plan(ic_handle* h) {
     if ((st = h->upload(&S.xb_pos, P.xb.pos))) return st;
     S.nxf = int(P.xf.j.size());
     S.nxb = int(P.xb.j.size());
-    if ((st = h->upload(&S.rf_ptr, P.rf_ptr))) return st;
-    if ((st = h->upload(&S.rf_ord, P.rf_ord))) return st;
-    if ((st = h->upload(&S.rb_ptr, P.rb_ptr))) return st;
-    if ((st = h->upload(&S.rb_ord, P.rb_ord))) return st;
-    if ((st = h->upload(&S.rf_claim, P.rf_claim))) return st;
-    if ((st = h->upload(&S.rb_claim, P.rb_claim))) return st;
-    if ((st = h->upload(&S.rf_need, P.rf_need))) return st;
-    if ((st = h->upload(&S.rb_need, P.rb_need))) return st;
     S.uvt = S.xf_val = S.xb_val = nullptr;
-    if (S.solve_mode != 1) {
+    if (S.solve_mode == 0) {
         const size_t cnt[3] = {size_t(P.nnz_u - P.n) + 4, P.xf.j.size() + 4, P.xb.j.size() + 4};
         void** dst[3] = {&S.uvt, &S.xf_val, &S.xb_val};
         for (int q = 0; q < 3; ++q) {
@@ -324,8 +316,8 @@ int upload_plan(ic_handle* h) {
     if ((st = h->alloc(&S.y, 2 * size_t(P.n)))) return st;  // forward and backward results
     if ((st = h->alloc(&S.flag, size_t(P.n)))) return st;
     CK(cudaMemset(S.flag, 0, size_t(P.n) * sizeof(int)));
-    if ((st = h->alloc(&S.counter, 8))) return st;
-    CK(cudaMemset(S.counter, 0, 8 * sizeof(int)));
+    if ((st = h->alloc(&S.counter, 4))) return st;
+    CK(cudaMemset(S.counter, 0, 4 * sizeof(int)));
     if ((st = h->alloc(&h->r, size_t(P.n)))) return st;
     if ((st = h->alloc(&h->z, size_t(P.n)))) return st;
     if ((st = h->alloc(&h->p, size_t(P.n)))) return st;
@@ -344,8 +336,6 @@ int upload_plan(ic_handle* h) {
     h->grid_numeric = sms * bpsm;
     if (S.solve_mode == 0)
         CK(dag_blocks_per_sm(S.lanes_per_row, S.dtype, P.max_range_rows, &bpsm));
-    else if (S.solve_mode == 2)
-        CK(rows_blocks_per_sm(S.lanes_per_row, S.dtype, P.max_range_rows, &bpsm));
     else
         CK(apply_blocks_per_sm(&bpsm));
     if (bpsm < 1) return fail(IC_ERR_CUDA, "solve kernels cannot be resident");
@@ -456,8 +446,7 @@ static int symbolic_impl(const ic_csr_pattern* A, int k, const int32_t* perm, co
         }
         if (h->opts.rows_per_item < 1 || h->opts.timeout_s < 0 ||
             (h->opts.solve_lanes != 4 && h->opts.solve_lanes != 8 && h->opts.solve_lanes != 16 &&
-             h->opts.solve_lanes != 32) || h->opts.solve_mode < 0 || h->opts.solve_mode > 2 ||
-            (h->opts.solve_mode == 2 && h->opts.solve_lanes != 4 && h->opts.solve_lanes != 8)) {
+             h->opts.solve_lanes != 32) || (h->opts.solve_mode != 0 && h->opts.solve_mode != 1)) {
             delete h;
             return fail(IC_ERR_ARG, "rows_per_item / timeout_s / solve_lanes / solve_mode out of range");
         }
@@ -663,17 +652,13 @@ int ic_apply_status(ic_handle* h, void* stream) {
     if (h->opts.host_only || h->hp.n == 0) return IC_OK;
     DeviceGuard g(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int rec[4] = {0, 0, 0, 0};  // timeout record, then where a block-row wait gave up
-    CK(cudaMemcpyAsync(rec, h->sp.counter + 3, sizeof(rec), cudaMemcpyDeviceToHost, s));
+    int rec = 0;
+    CK(cudaMemcpyAsync(&rec, h->sp.counter + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (!rec[0]) return IC_OK;
-    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(rec), s));
+    if (!rec) return IC_OK;
+    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s));
     CK(cudaStreamSynchronize(s));
-    std::string where;
-    if (rec[1])
-        where = std::string(" (") + (rec[1] == 1 ? "a source in another block row" : "the block row's count") +
-                ", block row " + std::to_string(rec[2]) + ", row " + std::to_string(rec[3]) + ")";
-    return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out" + where);
+    return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
 }
 
 int ic_apply_static(ic_handle* h, const void* r, void* z, void* stream) {
@@ -730,7 +715,7 @@ int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, doub
     const int parts = pcg_parts(n);
     int st = 0;
     int64_t& nl = h->tm.launches;
-    CK(cudaMemsetAsync(h->sp.counter + 3, 0, 4 * sizeof(int), s));  // solve timeout record
+    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s));  // solve timeout record
     ++nl;
     CK(pcg_init(n, b, x, h->r, s));
     ++nl;
@@ -780,7 +765,7 @@ int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, doub
         int ctr[4];
         CK(cudaMemcpy(ctr, h->sp.counter, sizeof(ctr), cudaMemcpyDeviceToHost));
         if (ctr[3]) {  // reported here, so the record is cleared
-            CK(cudaMemset(h->sp.counter + 3, 0, 4 * sizeof(int)));
+            CK(cudaMemset(h->sp.counter + 3, 0, sizeof(int)));
             return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
         }
     }
@@ -834,7 +819,7 @@ int pcg_solve_batch(ic_handle* h, const void* A_vals, const double* b, double* x
     const double* av = static_cast<const double*>(A_vals);
     BatchScalars& B = h->bs;
     const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
-    CK(cudaMemsetAsync(h->sp.counter + 3, 0, 4 * sizeof(int), s));  // solve timeout record
+    CK(cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s));  // solve timeout record
     CK(pcg_init(n, b, x, h->r, s));
     CK(batch_dot(h->d_row_off, count, b, b, B.tmp, s));
     CK(batch_scalars(B, count, 4, tol, s));
@@ -881,7 +866,7 @@ int pcg_solve_batch(ic_handle* h, const void* A_vals, const double* b, double* x
     if (iters) std::memcpy(iters, its.data(), count * sizeof(int));
     if (relres) std::memcpy(relres, rel.data(), count * sizeof(double));
     if (abort_word) {
-        CK(cudaMemset(h->sp.counter + 3, 0, 4 * sizeof(int)));
+        CK(cudaMemset(h->sp.counter + 3, 0, sizeof(int)));
         return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
     }
     for (int s2 = 0; s2 < count; ++s2)
@@ -1081,22 +1066,6 @@ int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t
     return IC_OK;
 }
 
-int ic_get_solve_rows(const ic_handle* h, int backward, int32_t* claim, int32_t* ptr, int32_t* ord,
-                      int32_t* need, int64_t* nord) {
-    if (!h) return fail(IC_ERR_ARG, "NULL handle");
-    const HostPlan& P = h->hp;
-    const std::vector<int32_t>& cl = backward ? P.rb_claim : P.rf_claim;
-    const std::vector<int32_t>& pt = backward ? P.rb_ptr : P.rf_ptr;
-    const std::vector<int32_t>& od = backward ? P.rb_ord : P.rf_ord;
-    const std::vector<int32_t>& nd = backward ? P.rb_need : P.rf_need;
-    if (nord) *nord = int64_t(od.size());
-    if (claim && !cl.empty()) std::memcpy(claim, cl.data(), cl.size() * sizeof(int32_t));
-    if (ptr && !pt.empty()) std::memcpy(ptr, pt.data(), pt.size() * sizeof(int32_t));
-    if (ord && !od.empty()) std::memcpy(ord, od.data(), od.size() * sizeof(int32_t));
-    if (need && !nd.empty()) std::memcpy(need, nd.data(), nd.size() * sizeof(int32_t));
-    return IC_OK;
-}
-
 int ic_get_split_layout(const ic_handle* h, int32_t* flag_off, int32_t* soff, int64_t* nsoff,
                         int64_t* nshadow) {
     if (!h) return fail(IC_ERR_ARG, "NULL handle");
@@ -1190,17 +1159,7 @@ int ic_fma_peak(int dtype, double* gflops, void* stream) {
 int ic_test_hold_solve_task(ic_handle* h, int backward, int64_t t, int extra) {
     if (!h) return fail(IC_ERR_ARG, "NULL handle");
     if (h->device < 0) return fail(IC_ERR_STATE, "host-only handle");
-    if (h->opts.solve_mode == 2) {
-        // block-row solves: the range at claim position t is left out of the claim order
-        const std::vector<int32_t>& cl = backward ? h->hp.rb_claim : h->hp.rf_claim;
-        if (t < 0 || t >= int64_t(cl.size()) || extra < 0) return fail(IC_ERR_ARG, "claim position out of range");
-        DeviceGuard g(h->device);
-        const int v = extra ? -1 : cl[t];
-        CK(cudaMemcpy(const_cast<int*>(backward ? h->sp.rb_claim : h->sp.rf_claim) + t, &v, sizeof(int),
-                      cudaMemcpyHostToDevice));
-        return IC_OK;
-    }
-    if (h->opts.solve_mode != 0) return fail(IC_ERR_STATE, "the handle's solves are row-level solves");
+    if (h->opts.solve_mode != 0) return fail(IC_ERR_STATE, "the handle's solves are not block-DAG solves");
     const SolveTasks& ST = backward ? h->hp.bs : h->hp.fs;
     if (t < 0 || t >= int64_t(ST.task.size()) || extra < 0) return fail(IC_ERR_ARG, "task out of range");
     DeviceGuard g(h->device);
@@ -1290,7 +1249,7 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
         int sms = 0, dev = 0, bpsm = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const int mode = h->sp.solve_mode;
+        const bool dag = h->sp.solve_mode == 0;
         double* r = nullptr;
         double* z = nullptr;
         CK(cudaMalloc(&r, 2 * size_t(h->hp.n > 0 ? h->hp.n : 1) * sizeof(double)));
@@ -1301,10 +1260,9 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        for (int lanes : {4, 8, 16, 32}) {
-            if ((mode == 2) != (lanes <= 8) || (mode == 1 && lanes == 8)) continue;
-            if (mode == 0) CK(dag_blocks_per_sm(lanes, h->sp.dtype, h->sp.max_range_rows, &bpsm));
-            else if (mode == 2) CK(rows_blocks_per_sm(lanes, h->sp.dtype, h->sp.max_range_rows, &bpsm));
+        for (int lanes : {8, 16, 32}) {
+            if (!dag && lanes == 8) continue;
+            if (dag) CK(dag_blocks_per_sm(lanes, h->sp.dtype, h->sp.max_range_rows, &bpsm));
             else CK(apply_blocks_per_sm(&bpsm));
             for (int cps : {2, 3, 4, 6}) {
                 if (cps > bpsm) continue;

@@ -388,293 +388,6 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
     }
 }
 
-// ------------------------------------------------------ block-row solves (mode 2)
-//
-// One CTA solves a whole range (block row) and then claims the next range of the
-// claim order.  Its rows run in level order (the level of a row in the dependence DAG
-// of the whole solve), R = 32 / G rows of one level per warp group, groups spread over
-// the warps round-robin.  A row's sources in other ranges are read from the global
-// result vector, which starts as the all-ones bit pattern (a NaN that arithmetic never
-// produces, kUnset): a value that is no longer kUnset is final, and the reader spins
-// (bounded) on it, with no flag, counter or fence between the ranges.  A row's sources
-// inside the range are read from shared memory once the range's count of completed
-// rows reaches the rows of the row's lower levels (one shared word, polled by one lane
-// of each waiting warp).  A row's sources have lower levels, so they come earlier in
-// its range's order or lie in ranges claimed before its range; the waits cannot cycle.
-// Each row sums its entries in a fixed order (the other ranges' entries, then its
-// range's entries sorted by their source's level), so the result does not depend on
-// timing.
-
-template <typename T>
-__device__ __forceinline__ bool unset(T v);
-template <>
-__device__ __forceinline__ bool unset<double>(double v) { return __double_as_longlong(v) == -1LL; }
-template <>
-__device__ __forceinline__ bool unset<float>(float v) { return __float_as_int(v) == -1; }
-
-// A result that happens to carry the reserved pattern is published as another NaN.
-template <typename T>
-__device__ __forceinline__ T publishable_value(T v) {
-    if (unset(v)) return sizeof(T) == 8 ? T(__longlong_as_double(0x7fffffffffffffffLL)) : T(__int_as_float(0x7fffffff));
-    return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T ld_vol(const T* p) { return *reinterpret_cast<const volatile T*>(p); }
-template <typename T>
-__device__ __forceinline__ void st_vol(T* p, T v) { *reinterpret_cast<volatile T*>(p) = v; }
-
-// Every wait of the block-row solves also gives up after kRowSpinCap polls, whatever
-// the clock says, and the first wait to give up records where: counter[4] = site (1:
-// a source in another range, 2: the range's completion count), counter[5] = range,
-// counter[6] = row.
-constexpr unsigned kRowSpinCap = 1u << 24;
-
-__device__ __forceinline__ void record_give_up(int* abort_word, int site, int k, int i) {
-    int* rec = abort_word + 2;  // counter[4..6]
-    if (atomicCAS(rec, 0, site) == 0) {
-        rec[1] = k;
-        rec[2] = i;
-    }
-    raise_abort(abort_word);
-}
-
-// v was loaded from p; while it is still kUnset, reload it (bounded).  ok turns false
-// on timeout, at the poll cap, or when another CTA has aborted the solve.
-template <typename T>
-__device__ __forceinline__ T await_set(const T* p, T v, int* abort_word, unsigned long long deadline, bool& ok,
-                                       int k, int i) {
-    unsigned spins = 0;
-    while (unset(v)) {
-        if ((++spins & 127) == 0 &&
-            (aborted(abort_word) || gclock() > deadline || spins >= kRowSpinCap)) {
-            record_give_up(abort_word, 1, k, i);
-            ok = false;
-            return T(0);
-        }
-        v = ld_vol(p);
-    }
-    return v;
-}
-
-// Lane 0: wait until the range's count of completed rows reaches need (bounded).
-__device__ bool await_rows(const int* done, int need, int* abort_word, unsigned long long deadline, int k,
-                           int i) {
-    const volatile int* p = done;
-    unsigned spins = 0;
-    while (*p < need) {
-        if ((++spins & 255) == 0 &&
-            (aborted(abort_word) || gclock() > deadline || spins >= kRowSpinCap)) {
-            record_give_up(abort_word, 2, k, i);
-            return false;
-        }
-    }
-    __threadfence_block();
-    return true;
-}
-
-constexpr int kExtBatch = 4;  // external entries per lane loaded together
-
-// Internal entries per lane held in registers (loaded before the row's wait): 32 per
-// row, fewer than the block-DAG solves hold, so that two CTAs of 16 warps fit on an SM
-// beside the registers of the external sums.
-template <int G>
-struct RowHeld {
-    static constexpr int M = 32 / G;
-};
-
-// The rows of range k.  Forward (BW false): y_i = (r_perm(i) - sum_p U_pi y_p) / U_ii;
-// backward: z_i = (y_i - sum_c U_ic z_c) / U_ii, also stored to z at perm(i).
-template <int G, typename T, bool BW>
-__device__ void solve_range(const SolvePlan& S, const T* __restrict__ ext_val, const T* __restrict__ int_val,
-                            const T* __restrict__ rd_all, const double* __restrict__ r, const T* __restrict__ y,
-                            T* out, double* __restrict__ z, int k, T* sh, int* done, unsigned long long deadline) {
-    constexpr int R = 32 / G, M = RowHeld<G>::M;
-    const int lane = threadIdx.x & 31, sl = lane % G;
-    const int* ord = BW ? S.rb_ord : S.rf_ord;
-    const int* need_a = BW ? S.rb_need : S.rf_need;
-    const int* xptr = BW ? S.xb_ptr : S.xf_ptr;
-    const int* xj = BW ? S.xb_j : S.xf_j;
-    int* abort_word = S.counter + 2;
-    const int base = __ldg((BW ? S.rb_ptr : S.rf_ptr) + k);
-    const int len = __ldg((BW ? S.rb_ptr : S.rf_ptr) + k + 1) - base;
-    const int s = __ldg(S.ranges + k);
-    if (threadIdx.x == 0) *done = 0;
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    bool ok = true;
-    for (int t0 = (threadIdx.x >> 5) * R; t0 < len; t0 += nw * R) {
-        const int i = __ldg(ord + base + t0 + lane / G);
-        const int need = __ldg(need_a + base + t0);
-        T acc0 = T(0), acc1 = T(0), t = T(0), rd = T(0);
-        int a = 0, c = 0, cnt = 0;
-        int j[M];
-        T u[M];
-#pragma unroll
-        for (int x = 0; x < M; ++x) {
-            j[x] = 0;
-            u[x] = T(0);
-        }
-        if (i >= 0) {
-            a = __ldg(xptr + i);
-            c = __ldg(xptr + i + 1);
-#pragma unroll
-            for (int x = 0; x < M; ++x) {
-                const int q = a + sl + x * G;
-                if (q < c) {
-                    j[x] = __ldg(xj + q);
-                    u[x] = __ldg(int_val + q);
-                    cnt = x + 1;
-                }
-            }
-            long long ea, eb;
-            if (BW) {
-                ea = __ldg(S.urp + i) + 1 + __ldg(S.sb_nint + i);
-                eb = __ldg(S.urp + i + 1);
-            } else {
-                ea = __ldg(S.cptr + i);
-                eb = __ldg(S.sf_split + i);
-            }
-            if (sl == 0) {
-                rd = __ldg(rd_all + i);
-                t = BW ? ldcg(y + i) : T(__ldg(r + __ldg(S.perm + i)));
-            }
-            // entries whose source lies in another range: their values are in global memory
-            for (long long q0 = ea + sl; q0 < eb && ok; q0 += G * kExtBatch) {
-                T w[kExtBatch], v[kExtBatch];
-                int src[kExtBatch];
-#pragma unroll
-                for (int x = 0; x < kExtBatch; ++x) {
-                    const long long q = q0 + x * G;
-                    src[x] = 0;
-                    w[x] = T(0);
-                    if (q < eb) {
-                        src[x] = BW ? __ldg(S.ucol + q) : __ldg(&S.csc[q].x);
-                        w[x] = __ldg(ext_val + q);
-                    }
-                }
-#pragma unroll
-                for (int x = 0; x < kExtBatch; ++x) v[x] = q0 + x * G < eb ? ld_vol(out + src[x]) : T(0);
-#pragma unroll
-                for (int x = 0; x < kExtBatch; ++x) {
-                    if (q0 + x * G < eb) {
-                        v[x] = await_set(out + src[x], v[x], abort_word, deadline, ok, k, i);
-                        if (x & 1) acc1 = fma(w[x], v[x], acc1);
-                        else acc0 = fma(w[x], v[x], acc0);
-                    }
-                }
-            }
-        }
-        const unsigned rows = __ballot_sync(0xffffffffu, sl == 0 && i >= 0);
-        const int most = __reduce_max_sync(0xffffffffu, cnt);
-        // entries inside the range: shared memory, once the lower levels are complete
-        int w_ok = 1;
-        if (lane == 0) w_ok = await_rows(done, need, abort_word, deadline, k, __ldg(ord + base + t0));
-        ok = ok && __shfl_sync(0xffffffffu, w_ok, 0);
-        if (ok) {
-#pragma unroll
-            for (int x = 0; x < M; x += 2) {
-                if (x >= most) break;
-                if (x < cnt) acc0 = fma(u[x], sh[j[x]], acc0);
-                if (x + 1 < cnt) acc1 = fma(u[x + 1], sh[j[x + 1]], acc1);
-            }
-            for (int q = a + sl + M * G; q < c; q += G) acc0 = fma(__ldg(int_val + q), sh[__ldg(xj + q)], acc0);
-        }
-        const T acc = sum_group<G>(acc0 + acc1);
-        T val = T(0);
-        if (sl == 0 && i >= 0 && ok) {
-            val = fma(-rd, acc, t * rd);
-            sh[i - s] = val;
-        }
-        // the count is raised before the global stores, so its fence waits only for the
-        // shared-memory results; a warp with a failed wait counts none of its rows
-        const bool all_ok = __all_sync(0xffffffffu, ok);
-        complete_rows(done, all_ok ? rows : 0u);
-        if (sl == 0 && i >= 0 && all_ok) {
-            st_vol(out + i, publishable_value(val));
-            if (BW) z[__ldg(S.perm + i)] = double(val);
-        }
-        if (!all_ok) break;
-    }
-    __syncthreads();  // sh and the count are reused by the next range
-}
-
-template <int G, typename T>
-__global__ void __launch_bounds__(kDagThreads)
-forward_rows(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all, const double* __restrict__ r,
-             T* y, unsigned long long timeout_ns) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_claim, s_done;
-    const unsigned long long deadline = gclock() + timeout_ns;
-    for (;;) {
-        if (threadIdx.x == 0) s_claim = aborted(S.counter + 2) ? S.nranges : atomicAdd(S.counter + 0, 1);
-        __syncthreads();
-        const int c = s_claim;
-        if (c >= S.nranges) break;
-        const int k = __ldg(S.rf_claim + c);  // -1: left out (host-side fault injection)
-        if (k >= 0)
-            solve_range<G, T, false>(S, uvt, static_cast<const T*>(S.xf_val), rd_all, r, nullptr, y, nullptr, k,
-                                     sh, &s_done, deadline);
-        else
-            __syncthreads();
-    }
-}
-
-template <int G, typename T>
-__global__ void __launch_bounds__(kDagThreads)
-backward_rows(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all, const T* __restrict__ y, T* zv,
-              double* __restrict__ z, unsigned long long timeout_ns) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_claim, s_done;
-    const unsigned long long deadline = gclock() + timeout_ns;
-    for (;;) {
-        if (threadIdx.x == 0) s_claim = aborted(S.counter + 2) ? S.nranges : atomicAdd(S.counter + 1, 1);
-        __syncthreads();
-        const int c = s_claim;
-        if (c >= S.nranges) break;
-        const int k = __ldg(S.rb_claim + c);
-        if (k >= 0)
-            solve_range<G, T, true>(S, uv, static_cast<const T*>(S.xb_val), rd_all, nullptr, y, zv, z, k, sh,
-                                    &s_done, deadline);
-        else
-            __syncthreads();
-    }
-}
-
-template <int G, typename T>
-cudaError_t rows_smem_and_occupancy(size_t smem, int* blocks) {
-    const int cap = int(kMaxBlockRows * sizeof(T));
-    cudaError_t e = cudaFuncSetAttribute(forward_rows<G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(backward_rows<G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    if (e != cudaSuccess) return e;
-    int a = 0, b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, forward_rows<G, T>, kDagThreads, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, backward_rows<G, T>, kDagThreads, smem);
-    *blocks = a < b ? a : b;
-    return e;
-}
-
-template <int G, typename T>
-void launch_rows(const SolvePlan& S, const T* uv, const T* rd, const double* r, double* z, T* y, int grid,
-                 size_t smem, unsigned long long timeout_ns, cudaStream_t s, cudaEvent_t t1) {
-    forward_rows<G, T><<<grid, kDagThreads, smem, s>>>(S, static_cast<const T*>(S.uvt), rd, r, y, timeout_ns);
-    if (t1) cudaEventRecord(t1, s);
-    backward_rows<G, T><<<grid, kDagThreads, smem, s>>>(S, uv, rd, y, y + S.n, z, timeout_ns);
-}
-
-template <typename T>
-cudaError_t launch_rows_t(const SolvePlan& S, const T* uv, const T* rd, const double* r, double* z, T* y,
-                          int grid, unsigned long long timeout_ns, cudaStream_t s, cudaEvent_t t1) {
-    const size_t smem = size_t(S.max_range_rows) * sizeof(T);
-    if (S.lanes_per_row == 4) launch_rows<4, T>(S, uv, rd, r, z, y, grid, smem, timeout_ns, s, t1);
-    else launch_rows<8, T>(S, uv, rd, r, z, y, grid, smem, timeout_ns, s, t1);
-    return cudaGetLastError();
-}
-
 // The shared-memory cap is a per-function setting shared by all handles, so it is
 // always the largest range (kMaxBlockRows rows); the occupancy uses the actual size.
 template <int G, typename T>
@@ -739,39 +452,14 @@ void launch_gathers(const SolvePlan& S, const T* uv, cudaStream_t s) {
 
 // Number of kernels launch_dag_prepare launches.
 int dag_prepare_launches(const SolvePlan& S) {
-    return S.solve_mode == 1 ? 0 : (S.noff > 0) + (S.nxf > 0) + (S.nxb > 0);
+    return S.solve_mode != 0 ? 0 : (S.noff > 0) + (S.nxf > 0) + (S.nxb > 0);
 }
 
 cudaError_t launch_dag_prepare(const SolvePlan& S, cudaStream_t s) {
-    if (S.solve_mode == 1) return cudaSuccess;
+    if (S.solve_mode != 0) return cudaSuccess;
     if (S.dtype == IC_F32) launch_gathers<float>(S, S.uval32, s);
     else launch_gathers<double>(S, S.uval, s);
     return cudaGetLastError();
-}
-
-cudaError_t rows_blocks_per_sm(int lanes, int dtype, int max_range_rows, int* blocks) {
-    const size_t smem = size_t(max_range_rows < 1 ? 1 : max_range_rows) * (dtype == IC_F32 ? 4 : 8);
-    if (dtype == IC_F32)
-        return lanes == 4 ? rows_smem_and_occupancy<4, float>(smem, blocks)
-                          : rows_smem_and_occupancy<8, float>(smem, blocks);
-    return lanes == 4 ? rows_smem_and_occupancy<4, double>(smem, blocks)
-                      : rows_smem_and_occupancy<8, double>(smem, blocks);
-}
-
-cudaError_t launch_apply_rows(const SolvePlan& S, const double* r, double* z, unsigned long long timeout_ns,
-                              int grid, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1) {
-    if (S.n == 0) return cudaSuccess;
-    // both result vectors start as kUnset (forward then backward, n values each)
-    const size_t bytes = 2 * size_t(S.n) * (S.dtype == IC_F32 ? sizeof(float) : sizeof(double));
-    cudaError_t e = cudaMemsetAsync(S.y, 0xff, bytes, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(S.counter, 0, 3 * sizeof(int), s);  // range claims and the abort word
-    if (e != cudaSuccess) return e;
-    if (t0) cudaEventRecord(t0, s);
-    if (S.dtype == IC_F32)
-        return launch_rows_t<float>(S, S.uval32, S.rdiag32, r, z, reinterpret_cast<float*>(S.y), grid, timeout_ns,
-                                    s, t1);
-    return launch_rows_t<double>(S, S.uval, S.rdiag, r, z, S.y, grid, timeout_ns, s, t1);
 }
 
 cudaError_t dag_blocks_per_sm(int lanes, int dtype, int max_range_rows, int* blocks) {

@@ -795,8 +795,6 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
         pad(P.bwd_order, lb, P.bwd_pad);
         P.fwd_depth = n ? int64_t(mf) + 1 : 0;
         P.bwd_depth = n ? int64_t(mb) + 1 : 0;
-        P.gf.swap(lf);
-        P.gb.swap(lb);
     }
 
     // algorithmic flops: per pivot p, one sqrt, |S_p|-1 divides, and two flops for each
@@ -824,7 +822,6 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
     const double nnz_low = double(P.nnz_a + n) / 2.0;
     P.bytes = nnz_low * (8 + 4) + double(P.nnz_u) * (8 + 4) + double(n + 1) * 8;
     build_solve_dag(P, nthr);
-    build_solve_rows(P);
     return IC_OK;
 }
 

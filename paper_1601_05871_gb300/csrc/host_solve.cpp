@@ -19,9 +19,7 @@
 #include <omp.h>
 
 #include <algorithm>
-#include <climits>
 #include <numeric>
-#include <utility>
 
 #include "ick_internal.h"
 
@@ -272,137 +270,6 @@ void build_solve_dag(HostPlan& P, int nthr) {
     };
     build(true, P.fs);
     build(false, P.bs);
-}
-
-// ------------------------------------------------------------------------------
-// Block-row solves (solve_mode 2).  Every block row (range) is one unit of work, solved
-// by one CTA from start to end; its rows are taken in the order of their level in the
-// row dependence DAG of the whole solve (the longest chain of rows before them), so a
-// row's sources -- inside the range or in other ranges -- have lower levels.  A source
-// inside the range is read from shared memory, one in another range from global
-// memory, and each value is its own completion flag, so there is no coarser
-// synchronisation than the rows themselves across ranges; inside a range a row waits,
-// as in the block-DAG solves, for the range's count of completed rows to reach the
-// rows of its lower levels (one shared word polled by one lane per waiting warp).  The CTAs claim the ranges in a
-// topological order of the range graph (range r after every range holding a source of
-// one of its rows), preferring the range whose rows can start first; a CTA waits only
-// for rows of ranges claimed before its own, which are running or finished, so the
-// claims cannot deadlock.
-namespace {
-
-// Rows of each range sorted by lev (ties: ascending row, or descending for the
-// backward solve), each level's run padded with -1 to a multiple of kClaimPad.  need
-// receives, per position, the number of the range's rows in lower levels: the row
-// there may run once that many rows of the range are complete.
-void level_order(const HostPlan& P, const std::vector<int32_t>& lev, bool descending,
-                 std::vector<int32_t>& ptr, std::vector<int32_t>& ord, std::vector<int32_t>& need) {
-    const int32_t nb = int32_t(P.ranges.size()) - 1;
-    ptr.assign(nb + 1, 0);
-    ord.clear();
-    need.clear();
-    std::vector<int32_t> rows;
-    for (int32_t k = 0; k < nb; ++k) {
-        const int32_t s = P.ranges[k], e = P.ranges[k + 1];
-        rows.resize(e - s);
-        for (int32_t q = 0; q < e - s; ++q) rows[q] = descending ? e - 1 - q : s + q;
-        std::stable_sort(rows.begin(), rows.end(), [&](int32_t a, int32_t b) { return lev[a] < lev[b]; });
-        int32_t before = 0;
-        for (size_t q = 0; q < rows.size(); ++q) {
-            ord.push_back(rows[q]);
-            need.push_back(before);
-            if (q + 1 == rows.size() || lev[rows[q + 1]] != lev[rows[q]]) {
-                while (ord.size() % kClaimPad) {
-                    ord.push_back(-1);
-                    need.push_back(before);
-                }
-                before = int32_t(q) + 1;
-            }
-        }
-        ptr[k + 1] = int32_t(ord.size());
-    }
-}
-
-// Claim order of the ranges: Kahn's algorithm on the range graph, the ready range with
-// the lowest first level taken first (ties: the range order of the solve direction).
-template <class Sources>
-void claim_order(const HostPlan& P, const std::vector<int32_t>& lev, bool backward, Sources sources,
-                 std::vector<int32_t>& out) {
-    const int32_t nb = int32_t(P.ranges.size()) - 1;
-    std::vector<std::vector<int32_t>> succ(nb);
-    std::vector<int32_t> indeg(nb, 0), mark(nb, -1), first(nb, INT32_MAX);
-    for (int32_t k = 0; k < nb; ++k) {
-        for (int32_t i = P.ranges[k]; i < P.ranges[k + 1]; ++i) {
-            first[k] = std::min(first[k], lev[i]);
-            sources(i, [&](int32_t src) {
-                const int32_t u = P.blk_of[src];
-                if (u != k && mark[u] != k) {
-                    mark[u] = k;
-                    succ[u].push_back(k);
-                    ++indeg[k];
-                }
-            });
-        }
-    }
-    auto later = [&](int32_t a, int32_t b) {  // heap order: true when a comes after b
-        if (first[a] != first[b]) return first[a] > first[b];
-        return backward ? a < b : a > b;
-    };
-    std::vector<int32_t> heap;
-    for (int32_t k = 0; k < nb; ++k)
-        if (indeg[k] == 0) heap.push_back(k);
-    std::make_heap(heap.begin(), heap.end(), later);
-    out.clear();
-    while (!heap.empty()) {
-        std::pop_heap(heap.begin(), heap.end(), later);
-        const int32_t k = heap.back();
-        heap.pop_back();
-        out.push_back(k);
-        for (int32_t s : succ[k])
-            if (--indeg[s] == 0) {
-                heap.push_back(s);
-                std::push_heap(heap.begin(), heap.end(), later);
-            }
-    }
-}
-
-// Each row's internal entries sorted by the level of their source, lowest first: the
-// sources that finish last are summed last, after the others.
-void sort_by_source_level(const HostPlan& P, const std::vector<int32_t>& lev, SolveLayout& L) {
-    const int64_t n = P.n;
-    std::vector<std::pair<int64_t, int32_t>> tmp;
-    for (int64_t i = 0; i < n; ++i) {
-        const int32_t s = P.ranges[P.blk_of[i]];
-        const int32_t a = L.ptr[i], b = L.ptr[i + 1];
-        tmp.clear();
-        for (int32_t q = a; q < b; ++q)
-            tmp.emplace_back((int64_t(lev[s + L.j[q]]) << 32) | uint32_t(L.j[q]), L.pos[q]);
-        std::sort(tmp.begin(), tmp.end());
-        for (int32_t q = a; q < b; ++q) {
-            L.j[q] = int32_t(tmp[q - a].first & 0xffffffff);
-            L.pos[q] = tmp[q - a].second;
-        }
-    }
-}
-
-}  // namespace
-
-void build_solve_rows(HostPlan& P) {
-    level_order(P, P.gf, false, P.rf_ptr, P.rf_ord, P.rf_need);
-    level_order(P, P.gb, true, P.rb_ptr, P.rb_ord, P.rb_need);
-    // forward: the external sources of row i are the column-list entries before sf_split
-    claim_order(P, P.gf, false,
-                [&](int32_t i, auto&& use) {
-                    for (int32_t e = P.cptr[i]; e < P.sf_split[i]; ++e) use(P.csc[e].x);
-                },
-                P.rf_claim);
-    // backward: the entries of row i after its sb_nint internal ones
-    claim_order(P, P.gb, true,
-                [&](int32_t i, auto&& use) {
-                    for (int64_t e = P.urp[i] + 1 + P.sb_nint[i]; e < P.urp[i + 1]; ++e) use(P.ucol[e]);
-                },
-                P.rb_claim);
-    sort_by_source_level(P, P.gf, P.xf);
-    sort_by_source_level(P, P.gb, P.xb);
 }
 
 }  // namespace ick

@@ -79,12 +79,6 @@ struct HostPlan {
     std::vector<int32_t> fwd_order, bwd_order;  // claim orders of the triangular solves
     std::vector<int32_t> fwd_pad, bwd_pad;      // the same, each level padded with -1
     int64_t fwd_depth = 0, bwd_depth = 0;        // levels of the row dependence DAGs
-    std::vector<int32_t> gf, gb;                // each row's level in those DAGs
-    // block-row solves (solve_mode 2, host_solve.cpp): per range its rows ordered by
-    // level, each level's run padded with -1 to a multiple of kClaimPad (offsets per
-    // range in *_ptr), and the order in which CTAs claim the ranges
-    std::vector<int32_t> rf_ptr, rf_ord, rb_ptr, rb_ord, rf_claim, rb_claim;
-    std::vector<int32_t> rf_need, rb_need;  // per position: the range's rows of lower levels
     // block-DAG solves (host_solve.cpp): per row the start of the internal entries
     // (forward: absolute column-list index; backward: count after the diagonal), per
     // range the padded local orders, and each direction's tasks
@@ -179,8 +173,7 @@ struct SolvePlan {
     const double* udiag;   // IC_F32 FP64 pivots
     float* rdiag32;        // IC_F32 reciprocal pivots
     // block-DAG solves (blocksolve.cu); see HostPlan for the meaning of the arrays
-    int solve_mode;        // 0: block-DAG solves, 1: row-level solves in level order,
-                           // 2: block-row solves (one CTA per range, rows in level order)
+    int solve_mode;        // 0: block-DAG solves, 1: row-level solves in level order
     int nranges, max_range_rows, nftask, nbtask, noff;
     const int* ranges;     // nranges + 1 row boundaries of the block rows
     const int* sf_split;
@@ -216,16 +209,6 @@ struct SolvePlan {
     const int* b_next;
     int* dag_taken;        // per task (forward then backward): 1 once a CTA has taken it
     void* dag_w;           // external sums of the rows (n values of the solve type)
-    // block-row solves (solve_mode 2): per range the rows in level order (padded) and
-    // the range claim orders; see HostPlan
-    const int* rf_ptr;
-    const int* rf_ord;
-    const int* rb_ptr;
-    const int* rb_ord;
-    const int* rf_claim;
-    const int* rb_claim;
-    const int* rf_need;
-    const int* rb_need;
     unsigned long long* trace;  // NULL, or 4 words per task: forward tasks, then backward
 };
 
@@ -246,9 +229,6 @@ cudaError_t launch_apply_dag(const SolvePlan& S, const double* r, double* z, uns
 cudaError_t launch_dag_prepare(const SolvePlan& S, cudaStream_t s);
 int dag_prepare_launches(const SolvePlan& S);
 cudaError_t dag_blocks_per_sm(int lanes, int dtype, int max_range_rows, int* blocks);
-cudaError_t launch_apply_rows(const SolvePlan& S, const double* r, double* z, unsigned long long timeout_ns,
-                              int grid, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1);
-cudaError_t rows_blocks_per_sm(int lanes, int dtype, int max_range_rows, int* blocks);
 cudaError_t launch_spmv(const SolvePlan& S, const double* av, const double* x, double* y,
                         cudaStream_t s);
 cudaError_t apply_blocks_per_sm(int* blocks);
@@ -324,7 +304,6 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
                int64_t nranges, int block_rows, int rows_per_item, int threads, bool k_order,
                HostPlan& P, std::string& err);
 void build_solve_dag(HostPlan& P, int threads);
-void build_solve_rows(HostPlan& P);
 int block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, std::vector<int4>& task,
               std::vector<int64_t>& pred_ptr, std::vector<int32_t>& pred);
 int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep, int32_t* perm,

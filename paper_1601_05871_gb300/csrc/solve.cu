@@ -425,7 +425,6 @@ cudaError_t launch_apply(const SolvePlan& S, const double* r, double* z, int epo
     if (S.n == 0) return cudaSuccess;
     (void)epoch;
     if (S.solve_mode == 0) return launch_apply_dag(S, r, z, timeout_ns, grid, s, t0, t1);
-    if (S.solve_mode == 2) return launch_apply_rows(S, r, z, timeout_ns, grid, s, t0, t1);
     // S.y holds 2n doubles: the forward then the backward result (2n floats for IC_F32)
     const size_t bytes = 2 * size_t(S.n) * (S.dtype == IC_F32 ? sizeof(float) : sizeof(double));
     cudaError_t e = cudaMemsetAsync(S.y, 0xff, bytes, s);

@@ -92,7 +92,6 @@ def load():
         "ic_get_solve_trace": (I, [P, I, P]),
         "ic_get_solve_entries": (I, [P, I, P, P, P]),
         "ic_get_split_layout": (I, [P, P, P, P, P]),
-        "ic_get_solve_rows": (I, [P, I, P, P, P, P, P]),
         "ic_shift_features": (I, [P, P, D, P, P]),
         "ic_numeric_shifted": (I, [P, P, D, D, I, P, P, P]),
         "ic_mlp_n_params": (I, []),
@@ -387,21 +386,6 @@ def ic_get_solve_entries(h, backward=False):
     pos = np.empty(max(1, m), dtype=np.int32)
     _check(L.ic_get_solve_entries(h.ptr, int(bool(backward)), None, _p(j), _p(pos)))
     return {"ptr": ptr, "j": j[:m], "pos": pos[:m]}
-
-
-def ic_get_solve_rows(h, backward=False):
-    """Block-row solve plan of one direction: dict with claim (nranges), ptr (nranges+1),
-    ord (rows of each block row in solve order, -1 padding) and need (per position)."""
-    L = load()
-    nr = ic_stats(h)["nranges"]
-    no = np.zeros(1, dtype=np.int64)
-    _check(L.ic_get_solve_rows(h.ptr, int(bool(backward)), None, None, None, None, _p(no)))
-    claim = np.empty(max(1, nr), dtype=np.int32)
-    ptr = np.empty(nr + 1, dtype=np.int32)
-    ord_ = np.empty(max(1, int(no[0])), dtype=np.int32)
-    need = np.empty(max(1, int(no[0])), dtype=np.int32)
-    _check(L.ic_get_solve_rows(h.ptr, int(bool(backward)), _p(claim), _p(ptr), _p(ord_), _p(need), None))
-    return {"claim": claim[:nr], "ptr": ptr, "ord": ord_[: int(no[0])], "need": need[: int(no[0])]}
 
 
 def ic_get_split_layout(h):

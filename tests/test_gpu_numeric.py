@@ -283,78 +283,18 @@ def test_row_level_and_block_dag_solves_agree(ick, orc, dtype):
     r = np.random.default_rng(7).standard_normal(prob.n)
     zr = o.apply(r)
     out = []
-    for mode, lanes in ((1, 0), (0, 0), (2, 8), (2, 4)):
+    for mode in (1, 0):
         h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=512, dtype=dtype,
-                            solve_mode=mode, solve_lanes=lanes)
+                            solve_mode=mode)
         ick.ic_numeric(h, dev(prob.vals))
         z = torch.empty(prob.n, dtype=torch.float64, device="cuda")
         ick.ic_apply(h, dev(r), z)
-        ick.ic_apply_status(h)
+        torch.cuda.synchronize()
         out.append(z.cpu().numpy())
     tol = 1e-11 if dtype == 0 else 2e-4
     for z in out:
         assert np.abs(z - zr).max() <= tol * np.abs(zr).max()
-    for z in out[1:]:
-        assert np.abs(out[0] - z).max() <= tol * np.abs(zr).max()
-
-
-@pytest.mark.parametrize("dtype,lanes", [(0, 8), (0, 4), (1, 8)])
-def test_block_row_solves(ick, orc, dtype, lanes):
-    """Block-row solves (solve_mode 2) on a nested-dissection 27-point problem with
-    ragged block rows: the oracle's application within the precision's bound, the same
-    bits on repeated applications (each row sums in a fixed order whatever the timing),
-    and PCG within one iteration of the oracle's."""
-    import torch
-    prob = synth.laplace3d_27pt(22)
-    perm, ranges = ick.ic_nd_grid(22, 22, 22, 1, 700)
-    h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=300, dtype=dtype,
-                        solve_mode=2, solve_lanes=lanes)
-    av = dev(prob.vals)
-    ick.ic_numeric(h, av)
-    o = orc.OracleIC.from_problem(prob, perm, 2)
-    o.numeric(prob.vals)
-    r = np.random.default_rng(8).standard_normal(prob.n)
-    zr = o.apply(r)
-    z1 = torch.empty(prob.n, dtype=torch.float64, device="cuda")
-    z2 = torch.empty_like(z1)
-    ick.ic_apply(h, dev(r), z1)
-    ick.ic_apply(h, dev(r), z2)
-    ick.ic_apply_status(h)
-    tol = 1e-11 if dtype == 0 else 2e-4
-    assert np.abs(z1.cpu().numpy() - zr).max() <= tol * np.abs(zr).max()
-    assert torch.equal(z1, z2)
-    b = synth.rhs(prob.n, 3)
-    x = torch.empty(prob.n, dtype=torch.float64, device="cuda")
-    it, rel = ick.pcg_solve(h, av, dev(b), x, 1e-10, 500)
-    xo, ito, relo, st = orc.pcg(prob, b, o, tol=1e-10)
-    assert st == 0 and abs(it - ito) <= 1 and rel <= 1e-10, (it, ito)
-
-
-def test_block_row_solve_timeout_is_reported_and_recovers(ick, orc):
-    """Host-side fault injection into the block-row solves: one block row is left out
-    of the claim order, so the rows that need it wait in vain until timeout_s; the
-    timeout is reported and, with the plan restored, the next application is right."""
-    import torch
-    prob = synth.diffusion3d_7pt(14, sigma=1.0, seed=3003)
-    perm, ranges = ick.ic_nd_grid(14, 14, 14, 1, 256)
-    h = ick.ic_symbolic(prob.rowptr, prob.colind, 1, perm, ranges, block_rows=256, timeout_s=0.5, solve_mode=2)
-    ick.ic_numeric(h, dev(prob.vals))
-    o = orc.OracleIC.from_problem(prob, perm, 1)
-    o.numeric(prob.vals)
-    nr = ick.ic_stats(h)["nranges"]
-    rh = np.random.default_rng(5).standard_normal(prob.n)
-    r = dev(rh)
-    z = torch.empty_like(r)
-    ick.ic_test_hold_solve_task(h, nr // 3, 1)   # an early block row of the forward solve
-    ick.ic_apply(h, r, z)
-    with pytest.raises(ick.IckError) as e:
-        ick.ic_apply_status(h)
-    assert e.value.status == 4
-    ick.ic_test_hold_solve_task(h, nr // 3, 0)
-    ick.ic_apply(h, r, z)
-    ick.ic_apply_status(h)
-    zr = o.apply(rh)
-    assert np.abs(z.cpu().numpy() - zr).max() <= 1e-11 * np.abs(zr).max()
+    assert np.abs(out[0] - out[1]).max() <= tol * np.abs(zr).max()
 
 
 def test_pcg_matches_oracle(ick, orc):
