@@ -74,7 +74,8 @@ __device__ bool await_count(const int* done, int need, int* abort_word, unsigned
         }
         (void)d;
     }
-    __threadfence_block();
+    // acquire: pairs with the release of complete_rows, so the rows counted are visible
+    asm volatile("fence.acq_rel.cta;" ::: "memory");
     return true;
 }
 
@@ -97,12 +98,15 @@ struct Held {
     static constexpr int M = 64 / G;
 };
 
-// Marks the warp's rows complete: every lane's stores precede the count update.
+// Marks the warp's rows complete: every lane's stores precede the count update (the
+// warp barrier orders them before lane 0's release-add, which publishes them to the
+// CTA's threads that acquire the count).
 __device__ __forceinline__ void complete_rows(int* done, unsigned rows_mask) {
     __syncwarp();
     if ((threadIdx.x & 31) == 0 && rows_mask) {
-        __threadfence_block();
-        atomicAdd(done, __popc(rows_mask));
+        const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(done));
+        asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(a), "r"(__popc(rows_mask))
+                     : "memory");
     }
 }
 
