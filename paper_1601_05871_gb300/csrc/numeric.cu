@@ -188,6 +188,11 @@ template <bool EXACT, typename T>
 __device__ __forceinline__ void apply_staged(WarpBuf<T>& W, const int* cols, const T* vals, int n,
                                              int c_0, unsigned span, T a) {
     const int lane = threadIdx.x & 31;
+    if (n <= 32) {  // most segments: one element per lane (n is the same for the warp)
+        const int i0 = lane < n ? find_col(W, cols[lane], c_0, span) : -1;
+        if (i0 >= 0) W.tval[i0] = sub_product<EXACT>(W.tval[i0], a, vals[lane]);
+        return;
+    }
     const int i0 = lane < n ? find_col(W, cols[lane], c_0, span) : -1;
     const int i1 = lane + 32 < n ? find_col(W, cols[lane + 32], c_0, span) : -1;
     const T v0 = vals[lane], v1 = vals[lane + 32];
