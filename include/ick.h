@@ -143,8 +143,9 @@ int ic_symbolic(const ic_csr_pattern* A, int k, const int32_t* perm, const int64
                 int64_t nranges, const ic_opts* opts, ic_handle** out);
 
 /* Numeric factorization (Section 3.3): scatters B's values onto S (zero on fill) and
- * runs the Chol / Trsm / Herk / Gemm task DAG in one persistent kernel launch that
- * drains a device ready queue through atomic dependency counters.  Updates that
+ * runs the Chol / Trsm / Herk / Gemm task DAG in one persistent kernel launch whose
+ * CTAs claim the work items in a precomputed order (ic_get_claim_order) and start each
+ * once its atomic dependency counter has reached zero.  Updates that
  * fall outside S are discarded.  Blocks until the stream has finished the launch.
  *   values  device, nnz(A) doubles in A's CSR order.
  *   breakdown_row  host out (may be NULL): -1, or the smallest row (permuted order)
@@ -290,6 +291,17 @@ int ic_get_solve_tasks(const ic_handle* h, int backward, int64_t* ntasks, int32_
  * (ptr[n]): the position of the value in ic_get_upper's row-major storage.
  * Errors: IC_ERR_ARG. */
 int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t* j, int32_t* pos);
+
+/* The order in which the persistent numeric kernel's CTAs claim the work items (ic_stats
+ * nitems of them), for inspection: task[q] and chunk[q] (host buffers of nitems
+ * entries, either may be NULL) of the q-th item claimed.  The symbolic phase computes
+ * it as a list schedule of the task DAG (Section 3.3) on the kernel's CTAs, under a
+ * duration model of the items, running first the ready item whose task has the
+ * longest remaining path; every item comes after all items of its task's
+ * predecessors, so a CTA waiting for a claimed item's predecessors waits only for
+ * items held by running CTAs.  A host-only handle's order assumes 152 CTAs.
+ * Errors: IC_ERR_ARG. */
+int ic_get_claim_order(const ic_handle* h, int32_t* task, int32_t* chunk);
 
 /* Layout of the split Chol/Trsm tasks (ic_stats nsplit), for inspection.  A split
  * task's finished rows are published in a shadow array of *nshadow values: the target

@@ -57,7 +57,6 @@ struct ic_handle {
     SolvePlan sp{};
     int grid_numeric = 0;
     int grid_apply = 0;
-    int epoch = 0;
     int apply_epoch = 0;
     bool factored = false;
     double symbolic_s = 0.0;
@@ -128,6 +127,10 @@ namespace {
 // count: systems in the handle.  One system: a CTA of 32 warps per SM, so the Chol
 // tasks of the top separators, which run alone, get a whole SM; a batch of small
 // systems: two CTAs of 16 warps per SM, twice the tasks in flight.
+// CTAs of the numeric kernel assumed by a host-only handle's claim order (one 32-warp
+// CTA per SM of a GB300).
+constexpr int kHostOnlyCtas = 152;
+
 ic_opts normalise(const ic_opts* o, int64_t count) {
     ic_opts r{};
     if (o) r = *o;
@@ -149,7 +152,6 @@ int upload_plan(ic_handle* h) {
     D.nb = int(P.ranges.size()) - 1;
     D.ntasks = int(P.task.size());
     D.total_items = int(P.total_items);
-    D.nseeds = int(P.seeds.size());
     D.rows_per_item = P.rows_per_item;
     {
         const int64_t* dptr = nullptr;
@@ -181,7 +183,6 @@ int upload_plan(ic_handle* h) {
     if ((st = h->upload(&D.succ_ptr, P.succ_ptr))) return st;
     if ((st = h->upload(&D.succ, P.succ))) return st;
     if ((st = h->upload(&D.indeg0, P.indeg0))) return st;
-    if ((st = h->upload(&D.seeds, P.seeds))) return st;
     if ((st = h->upload(&D.flag_off, P.flag_off))) return st;
     if ((st = h->upload(&D.soff, P.soff))) return st;
     D.nshadow = P.nshadow;
@@ -213,14 +214,9 @@ int upload_plan(ic_handle* h) {
     if ((st = h->alloc(&D.urcp, size_t(P.n)))) return st;
     if ((st = h->alloc(&D.indeg, P.task.size()))) return st;
     if ((st = h->alloc(&D.items_left, P.task.size()))) return st;
-    if ((st = h->alloc(&D.queue, size_t(P.total_items)))) return st;
-    if ((st = h->alloc(&D.qstamp, size_t(P.total_items)))) return st;
-    CK(cudaMemset(D.qstamp, 0, size_t(P.total_items) * sizeof(int)));
     if ((st = h->alloc(&D.counters, 8))) return st;
     if ((st = h->alloc(&D.brk_row, 1))) return st;
     if ((st = h->alloc(&D.diag, 8))) return st;
-    if ((st = h->alloc(&D.epoch_dev, 1))) return st;
-    CK(cudaMemset(D.epoch_dev, 0, sizeof(int)));
 
     // solve / PCG buffers
     SolvePlan& S = h->sp;
@@ -334,6 +330,10 @@ int upload_plan(ic_handle* h) {
     CK(numeric_blocks_per_sm(h->opts.warps_per_cta, h->opts.exact != 0, h->opts.dtype, &bpsm));
     if (bpsm < 1) return fail(IC_ERR_CUDA, "numeric kernel cannot be resident");
     h->grid_numeric = sms * bpsm;
+    // the order in which the persistent kernel's CTAs claim the work items
+    build_claim_order(P, h->grid_numeric);
+    if (int64_t(P.claim.size()) != P.total_items) return fail(IC_ERR_ARG, "task graph has a cycle");
+    if ((st = h->upload(&D.claim, P.claim))) return st;
     if (S.solve_mode == 0)
         CK(dag_blocks_per_sm(S.lanes_per_row, S.dtype, P.max_range_rows, &bpsm));
     else
@@ -458,6 +458,7 @@ static int symbolic_impl(const ic_csr_pattern* A, int k, const int32_t* perm, co
             return fail(st, err);
         }
         if (h->opts.host_only) {
+            build_claim_order(h->hp, kHostOnlyCtas);
             h->row_off.assign(row_off, row_off + count + 1);
             h->symbolic_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
             *out = h;
@@ -549,15 +550,14 @@ int ic_batch_info(const ic_handle* h, int64_t* count, int64_t* row_off) {
 static int numeric_enqueue(ic_handle* h, const void* values, cudaStream_t s, bool timing) {
     if (!values && h->hp.nnz_a > 0) return fail(IC_ERR_ARG, "NULL values");
     if (h->opts.host_only) return fail(IC_ERR_STATE, "handle was created with host_only");
-    const int epoch = ++h->epoch;
     const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
     if (timing) CK(cudaEventRecord(h->ev[0], s));
-    CK(launch_numeric_prepare(h->dp, static_cast<const double*>(values), h->opts.shift_alpha, epoch,
-                              h->opts.dtype, s));
+    CK(launch_numeric_prepare(h->dp, static_cast<const double*>(values), h->opts.shift_alpha, h->opts.dtype,
+                              s));
     ++h->tm.launches;
     if (timing) CK(cudaEventRecord(h->ev[1], s));
     if (h->dp.total_items > 0) {
-        CK(launch_numeric(h->dp, epoch, h->opts.warps_per_cta, h->opts.exact != 0, h->opts.dtype,
+        CK(launch_numeric(h->dp, h->opts.warps_per_cta, h->opts.exact != 0, h->opts.dtype,
                           h->grid_numeric, tmo, s));
         ++h->tm.launches;
     }
@@ -1066,6 +1066,16 @@ int ic_get_solve_entries(const ic_handle* h, int backward, int32_t* ptr, int32_t
     return IC_OK;
 }
 
+int ic_get_claim_order(const ic_handle* h, int32_t* task, int32_t* chunk) {
+    if (!h) return fail(IC_ERR_ARG, "NULL handle");
+    const std::vector<int2>& c = h->hp.claim;
+    for (size_t q = 0; q < c.size(); ++q) {
+        if (task) task[q] = c[q].x;
+        if (chunk) chunk[q] = c[q].y;
+    }
+    return IC_OK;
+}
+
 int ic_get_split_layout(const ic_handle* h, int32_t* flag_off, int32_t* soff, int64_t* nsoff,
                         int64_t* nshadow) {
     if (!h) return fail(IC_ERR_ARG, "NULL handle");
@@ -1176,19 +1186,6 @@ int ic_test_hold_task(ic_handle* h, int64_t t, int extra) {
     DeviceGuard g(h->device);
     const int v = h->hp.indeg0[t] + extra;
     CK(cudaMemcpy(const_cast<int*>(h->dp.indeg0) + t, &v, sizeof(int), cudaMemcpyHostToDevice));
-    // a held task that had no predecessor must also leave the seed list
-    int nseed = 0;
-    std::vector<int2> seeds;
-    for (size_t u = 0; u < h->hp.task.size(); ++u) {
-        const int deg = (int64_t(u) == t) ? v : h->hp.indeg0[u];
-        if (deg == 0)
-            for (int c = 0; c < h->hp.nitems[u]; ++c) seeds.push_back(make_int2(int(u), c));
-    }
-    nseed = int(seeds.size());
-    if (!seeds.empty())
-        CK(cudaMemcpy(const_cast<int2*>(h->dp.seeds), seeds.data(), seeds.size() * sizeof(int2),
-                      cudaMemcpyHostToDevice));
-    h->dp.nseeds = nseed;
     return IC_OK;
 }
 

@@ -6,7 +6,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <numeric>
+#include <queue>
 
 #include "ick_internal.h"
 
@@ -692,7 +694,7 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
 
     if (!k_order) order_updates(P, ttgt);
 
-    // items, successors, in-degrees, seeds, critical path, type counts
+    // items, successors, in-degrees, critical path, type counts
     P.nitems.resize(nt);
     P.indeg0.resize(nt);
     P.total_items = 0;
@@ -718,10 +720,6 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
         for (int64_t t = 0; t < nt; ++t)
             for (int64_t e = P.pred_ptr[t]; e < P.pred_ptr[t + 1]; ++e) P.succ[fill[P.pred[e]]++] = int32_t(t);
     }
-    P.seeds.clear();
-    for (int64_t t = 0; t < nt; ++t)
-        if (P.indeg0[t] == 0)
-            for (int32_t c = 0; c < P.nitems[t]; ++c) P.seeds.push_back(make_int2(int(t), c));
     {
         // longest chain of tasks, over a topological order (in FMA mode an update's
         // predecessor in its block's chain can have a larger index)
@@ -823,6 +821,145 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
     P.bytes = nnz_low * (8 + 4) + double(P.nnz_u) * (8 + 4) + double(n + 1) * 8;
     build_solve_dag(P, nthr);
     return IC_OK;
+}
+
+// ---------------------------------------------------------------- claim order
+
+namespace {
+
+// Duration model of a work item (microseconds), fitted on %globaltimer traces of the
+// persistent kernel on a GB300 (27-point Laplacian 96^3, IC(2), FP64, 32 warps per CTA:
+// median relative error 1-15 % per kind).  A Chol or Trsm task on one CTA runs its
+// block's rows in dependence levels (L levels, about 1.3 us each for Chol) plus its
+// pivot applications spread over the CTA's warps; an item of a split task advances
+// about 2.3 us per level (rows handed between CTAs through L2); a Herk/Gemm item costs
+// a fixed part plus about 20 ns per pivot application.  Only the claim order depends on
+// these numbers, never the results.
+double item_cost(int type, bool split, double levels, double pivots) {
+    double d;
+    if (split) d = 14.74 + 2.343 * levels + 0.0521 * pivots / 256.0;
+    else if (type == T_CHOL) d = -36.83 + 1.298 * levels + 0.774 * pivots / 32.0;
+    else if (type == T_TRSM) d = 55.57 + 0.0659 * levels + 0.751 * pivots / 32.0;
+    else if (type == T_HERK) d = 6.162 + 0.0213 * pivots;
+    else d = 16.41 + 0.0133 * pivots;
+    return std::max(d, 0.5);
+}
+
+}  // namespace
+
+// Claim order of the persistent numeric kernel's work items (Section 2.2's scheduler
+// duty of running ready tasks, with an order chosen on the host): a list schedule of
+// the task DAG on nctas CTAs under item_cost, in which a free CTA takes the ready item
+// whose task has the longest remaining path to the end of the DAG; the order in which
+// items start is the order in which the kernel's CTAs claim them.  An item is listed
+// only after every item of its task's predecessors, so a CTA that waits for an item's
+// predecessors waits only for items claimed before it, held by running CTAs.
+void build_claim_order(HostPlan& P, int nctas) {
+    const int64_t nt = int64_t(P.task.size()), n = P.n;
+    P.claim.clear();
+    if (nt == 0) return;
+    nctas = std::max(nctas, 1);
+    // dependence levels of every block's rows (the Chol/Trsm chain of that block)
+    std::vector<int32_t> lev(size_t(n), 0);
+    std::vector<int32_t> blev(P.ranges.size(), 0);
+    for (int64_t r = 0; r < n; ++r) {
+        const int32_t b = P.blk_of[r];
+        int32_t d = 0;
+        for (int32_t e = P.cptr[r]; e < P.cptr[r + 1]; ++e) {
+            const int32_t p = P.csc[e].x;
+            if (P.blk_of[p] == b) d = std::max(d, lev[p] + 1);
+        }
+        lev[r] = d;
+        blev[b] = std::max(blev[b], d + 1);
+    }
+    // item costs and task durations
+    std::vector<int64_t> first(nt + 1, 0);
+    for (int64_t t = 0; t < nt; ++t) first[t + 1] = first[t] + P.nitems[t];
+    std::vector<double> cost(static_cast<size_t>(first[nt])), tdur(static_cast<size_t>(nt));
+    const int rpi = std::max(P.rows_per_item, 1);
+    for (int64_t t = 0; t < nt; ++t) {
+        const int type = P.task[t].x;
+        const int32_t a = P.tgt_ptr[t], b = P.tgt_ptr[t + 1];
+        if (type == T_CHOL || type == T_TRSM) {
+            double piv = 0.0;
+            for (int32_t q = a; q < b; ++q) piv += double(P.tgt[q].z - P.tgt[q].y);
+            const double c = item_cost(type, P.nitems[t] > 1, double(blev[P.task[t].y]), piv);
+            for (int64_t it = first[t]; it < first[t + 1]; ++it) cost[it] = c;
+            tdur[t] = c;
+        } else {
+            double sum = 0.0;
+            for (int32_t c = 0; c < P.nitems[t]; ++c) {
+                double piv = 0.0;
+                for (int32_t q = a + c * rpi; q < std::min(b, a + (c + 1) * rpi); ++q)
+                    piv += double(P.tgt[q].z - P.tgt[q].y);
+                cost[first[t] + c] = item_cost(type, false, 0.0, piv);
+                sum += cost[first[t] + c];
+            }
+            tdur[t] = sum / double(std::min<int64_t>(P.nitems[t], nctas));
+        }
+    }
+    // longest remaining path of every task, over a topological order
+    std::vector<int32_t> left(P.indeg0), topo;
+    topo.reserve(nt);
+    for (int64_t t = 0; t < nt; ++t)
+        if (left[t] == 0) topo.push_back(int32_t(t));
+    for (size_t q = 0; q < topo.size(); ++q)
+        for (int32_t e = P.succ_ptr[topo[q]]; e < P.succ_ptr[topo[q] + 1]; ++e)
+            if (--left[P.succ[e]] == 0) topo.push_back(P.succ[e]);
+    if (int64_t(topo.size()) != nt) return;  // not a DAG: reported by the caller
+    std::vector<double> rem(nt, 0.0);
+    for (int64_t q = nt - 1; q >= 0; --q) {
+        const int32_t t = topo[q];
+        double m = 0.0;
+        for (int32_t e = P.succ_ptr[t]; e < P.succ_ptr[t + 1]; ++e) m = std::max(m, rem[P.succ[e]]);
+        rem[t] = tdur[t] + m;
+    }
+    // the list schedule (1 us per claim)
+    struct Ready {
+        double rem;
+        int32_t task, chunk;
+        bool operator<(const Ready& o) const {  // max-heap: longest remaining path first
+            if (rem != o.rem) return rem < o.rem;
+            if (task != o.task) return task > o.task;
+            return chunk > o.chunk;
+        }
+    };
+    std::priority_queue<Ready> ready;
+    using Ev = std::pair<double, int32_t>;  // (finish time, task)
+    std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> running;
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (int c = 0; c < nctas; ++c) free_at.push(0.0);
+    std::vector<int32_t> deg(P.indeg0), items_left(P.nitems);
+    for (int64_t t = 0; t < nt; ++t)
+        if (deg[t] == 0)
+            for (int32_t c = 0; c < P.nitems[t]; ++c) ready.push({rem[t], int32_t(t), c});
+    P.claim.reserve(size_t(first[nt]));
+    while (int64_t(P.claim.size()) < first[nt]) {
+        const double tf = free_at.top();
+        free_at.pop();
+        while (!running.empty() && running.top().first <= tf) {
+            const int32_t t = running.top().second;
+            running.pop();
+            if (--items_left[t] == 0)
+                for (int32_t e = P.succ_ptr[t]; e < P.succ_ptr[t + 1]; ++e) {
+                    const int32_t u = P.succ[e];
+                    if (--deg[u] == 0)
+                        for (int32_t c = 0; c < P.nitems[u]; ++c) ready.push({rem[u], u, c});
+                }
+        }
+        if (!ready.empty()) {
+            const Ready r = ready.top();
+            ready.pop();
+            P.claim.push_back(make_int2(r.task, r.chunk));
+            const double fin = tf + 1.0 + cost[first[r.task] + r.chunk];
+            running.push({fin, r.task});
+            free_at.push(fin);
+        } else if (!running.empty()) {
+            free_at.push(running.top().first);
+        } else {
+            break;  // cannot happen in a DAG
+        }
+    }
 }
 
 }  // namespace ick

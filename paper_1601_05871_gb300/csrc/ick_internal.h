@@ -75,7 +75,7 @@ struct HostPlan {
     std::vector<int32_t> tgt_ptr;   // ntasks + 1
     std::vector<int4> tgt;          // (r, csc_a, csc_b, seg_begin)
     std::vector<int32_t> tgt_end;   // seg_end
-    std::vector<int2> seeds;        // (task, chunk) items ready at start
+    std::vector<int2> claim;        // (task, chunk) of every work item in claim order
     std::vector<int32_t> fwd_order, bwd_order;  // claim orders of the triangular solves
     std::vector<int32_t> fwd_pad, bwd_pad;      // the same, each level padded with -1
     int64_t fwd_depth = 0, bwd_depth = 0;        // levels of the row dependence DAGs
@@ -98,7 +98,7 @@ struct HostPlan {
 
 // Plain pointers handed to the kernels by value.
 struct DevPlan {
-    int n, nnz_u, nb, ntasks, total_items, nseeds, rows_per_item;
+    int n, nnz_u, nb, ntasks, total_items, rows_per_item;
     const long long* urp;
     const int* ucol;
     const int* gsrc;
@@ -117,7 +117,7 @@ struct DevPlan {
     const int* succ_ptr;
     const int* succ;
     const int* indeg0;
-    const int2* seeds;
+    const int2* claim;     // work items (task, chunk) in the order the CTAs claim them
     const int* flag_off;   // per task: its block's rows in soff (split Chol/Trsm) or -1
     const int* soff;       // per row of a split task's block: shadow position - U position
     long long nshadow;
@@ -125,9 +125,7 @@ struct DevPlan {
     void* uval;            // factor values (double for IC_F64)
     int* indeg;
     int* items_left;
-    int2* queue;
-    int* qstamp;
-    int* counters;         // [0] queue head, [1] queue tail, [2] status bits, [3] abort
+    int* counters;         // [0] claim counter, [1] unused, [2] status bits, [3] abort
     long long* brk_row;    // smallest breakdown row
     int* diag;             // [0] items completed, [1] timeout site
     unsigned long long* trace;  // NULL, or 4 words per queue slot: start ns, end ns,
@@ -135,7 +133,6 @@ struct DevPlan {
     double* udiag;         // IC_F32: FP64 diagonal pivots (U_ii) of the factor
     double* urcp;          // FMA mode: 1/U_ii of every row, kept by its Chol for Trsm
     const int* diag_src;   // IC_F32: index of A's diagonal value of each row
-    int* epoch_dev;        // queue epoch, advanced on the device before each numeric phase
     void* shadow;          // finished rows of split Chol/Trsm tasks, else the sentinel
     int* row_next;         // per task: next target to claim (split Chol/Trsm)
 };
@@ -213,9 +210,9 @@ struct SolvePlan {
 };
 
 // Kernel entry points (numeric.cu, solve.cu).
-cudaError_t launch_numeric_prepare(const DevPlan& P, const double* avals, double shift_alpha,
-                                   int epoch, int dtype, cudaStream_t s);
-cudaError_t launch_numeric(const DevPlan& P, int epoch, int warps, bool exact, int dtype, int grid,
+cudaError_t launch_numeric_prepare(const DevPlan& P, const double* avals, double shift_alpha, int dtype,
+                                   cudaStream_t s);
+cudaError_t launch_numeric(const DevPlan& P, int warps, bool exact, int dtype, int grid,
                            unsigned long long timeout_ns, cudaStream_t s);
 cudaError_t numeric_blocks_per_sm(int warps, bool exact, int dtype, int* blocks);
 
@@ -304,6 +301,7 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
                int64_t nranges, int block_rows, int rows_per_item, int threads, bool k_order,
                HostPlan& P, std::string& err);
 void build_solve_dag(HostPlan& P, int threads);
+void build_claim_order(HostPlan& P, int nctas);
 int block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, std::vector<int4>& task,
               std::vector<int64_t>& pred_ptr, std::vector<int32_t>& pred);
 int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep, int32_t* perm,

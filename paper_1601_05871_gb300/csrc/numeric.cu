@@ -1,12 +1,15 @@
 // Numeric phase of IC(k) by blocks (Section 3.3) on sm_103a.
 //
-// One persistent kernel drains a device ready queue of work items.  A work item is a
-// block task of the Cholesky-by-blocks DAG (Chol, Trsm, Herk, Gemm), a chunk of a
-// Herk/Gemm task's target rows, or one of the CTAs that share a split Chol/Trsm task.
-// A task's in-degree counter is decremented by each finishing predecessor; the
-// predecessor that brings it to zero pushes the task's items onto the queue (the
-// scheduler duties of Section 2.2: track ready and waiting tasks, run ready ones,
-// release dependents on completion).
+// One persistent kernel runs every work item of the Cholesky-by-blocks DAG.  A work item
+// is a block task (Chol, Trsm, Herk, Gemm), a chunk of a Herk/Gemm task's target rows,
+// or one of the CTAs that share a split Chol/Trsm task.  The CTAs claim items in a
+// fixed order computed by the symbolic phase (a list schedule that runs first the ready
+// items whose tasks have the longest remaining path); a CTA waits (bounded) until the
+// claimed item's task has no unfinished predecessor, runs it, and the CTA that finishes
+// a task's last item decrements its successors' in-degree counters (the scheduler
+// duties of Section 2.2: track waiting tasks, run ready ones, release dependents on
+// completion).  Every item comes after all items of its predecessors in the order, so a
+// CTA only waits for items that running CTAs hold.
 //
 // Inside a task every target row r is owned by one warp (data parallelism within a
 // task, the remedy Section 6 plans for task granularity).  The warp stages the
@@ -514,10 +517,7 @@ static_assert(sizeof(Slot<double>) % 16 == 0 && sizeof(Slot<float>) % 16 == 0,
 
 template <int WARPS, bool EXACT, typename T>
 __global__ void __launch_bounds__(WARPS * 32)
-numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
-    // the queue's epoch lives on the device (advanced before every numeric phase), so a
-    // replayed CUDA graph never mistakes the previous run's slots for filled ones
-    const int epoch = *reinterpret_cast<const volatile int*>(P.epoch_dev);
+numeric_persistent(DevPlan P, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     unsigned char* s_done = smem_raw + kSmemHead;
@@ -533,9 +533,11 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
             int task = -1, chunk = 0;
             const int slot = atomicAdd(P.counters + 0, 1);
             if (slot < P.total_items) {
+                // the claimed item runs once its task's predecessors have all finished
+                const int2 it = __ldg(P.claim + slot);
                 unsigned spins = 0;
                 bool ok = true;
-                while (ld_volatile(P.qstamp + slot) != epoch) {
+                while (ld_volatile(P.indeg + it.x) != 0) {
                     if ((++spins & 63) == 0) {
                         if (ld_volatile(P.counters + 3)) { ok = false; break; }
                         if (gtimer() > deadline) { set_timeout(P, 1); ok = false; break; }
@@ -544,9 +546,8 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
                 }
                 if (ok) {
                     __threadfence();
-                    const volatile int* q = reinterpret_cast<const volatile int*>(P.queue + slot);
-                    task = q[0];
-                    chunk = q[1];
+                    task = it.x;
+                    chunk = it.y;
                 }
             }
             sm.task = task;
@@ -639,17 +640,7 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last) {
                 const int s0 = __ldg(P.succ_ptr + task), s1 = __ldg(P.succ_ptr + task + 1);
-                for (int e = s0 + lane; e < s1; e += 32) {
-                    const int s = __ldg(P.succ + e);
-                    if (atomicSub(P.indeg + s, 1) == 1) {
-                        const int ni = __ldg(P.nitems + s);
-                        const int base = atomicAdd(P.counters + 1, ni);
-                        for (int c = 0; c < ni; ++c) P.queue[base + c] = make_int2(s, c);
-                        __threadfence();
-                        for (int c = 0; c < ni; ++c)
-                            *reinterpret_cast<volatile int*>(P.qstamp + base + c) = epoch;
-                    }
-                }
+                for (int e = s0 + lane; e < s1; e += 32) atomicSub(P.indeg + __ldg(P.succ + e), 1);
             }
         }
     }
@@ -660,9 +651,7 @@ numeric_persistent(DevPlan P, int, unsigned long long timeout_ns) {
 // <= -2: the diagonal, whose index is -2 - gsrc.  With T = float the off-diagonal
 // values are rounded to FP32 and the diagonals go to the FP64 array udiag.
 template <typename T>
-__global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double alpha, int nnz_u,
-                                int) {
-    const int epoch = *reinterpret_cast<const volatile int*>(P.epoch_dev);
+__global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double alpha, int nnz_u) {
     constexpr bool MIXED = std::is_same<T, float>::value;
     const int stride = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -696,13 +685,9 @@ __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double
         unsigned long long* sh = static_cast<unsigned long long*>(P.shadow);
         for (long long i = tid; i < P.nshadow; i += stride) sh[i] = kSentinel64;
     }
-    for (int s = tid; s < P.nseeds; s += stride) {
-        P.queue[s] = __ldg(P.seeds + s);
-        P.qstamp[s] = epoch;
-    }
     if (tid == 0) {
         P.counters[0] = 0;
-        P.counters[1] = P.nseeds;
+        P.counters[1] = 0;
         P.counters[2] = 0;
         P.counters[3] = 0;
         *P.brk_row = 0x7fffffffffffffffLL;
@@ -711,14 +696,9 @@ __global__ void numeric_prepare(DevPlan P, const double* __restrict__ av, double
     }
 }
 
-// Starts a new queue epoch (stamps never repeat between numeric phases, whether issued
-// directly or replayed from a graph; stamps wrap after 2^31 phases).
-__global__ void advance_epoch(int* e) { *e = (*e == 0x7fffffff) ? 1 : *e + 1; }
-
 template <int WARPS, bool EXACT, typename T>
-cudaError_t launch_t(const DevPlan& P, int grid, int epoch, unsigned long long timeout_ns,
-                     cudaStream_t s) {
-    numeric_persistent<WARPS, EXACT, T><<<grid, WARPS * 32, smem_bytes<T>(WARPS), s>>>(P, epoch, timeout_ns);
+cudaError_t launch_t(const DevPlan& P, int grid, unsigned long long timeout_ns, cudaStream_t s) {
+    numeric_persistent<WARPS, EXACT, T><<<grid, WARPS * 32, smem_bytes<T>(WARPS), s>>>(P, timeout_ns);
     return cudaGetLastError();
 }
 
@@ -743,35 +723,32 @@ cudaError_t numeric_blocks_per_sm(int warps, bool exact, int dtype, int* blocks)
     return exact ? occupancy_t<16, true, double>(blocks) : occupancy_t<16, false, double>(blocks);
 }
 
-cudaError_t launch_numeric_prepare(const DevPlan& P, const double* avals, double shift_alpha,
-                                   int epoch, int dtype, cudaStream_t s) {
+cudaError_t launch_numeric_prepare(const DevPlan& P, const double* avals, double shift_alpha, int dtype,
+                                   cudaStream_t s) {
     const int work = P.nnz_u > P.ntasks ? P.nnz_u : P.ntasks;
     int pgrid = (work + 255) / 256;
     pgrid = pgrid < 1 ? 1 : (pgrid > 8192 ? 8192 : pgrid);
-    advance_epoch<<<1, 1, 0, s>>>(P.epoch_dev);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     if (dtype == IC_F32)
-        numeric_prepare<float><<<pgrid, 256, 0, s>>>(P, avals, shift_alpha, P.nnz_u, epoch);
+        numeric_prepare<float><<<pgrid, 256, 0, s>>>(P, avals, shift_alpha, P.nnz_u);
     else
-        numeric_prepare<double><<<pgrid, 256, 0, s>>>(P, avals, shift_alpha, P.nnz_u, epoch);
+        numeric_prepare<double><<<pgrid, 256, 0, s>>>(P, avals, shift_alpha, P.nnz_u);
     return cudaGetLastError();
 }
 
-cudaError_t launch_numeric(const DevPlan& P, int epoch, int warps, bool exact, int dtype, int grid,
+cudaError_t launch_numeric(const DevPlan& P, int warps, bool exact, int dtype, int grid,
                            unsigned long long timeout_ns, cudaStream_t s) {
     if (dtype == IC_F32)
-        return warps == 8 ? launch_t<8, false, float>(P, grid, epoch, timeout_ns, s)
-             : warps == 32 ? launch_t<32, false, float>(P, grid, epoch, timeout_ns, s)
-                           : launch_t<16, false, float>(P, grid, epoch, timeout_ns, s);
+        return warps == 8 ? launch_t<8, false, float>(P, grid, timeout_ns, s)
+             : warps == 32 ? launch_t<32, false, float>(P, grid, timeout_ns, s)
+                           : launch_t<16, false, float>(P, grid, timeout_ns, s);
     if (warps == 8)
-        return exact ? launch_t<8, true, double>(P, grid, epoch, timeout_ns, s)
-                     : launch_t<8, false, double>(P, grid, epoch, timeout_ns, s);
+        return exact ? launch_t<8, true, double>(P, grid, timeout_ns, s)
+                     : launch_t<8, false, double>(P, grid, timeout_ns, s);
     if (warps == 32)
-        return exact ? launch_t<32, true, double>(P, grid, epoch, timeout_ns, s)
-                     : launch_t<32, false, double>(P, grid, epoch, timeout_ns, s);
-    return exact ? launch_t<16, true, double>(P, grid, epoch, timeout_ns, s)
-                 : launch_t<16, false, double>(P, grid, epoch, timeout_ns, s);
+        return exact ? launch_t<32, true, double>(P, grid, timeout_ns, s)
+                     : launch_t<32, false, double>(P, grid, timeout_ns, s);
+    return exact ? launch_t<16, true, double>(P, grid, timeout_ns, s)
+                 : launch_t<16, false, double>(P, grid, timeout_ns, s);
 }
 
 }  // namespace ick

@@ -92,6 +92,7 @@ def load():
         "ic_get_solve_trace": (I, [P, I, P]),
         "ic_get_solve_entries": (I, [P, I, P, P, P]),
         "ic_get_split_layout": (I, [P, P, P, P, P]),
+        "ic_get_claim_order": (I, [P, P, P]),
         "ic_shift_features": (I, [P, P, D, P, P]),
         "ic_numeric_shifted": (I, [P, P, D, D, I, P, P, P]),
         "ic_mlp_n_params": (I, []),
@@ -386,6 +387,15 @@ def ic_get_solve_entries(h, backward=False):
     pos = np.empty(max(1, m), dtype=np.int32)
     _check(L.ic_get_solve_entries(h.ptr, int(bool(backward)), None, _p(j), _p(pos)))
     return {"ptr": ptr, "j": j[:m], "pos": pos[:m]}
+
+
+def ic_get_claim_order(h):
+    """(task, chunk) of every numeric work item, in the order the kernel's CTAs claim them."""
+    n = ic_stats(h)["nitems"]
+    task = np.empty(max(1, n), dtype=np.int32)
+    chunk = np.empty(max(1, n), dtype=np.int32)
+    _check(load().ic_get_claim_order(h.ptr, _p(task), _p(chunk)))
+    return task[:n], chunk[:n]
 
 
 def ic_get_split_layout(h):

@@ -525,3 +525,45 @@ def test_batch_plan_executes_bitwise_per_system(orc):
         upos = urp[lci + a] + np.array([np.searchsorted(ucol[urp[c + a]:urp[c + a + 1]], r + a)
                                         for r, c in zip(rws, lci)])
         assert np.array_equal(U[upos], o.values()), s
+
+
+@pytest.mark.parametrize("exact", [0, 1])
+def test_claim_order_covers_every_item_after_its_predecessors(orc, exact):
+    """The persistent numeric kernel's CTAs claim the work items in this order and wait
+    for each item's predecessors: every item must appear exactly once and after every
+    item of its task's predecessors (so a waiting CTA waits only for items held by
+    running CTAs).  Executing the tasks in the order their last items are claimed
+    reproduces the oracle (bit for bit in exact mode)."""
+    for prob, (perm, ranges), k in _cases(orc)[:4]:
+        h = ick.ic_symbolic(prob.rowptr, prob.colind, k, perm, ranges, block_rows=32, host_only=1, exact=exact)
+        st = ick.ic_stats(h)
+        d = ick.ic_get_tasks(h)
+        task, chunk = ick.ic_get_claim_order(h)
+        assert len(task) == st["nitems"]
+        nt = len(d["type"])
+        nitems = np.bincount(task, minlength=nt)
+        assert np.all(nitems >= 1)
+        pairs = set(zip(task.tolist(), chunk.tolist()))
+        assert len(pairs) == st["nitems"]
+        assert all(0 <= c < nitems[t] for t, c in pairs)
+        last = np.zeros(nt, dtype=np.int64)
+        firstpos = np.full(nt, -1, dtype=np.int64)
+        for q, t in enumerate(task):
+            last[t] = q
+            if firstpos[t] < 0:
+                firstpos[t] = q
+        pp, pr = d["pred_ptr"], d["pred"]
+        for t in range(nt):
+            for p in pr[pp[t]:pp[t + 1]]:
+                assert last[p] < firstpos[t], (t, p)
+        o = orc.OracleIC.from_problem(prob, perm, k)
+        assert o.numeric(prob.vals) == 0
+        lref = o.values()
+        lrp, lci, _ = o.pattern()
+        urp, ucol, U = _execute_plan(prob, perm, h, np.argsort(last))
+        rows = np.repeat(np.arange(prob.n), np.diff(lrp))
+        upos = urp[lci] + np.array([np.searchsorted(ucol[urp[c]:urp[c + 1]], r) for r, c in zip(rows, lci)])
+        if exact:
+            assert np.array_equal(U[upos], lref)
+        else:
+            assert np.abs(U[upos] - lref).max() <= 1e-12 * np.abs(prob.vals).max()
