@@ -54,18 +54,6 @@ __device__ __forceinline__ unsigned smid() {
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
-// 16-byte asynchronous copy global -> shared that is cached in L2 only (.cg), so it
-// never returns a stale L1 line of data another SM has rewritten.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
 
@@ -136,31 +124,14 @@ __device__ bool wait_row(const DevPlan& P, volatile unsigned char* done, int loc
     return true;
 }
 
-constexpr int kLenBits = 14;    // pivot descriptor: segment length in the low bits, then
-constexpr int kLenMask = (1 << kLenBits) - 1;  // the staged part's value and column chunk counts
-static_assert(kMaxBlockRows <= kLenMask, "a segment length must fit the descriptor");
 constexpr int kMapWords = 128;  // per-warp column map: 4096 column offsets
 constexpr int kMapBits = 32 * kMapWords;
-constexpr int kRing = 4;        // staging slots per warp: kRing - 1 pivots in flight
-constexpr int kSegStage = 64;   // source elements of one pivot staged by copies
-static_assert(kSegStage <= 64, "a staged segment is applied as two elements per lane");
 
-// One staged pivot segment: values and columns copied as the enclosing 16-byte
-// aligned spans, plus the 16 bytes holding U_pr when it lies outside the segment.
-template <typename T>
-struct Slot {
-    T vals[kSegStage + 16 / sizeof(T)];
-    T aval[16 / sizeof(T)];
-    int cols[kSegStage + 4];
-};
-
-// Per-warp shared-memory work area (16-byte multiples first for the async copies).
-// The target chunk's columns, offsets from its first column c_0, are a bit map with
-// the rank of each word's first bit: column c sits at slot
-// rank[w] + popc(bits[w] below bit b), w = (c - c_0) / 32, b = (c - c_0) % 32.
+// Per-warp shared-memory work area.  The target chunk's columns, offsets from its first
+// column c_0, are a bit map with the rank of each word's first bit: column c sits at
+// slot rank[w] + popc(bits[w] below bit b), w = (c - c_0) / 32, b = (c - c_0) % 32.
 template <typename T>
 struct WarpBuf {
-    Slot<T> ring[kRing];
     int4 piv[32];          // pivot row, position of U_pr, source segment start, length
     int psoff[32];         // split tasks: the pivot row's shadow offset
     double dacc;           // FP64 diagonal accumulator (T = float)
@@ -185,25 +156,6 @@ __device__ __forceinline__ void apply_one(WarpBuf<T>& W, int c, int c_0, unsigne
     if (idx >= 0) W.tval[idx] = sub_product<EXACT>(W.tval[idx], a, v);
 }
 
-// Elements lane and lane + 32 of a staged segment of n <= 64 elements: the two
-// lookups and loads overlap (the slots differ: a pivot row's columns are distinct).
-template <bool EXACT, typename T>
-__device__ __forceinline__ void apply_staged(WarpBuf<T>& W, const int* cols, const T* vals, int n,
-                                             int c_0, unsigned span, T a) {
-    const int lane = threadIdx.x & 31;
-    if (n <= 32) {  // most segments: one element per lane (n is the same for the warp)
-        const int i0 = lane < n ? find_col(W, cols[lane], c_0, span) : -1;
-        if (i0 >= 0) W.tval[i0] = sub_product<EXACT>(W.tval[i0], a, vals[lane]);
-        return;
-    }
-    const int i0 = lane < n ? find_col(W, cols[lane], c_0, span) : -1;
-    const int i1 = lane + 32 < n ? find_col(W, cols[lane + 32], c_0, span) : -1;
-    const T v0 = vals[lane], v1 = vals[lane + 32];
-    const T t0 = W.tval[max(i0, 0)], t1 = W.tval[max(i1, 0)];
-    if (i0 >= 0) W.tval[i0] = sub_product<EXACT>(t0, a, v0);
-    if (i1 >= 0) W.tval[i1] = sub_product<EXACT>(t1, a, v1);
-}
-
 // Split tasks publish finished rows in a shadow array that holds a signalling NaN
 // with a fixed payload until each value is written.  Arithmetic never produces that
 // bit pattern (a NaN result is the quiet canonical one), and an aligned 8- or 4-byte
@@ -221,38 +173,6 @@ __device__ __forceinline__ float ld_vol(const float* p) {
     return *reinterpret_cast<const volatile float*>(p);
 }
 
-// The n <= 64 staged values vals[0, n) of a split task's pivot segment, copied from
-// src: any still holding the sentinel are read again (bounded) until published.
-// False on timeout or abort.
-template <typename T>
-__device__ bool await_published(const DevPlan& P, T* vals, int n, const T* src,
-                                unsigned long long deadline) {
-    const int lane = threadIdx.x & 31;
-    const unsigned full = 0xffffffffu;
-    bool v0 = lane >= n || !is_sentinel(vals[lane]);
-    bool v1 = lane + 32 >= n || !is_sentinel(vals[lane + 32]);
-    unsigned spins = 0;
-    while (!__all_sync(full, v0 && v1)) {
-        if (!v0) {
-            const T t = ld_vol(src + lane);
-            if (!is_sentinel(t)) { vals[lane] = t; v0 = true; }
-        }
-        if (!v1) {
-            const T t = ld_vol(src + lane + 32);
-            if (!is_sentinel(t)) { vals[lane + 32] = t; v1 = true; }
-        }
-        int stop = 0;
-        if (lane == 0 && (++spins & 63) == 0) {
-            if (ld_volatile(P.counters + 3)) stop = 1;
-            else if (gtimer() > deadline) { set_timeout(P, 3); stop = 1; }
-        }
-        if (__shfl_sync(full, stop, 0)) return false;
-        __nanosleep(20);
-    }
-    __syncwarp();
-    return true;
-}
-
 // One published value of a split task's pivot row (per lane, bounded).
 template <typename T>
 __device__ T await_value(const DevPlan& P, const T* src, unsigned long long deadline) {
@@ -268,46 +188,86 @@ __device__ T await_value(const DevPlan& P, const T* src, unsigned long long dead
     }
 }
 
-// Issue the copies of pivot q's source segment into ring slot q % kRing.  Returns 1
-// when the slot will hold the data (or the segment is empty), 0 when the pivot row is
-// not complete yet (Chol/Trsm): then the consumer waits and loads it directly.  Bit q
-// of seen: pivot q's row was seen complete.  When pivot q has not been, the flags of
-// all the batch's pivots not seen yet are read again, one per lane, so that rows
-// completed meanwhile cost one round trip together, not one each.  SPLIT: no flags;
-// the values come from the published copy and are checked by the consumer.
+// One pivot in registers: lane l holds element l of the pivot row's source segment
+// (value v and column c), a the multiplier U_pr when it lies outside the segment, st 0
+// (empty segment), 1 (loaded) or 2 (the pivot row is not complete yet: it is waited for
+// and loaded when it is applied).
+template <typename T>
+struct PivReg {
+    T v, a;
+    int c, st;
+};
+
+// Load pivot j of the batch (W.piv) into R.  Chol/Trsm on one CTA: the pivot row's
+// completion flag must have been seen; when it has not, the flags of every pivot of the
+// batch not seen yet are read again (one per lane), so rows completed meanwhile cost
+// one round trip together.  SPLIT: the values come from the pivot rows' published
+// copies and are checked against the sentinel when applied.
 template <int MODE, bool SPLIT, typename T>
-__device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, const T* shadow, WarpBuf<T>& W,
-                                           int q, int nq, bool start_at_r, int rbase,
-                                           volatile unsigned char* done, unsigned& seen) {
-    constexpr int EPC = 16 / sizeof(T);  // elements per 16-byte chunk
+__device__ __forceinline__ void load_pivot(const DevPlan& P, const T* U, const T* shadow, const WarpBuf<T>& W,
+                                           int j, int nq, bool start_at_r, int rbase,
+                                           volatile unsigned char* done, unsigned& seen, PivReg<T>& R) {
+    const int lane = threadIdx.x & 31;
+    const int4 pi = W.piv[j];
+    const int len = pi.w;
+    R.st = 0;
+    if (len == 0) return;
+    if (!SPLIT && MODE != M_UPDATE && !((seen >> j) & 1u)) {
+        int dn = 1;
+        if (lane < nq && !((seen >> lane) & 1u)) dn = done[W.piv[lane].x - rbase];
+        const unsigned now = __ballot_sync(0xffffffffu, dn != 0);
+        if (now & ~seen) __threadfence_block();
+        seen |= now;
+        if (!((seen >> j) & 1u)) {
+            R.st = 2;
+            return;
+        }
+    }
+    const T* V = SPLIT ? shadow + W.psoff[j] : U;
+    R.v = lane < len ? ld_cg(V + pi.z + lane) : T(0);
+    R.c = lane < len ? __ldg(P.ucol + pi.z + lane) : 0;
+    R.a = start_at_r ? T(0) : ld_cg(U + pi.y);
+    R.st = 1;
+}
+
+// Apply pivot q (loaded in R) to the target chunk: U_rc -= U_pr * U_pc for the columns
+// c of the source segment that lie in the chunk, elements 0..31 from the registers and
+// any further ones loaded directly.  False when a wait gave up (timeout or abort).
+template <int MODE, bool EXACT, bool SPLIT, typename T>
+__device__ __forceinline__ bool apply_pivot(const DevPlan& P, const T* U, const T* shadow, WarpBuf<T>& W, int q,
+                                            bool start_at_r, int rbase, volatile unsigned char* done,
+                                            unsigned& seen, PivReg<T>& R, int c_0, unsigned span, bool dchunk,
+                                            unsigned long long deadline) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const int4 pi = W.piv[q];
-    if ((pi.w & kLenMask) == 0) return 1;
-    if (!SPLIT && MODE != M_UPDATE && !((seen >> q) & 1u)) {
-        int dn = 1;
-        if (lane < nq && !((seen >> lane) & 1u)) dn = done[W.piv[lane].x - rbase];
-        const unsigned now = __ballot_sync(full, dn != 0);
-        if (now & ~seen) __threadfence_block();
-        seen |= now;
-        if (!((seen >> q) & 1u)) return 0;
+    const int len = pi.w;
+    if (len > 0) {
+        if (R.st == 2) {  // the pivot row is waited for, then loaded
+            int ok = 1;
+            if (lane == 0) ok = wait_row(P, done, pi.x - rbase, deadline);
+            if (!__shfl_sync(full, ok, 0)) return false;
+            __threadfence_block();
+            seen |= 1u << q;
+            R.v = lane < len ? ld_cg(U + pi.z + lane) : T(0);
+            R.c = lane < len ? __ldg(P.ucol + pi.z + lane) : 0;
+            R.a = start_at_r ? T(0) : ld_cg(U + pi.y);
+        }
+        const T* V = SPLIT ? shadow + W.psoff[q] : U;
+        if (SPLIT && lane < len && is_sentinel(R.v)) R.v = await_value(P, V + pi.z + lane, deadline);
+        const T a = start_at_r ? __shfl_sync(full, R.v, 0) : R.a;
+        if (lane < len) {
+            const int idx = find_col(W, R.c, c_0, span);
+            if (idx >= 0) W.tval[idx] = sub_product<EXACT>(W.tval[idx], a, R.v);
+        }
+        for (int o = 32 + lane; o < len; o += 32) {
+            const T v = SPLIT ? await_value(P, V + pi.z + o, deadline) : ld_cg(U + pi.z + o);
+            apply_one<EXACT>(W, __ldg(P.ucol + pi.z + o), c_0, span, a, v);
+        }
+        if (dchunk && lane == 0) W.dacc = fma(-double(a), double(a), W.dacc);
     }
-    // split task: the values from the pivot row's published copy (checked on use)
-    const T* V = SPLIT ? shadow + W.psoff[q] : U;
-    Slot<T>& S = W.ring[q % kRing];
-    const int vb = pi.z & ~(EPC - 1), nv = (pi.w >> kLenBits) & 63;
-    const int cb = pi.z & ~3, nc = (pi.w >> (kLenBits + 6)) & 63;
-    const int total = nv + nc + (start_at_r ? 0 : 1);
-    for (int t = lane; t < total; t += 32) {
-        const bool isv = t < nv, isc = !isv && t < nv + nc;
-        const void* src = isv ? static_cast<const void*>(V + vb + EPC * t)
-                        : isc ? static_cast<const void*>(P.ucol + cb + 4 * (t - nv))
-                              : static_cast<const void*>(U + (pi.y & ~(EPC - 1)));
-        void* dst = isv ? static_cast<void*>(&S.vals[EPC * t])
-                  : isc ? static_cast<void*>(&S.cols[4 * (t - nv)]) : static_cast<void*>(&S.aval[0]);
-        cp_async16(dst, src);
-    }
-    return 1;
+    __syncwarp();
+    return true;
 }
 
 // One target row: r, pivots csc[ca, cb), target segment [tb, te) of row r.
@@ -320,15 +280,13 @@ __device__ __forceinline__ int issue_pivot(const DevPlan& P, const T* U, const T
 // The target segment is processed in chunks of at most kSegCap entries whose columns
 // lie within kMapBits of the chunk's first column, so that a column is found through
 // the chunk's bit map and word ranks with no probing.  Pivots are applied one at a
-// time in ascending order, lane l taking source elements l, l+32, ...  The source
-// segments of the next kRing-1 pivots are copied asynchronously into a ring of
-// shared-memory slots while the current one is applied.  For Chol and Trsm on one CTA
-// a copy is issued only once the pivot row's completion flag is seen; a pivot that was
-// not complete at issue time is waited for and loaded directly when its turn comes.
-// SPLIT (a Chol/Trsm task shared by several CTAs): there are no flags; the copies come
-// from the pivot rows' published copies (shadow, offsets soffs per row of the block),
-// every value is checked against the sentinel on use, and the finished row is
-// published in turn.
+// time in ascending order, lane l taking source elements l, l+32, ... straight from L2
+// (ld.cg) into registers.  For Chol and Trsm on one CTA a pivot is loaded
+// only once its row's completion flag is seen; a pivot whose row was not complete at
+// load time is waited for and loaded when its turn comes.  SPLIT (a Chol/Trsm task
+// shared by several CTAs): there are no flags; the values come from the pivot rows'
+// published copies (shadow, offsets soffs per row of the block), every value is checked
+// against the sentinel on use, and the finished row is published in turn.
 template <int MODE, bool EXACT, bool SPLIT, typename T>
 __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, int tb, int te,
                                int srcblk, bool start_at_r, int rbase,
@@ -336,7 +294,6 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                                unsigned long long deadline, const int* soffs = nullptr,
                                T* shadow = nullptr) {
     constexpr bool MIXED = std::is_same<T, float>::value;
-    constexpr int EPC = 16 / sizeof(T);
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     // Trsm: exact mode divides by the pivot itself (the operation of the definition);
@@ -390,11 +347,7 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                     sb = s.x;
                     len = s.y - s.x;
                 }
-                // copy counts of the staged part: 16-byte chunks of values and of columns
-                const int n = min(len, kSegStage);
-                const int nv = (((sb + n + EPC - 1) & ~(EPC - 1)) - (sb & ~(EPC - 1))) / EPC;
-                const int nc = (((sb + n + 3) & ~3) - (sb & ~3)) >> 2;
-                W.piv[lane] = make_int4(pe.x, pe.y, sb, len | (nv << kLenBits) | (nc << (kLenBits + 6)));
+                W.piv[lane] = make_int4(pe.x, pe.y, sb, len);
                 if (SPLIT) W.psoff[lane] = len > 0 ? __ldg(soffs + pe.x - rbase) : 0;
                 // one CTA's Chol/Trsm: the completion flags of the whole batch, one per lane
                 else if (MODE != M_UPDATE && len > 0) dn = done[pe.x - rbase];
@@ -402,60 +355,17 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
             unsigned seen = __ballot_sync(full, dn != 0);
             if (!SPLIT && MODE != M_UPDATE) __threadfence_block();
             __syncwarp();
-            unsigned issued = 0;
-#pragma unroll
-            for (int s = 0; s < kRing - 1; ++s) {
-                if (s < nq)
-                    issued |= unsigned(issue_pivot<MODE, SPLIT>(P, U, shadow, W, s, nq, start_at_r, rbase,
-                                                                done, seen)) << s;
-                cp_async_commit();
-            }
+            // each pivot is loaded when its turn comes (the other warps of the CTA cover
+            // the L2 latency; keeping the next pivot in registers meanwhile costs more
+            // registers than a 32-warp CTA has)
+            PivReg<T> cur;
+#pragma unroll 1
             for (int q = 0; q < nq; ++q) {
-                const int nxt = q + kRing - 1;
-                if (nxt < nq)
-                    issued |= unsigned(issue_pivot<MODE, SPLIT>(P, U, shadow, W, nxt, nq, start_at_r,
-                                                                rbase, done, seen)) << nxt;
-                cp_async_commit();
-                cp_async_wait<kRing - 1>();
-                __syncwarp();
-                const int4 pi = W.piv[q];
-                const int len = pi.w & kLenMask;
-                if (len > 0) {
-                    int first_direct = 0;
-                    T a;
-                    if ((issued >> q) & 1u) {
-                        Slot<T>& S = W.ring[q % kRing];
-                        const int n = min(len, kSegStage);
-                        const int vo = pi.z - (pi.z & ~(EPC - 1)), co = pi.z - (pi.z & ~3);
-                        if (SPLIT &&
-                            !await_published(P, S.vals + vo, n, shadow + W.psoff[q] + pi.z, deadline)) {
-                            cp_async_wait<0>();
-                            return;
-                        }
-                        a = start_at_r ? S.vals[vo] : S.aval[pi.y & (EPC - 1)];
-                        apply_staged<EXACT>(W, S.cols + co, S.vals + vo, n, c_0, span, a);
-                        first_direct = n;
-                    } else {
-                        int ok = 1;
-                        if (lane == 0) ok = wait_row(P, done, pi.x - rbase, deadline);
-                        if (!__shfl_sync(full, ok, 0)) {
-                            cp_async_wait<0>();
-                            return;
-                        }
-                        __threadfence_block();
-                        seen |= 1u << q;
-                        a = ld_cg(U + pi.y);
-                    }
-                    for (int o = first_direct + lane; o < len; o += 32) {
-                        const T v = SPLIT ? await_value(P, shadow + W.psoff[q] + pi.z + o, deadline)
-                                       : ld_cg(U + pi.z + o);
-                        apply_one<EXACT>(W, __ldg(P.ucol + pi.z + o), c_0, span, a, v);
-                    }
-                    if (dchunk && lane == 0) W.dacc = fma(-double(a), double(a), W.dacc);
-                }
-                __syncwarp();
+                load_pivot<MODE, SPLIT>(P, U, shadow, W, q, nq, start_at_r, rbase, done, seen, cur);
+                if (!apply_pivot<MODE, EXACT, SPLIT>(P, U, shadow, W, q, start_at_r, rbase, done, seen, cur, c_0,
+                                                     span, dchunk, deadline))
+                    return;
             }
-            cp_async_wait<0>();
             __syncwarp();
         }
         if (MODE == M_CHOL) {
@@ -512,8 +422,6 @@ __host__ __device__ constexpr size_t smem_bytes(int warps) {
     return kSmemHead + kMaxBlockRows + size_t(warps) * warp_bytes<T>();
 }
 static_assert((kSmemHead + kMaxBlockRows) % 16 == 0, "warp buffers must start 16-byte aligned");
-static_assert(sizeof(Slot<double>) % 16 == 0 && sizeof(Slot<float>) % 16 == 0,
-              "staging slots must be 16-byte multiples");
 
 template <int WARPS, bool EXACT, typename T>
 __global__ void __launch_bounds__(WARPS * 32)
