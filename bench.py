@@ -47,9 +47,9 @@ FP64_NOMINAL_GFLOPS = 1250.0  # GB300's nominal FP64 rate, used only if the prob
 SOLVE_TRAFFIC_PER_ENTRY = {(2, "forward_dag"): 14.80, (2, "backward_dag"): 15.01}
 # DRAM bytes (read + write) per factor entry of one launch of the numeric task kernel
 # of the 27-point IC(k) problem, by k: ncu captures of the 48^3, 64^3 and 80^3
-# problems gave 50.7, 59.5 and 56.6 bytes per entry; the 80^3 figure is scaled to the
+# problems gave 50.4, 57.7 and 54.9 bytes per entry; the 80^3 figure is scaled to the
 # factor at hand
-NUMERIC_TRAFFIC_PER_ENTRY = {2: 56.6}
+NUMERIC_TRAFFIC_PER_ENTRY = {2: 54.9}
 
 
 def parse():
