@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--solve-mode", type=int, default=0, choices=[0, 1],
                     help="triangular solves: 0 block-DAG, 1 row-level")
     ap.add_argument("--solve-lanes", type=int, default=0, help="lanes per row of the solves (0: default)")
+    ap.add_argument("--solve-ctas", type=int, default=0, help="CTAs per SM of the solves (0: default)")
     ap.add_argument("--shift", action="store_true",
                     help="learned-shift workload instead: Q1 elasticity, FP32 + learned shift vs plain FP64")
     ap.add_argument("--ne", type=int, default=48, help="elements per side of the --shift workload")
@@ -455,7 +456,8 @@ def main():
     prob = synth.laplace3d_27pt(a.side)
     perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.leaf_rows)
     h = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
-                        warps_per_cta=a.warps, solve_mode=a.solve_mode, solve_lanes=a.solve_lanes)
+                        warps_per_cta=a.warps, solve_mode=a.solve_mode, solve_lanes=a.solve_lanes,
+                        solve_ctas_per_sm=a.solve_ctas)
     st = ick.ic_stats(h)
     ick.ic_set_timing(h, True)
     stream = torch.cuda.current_stream()
@@ -615,7 +617,7 @@ def main():
     if not a.numeric_only and not a.no_f32:
         h32 = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
                               warps_per_cta=a.warps, dtype=ick.IC_F32, solve_mode=a.solve_mode,
-                              solve_lanes=a.solve_lanes)
+                              solve_lanes=a.solve_lanes, solve_ctas_per_sm=a.solve_ctas)
         ick.ic_set_timing(h32, True)
         x32 = torch.empty_like(x)
 
