@@ -214,13 +214,18 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
         if (lane == 0) ok = await_count(done, need, S.counter + 2, deadline);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
-        // two accumulators halve the dependent FMA chain (64 cycles per FP64 FMA)
+        // the source values first: M independent shared-memory loads issued together
+        // (an unused slot reads sh[0], which is never used), so their latency is paid
+        // once instead of once per entry; then the FMA chain, two accumulators
+        T sv[M];
+#pragma unroll
+        for (int x = 0; x < M; ++x) sv[x] = sh[j[x]];
         T acc0 = T(0), acc1 = T(0);
 #pragma unroll
         for (int x = 0; x < M; x += 2) {
             if (x >= most) break;
-            if (x < cnt) acc0 = fma(u[x], sh[j[x]], acc0);
-            if (x + 1 < cnt) acc1 = fma(u[x + 1], sh[j[x + 1]], acc1);
+            if (x < cnt) acc0 = fma(u[x], sv[x], acc0);
+            if (x + 1 < cnt) acc1 = fma(u[x + 1], sv[x + 1], acc1);
         }
         for (int q = a + sl + M * G; q < c; q += G) acc0 = fma(__ldg(xv + q), sh[__ldg(xj + q)], acc0);
         const T acc = sum_group<G>(acc0 + acc1);
