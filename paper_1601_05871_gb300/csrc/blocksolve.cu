@@ -61,20 +61,21 @@ __device__ bool await_zero(const int* c, int* abort_word, unsigned long long dea
     return true;
 }
 
-// Lane 0: wait until the range's count of completed rows reaches need (one shared
-// word, read by one lane per waiting warp); false on abort or timeout.
+// Whole warp: wait until the range's count of completed rows reaches need; false on
+// abort or timeout.  The count is one shared word that all lanes read in the same
+// load (a broadcast), so every lane sees the same values and takes the same branch:
+// no lane has to pass the outcome on to the others.
 __device__ bool await_count(const int* done, int need, int* abort_word, unsigned long long deadline) {
     const volatile int* p = done;
     unsigned spins = 0;
-    int d;
-    while ((d = *p) < need) {
+    while (*p < need) {
         if ((++spins & 255) == 0 && (aborted(abort_word) || gclock() > deadline)) {
-            raise_abort(abort_word);
+            if ((threadIdx.x & 31) == 0) raise_abort(abort_word);
             return false;
         }
-        (void)d;
     }
-    // acquire: pairs with the release of complete_rows, so the rows counted are visible
+    // acquire: pairs with the release-add of each completed row, so the rows counted
+    // are visible
     asm volatile("fence.acq_rel.cta;" ::: "memory");
     return true;
 }
@@ -98,16 +99,11 @@ struct Held {
     static constexpr int M = 64 / G;
 };
 
-// Marks the warp's rows complete: every lane's stores precede the count update (the
-// warp barrier orders them before lane 0's release-add, which publishes them to the
-// CTA's threads that acquire the count).
-__device__ __forceinline__ void complete_rows(int* done, unsigned rows_mask) {
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0 && rows_mask) {
-        const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(done));
-        asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(a), "r"(__popc(rows_mask))
-                     : "memory");
-    }
+// Marks one row complete, by the lane that stored its result: the release orders that
+// store before the count update, for the CTA's threads that acquire the count.
+__device__ __forceinline__ void complete_row(int* done) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(done));
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], 1;" ::"r"(a) : "memory");
 }
 
 // ------------------------------------------------------------------ forward tasks
@@ -208,12 +204,8 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
                 cnt = x + 1;
             }
         }
-        const unsigned rows = __ballot_sync(0xffffffffu, sl == 0 && i >= 0);
         const int most = __reduce_max_sync(0xffffffffu, cnt);
-        int ok = 1;
-        if (lane == 0) ok = await_count(done, need, S.counter + 2, deadline);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
+        if (!await_count(done, need, S.counter + 2, deadline)) break;
         // the source values first: M independent shared-memory loads issued together
         // (an unused slot reads sh[0], which is never used), so their latency is paid
         // once instead of once per entry; then the FMA chain, two accumulators
@@ -229,16 +221,13 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
         }
         for (int q = a + sl + M * G; q < c; q += G) acc0 = fma(__ldg(xv + q), sh[__ldg(xj + q)], acc0);
         const T acc = sum_group<G>(acc0 + acc1);
-        T v = T(0);
         if (sl == 0 && i >= 0) {
-            v = fma(-rd, acc, t);
+            const T v = fma(-rd, acc, t);
             sh[i - s] = v;
-        }
-        // the count is raised before the global stores, so its fence waits only for
-        // the shared-memory results; later tasks read the global copies after the
-        // task's closing fence
-        complete_rows(done, rows);
-        if (sl == 0 && i >= 0) {
+            // the count is raised before the global stores, so its release waits only
+            // for the shared-memory result; later tasks read the global copies after
+            // the task's closing fence
+            complete_row(done);
             out[i] = v;
             if (BW) z[dst] = double(v);
         }
