@@ -305,8 +305,11 @@ int upload_plan(ic_handle* h) {
     if ((st = h->upload(&S.f_next, P.fs.next))) return st;
     if ((st = h->upload(&S.b_next, P.bs.next))) return st;
     {
+        // forward external sums, then backward ones; a row without external entries in
+        // a direction is never written there and keeps the zero set here
         double* w = nullptr;
-        if ((st = h->alloc(&w, size_t(P.n)))) return st;
+        if ((st = h->alloc(&w, 2 * size_t(P.n)))) return st;
+        CK(cudaMemset(w, 0, 2 * size_t(P.n) * sizeof(double)));
         S.dag_w = w;
     }
     if ((st = h->alloc(&S.y, 2 * size_t(P.n)))) return st;  // forward and backward results

@@ -74,9 +74,12 @@ __device__ bool await_count(const int* done, int need, int* abort_word, unsigned
             return false;
         }
     }
-    // acquire: pairs with the release-add of each completed row, so the rows counted
-    // are visible
-    asm volatile("fence.acq_rel.cta;" ::: "memory");
+    // one acquire load of the count (lighter than a fence): it reads a value made by
+    // the chain of release-adds of the completed rows, so their results are visible
+    int v;
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(done));
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    (void)v;
     return true;
 }
 
@@ -131,68 +134,73 @@ __device__ void fwd_external(const SolvePlan& S, const T* __restrict__ uvt, cons
     }
 }
 
+// Thread 0 waits until task t's in-degree is zero, then the CTA synchronises; false
+// (in every thread) on abort or timeout.
+__device__ bool wait_ready(int t, const int* indeg, int* abort_word, unsigned long long deadline,
+                           unsigned long long* trace, int* s_ok) {
+    if (threadIdx.x == 0) {
+        const bool ok = await_zero(indeg + t, abort_word, deadline);
+        if (trace && ok) trace[4 * t + 1] = gclock();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
 // L of either direction: the rows at order positions [lo, hi) of range k (whole
 // levels), G lanes per row and 32/G rows per warp (one level per claim).  The range's
 // earlier results (positions before lo, finished by the range's previous parts) are
 // first loaded into shared memory and counted as complete; a row runs once every row
 // of the lower levels is complete (done >= need); its internal operands come from
-// shared memory and its other operands are loaded before the wait.
+// shared memory and its other operands are loaded before the wait.  For a task just
+// claimed (wait_t >= 0), each warp loads its first group's operands (factor values,
+// indices, the right-hand side: none is written by an earlier task) before waiting
+// for the task's in-degree, so the chain of dependent loads overlaps the wait; only
+// the external sum, written by the part's E tasks, is read after it.  Returns false
+// when that wait gave up.
 //   forward:  y_i = (r_perm(i) - w_i - sum) / U_ii, stored to y
 //   backward: z_i = (y_i - w_i - sum) / U_ii, stored to zv and to z at perm(i)
 template <int G, typename T, bool BW>
-__device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const T* __restrict__ rd_all,
+__device__ bool solve_local(const SolvePlan& S, const T* __restrict__ xv, const T* __restrict__ rd_all,
                             const double* __restrict__ r, const T* y, T* out, double* __restrict__ z, const T* w,
-                            int k, int lo, int hi, T* sh, int* done, bool cont,
-                            unsigned long long deadline) {
+                            int k, int lo, int hi, T* sh, int* done, bool cont, int wait_t, const int* indeg,
+                            unsigned long long deadline, int* s_ok) {
     constexpr int R = 32 / G, M = Held<G>::M;
     const int lane = threadIdx.x & 31, sl = lane % G;
     const int* ord = BW ? S.lb_ord : S.lf_ord;
     const int* need_a = BW ? S.lb_need : S.lf_need;
     const int* xptr = BW ? S.xb_ptr : S.xf_ptr;
     const int* xj = BW ? S.xb_j : S.xf_j;
-    const int base = __ldg((BW ? S.lb_ptr : S.lf_ptr) + k);
-    const int s = __ldg(S.ranges + k);
-    if (!cont) {  // a continuation already holds the range's earlier results and count
-        for (int q = base + int(threadIdx.x); q < lo; q += blockDim.x) {
-            const int i = __ldg(ord + q);
-            if (i >= 0) sh[i - s] = ldcg(out + i);
-        }
-        if (threadIdx.x == 0) *done = lo > base ? __ldg(need_a + lo) : 0;
-        __syncthreads();
-    }
     const int len = hi - lo;
-    // group g of R positions goes to warp g mod (warps): the groups of one level sit on
-    // consecutive warps, i.e. on different SM sub-partitions, whose FP64 units then
-    // work in parallel; each warp takes its groups in order, and a group depends only
-    // on lower groups, so the waits cannot cycle
-    const int nw = blockDim.x >> 5;
-    for (int t0 = (threadIdx.x >> 5) * R;; t0 += nw * R) {
-        if (t0 >= len) break;
-        const int i = __ldg(ord + lo + t0 + lane / G);
-        const int need = __ldg(need_a + lo + t0);
-        T t = T(0), rd = T(0);
-        int a = 0, c = 0, dst = 0;
+    // the warp's current group: row, rows of lower levels it waits for, entry range,
+    // permutation entry, reciprocal pivot, right-hand side and its first 64 internal
+    // entries (64 / G per lane)
+    int i = -1, need = 0, a = 0, c = 0, dst = 0, cnt = 0, most = 0;
+    T t = T(0), rd = T(0);
+    int j[M];
+    T u[M];
+    auto load = [&](int t0) {
+        i = __ldg(ord + lo + t0 + lane / G);
+        need = __ldg(need_a + lo + t0);
+        t = T(0);
+        rd = T(0);
+        a = 0;
+        c = 0;
+        dst = 0;
         if (i >= 0) {
             a = __ldg(xptr + i);
             c = __ldg(xptr + i + 1);
             if (sl == 0) {
                 rd = __ldg(rd_all + i);
-                bool ext;
                 if (BW) {
                     t = ldcg(y + i);
                     dst = __ldg(S.perm + i);
-                    ext = __ldg(S.sb_nint + i) < int(__ldg(S.urp + i + 1) - __ldg(S.urp + i)) - 1;
                 } else {
                     t = T(__ldg(r + __ldg(S.perm + i)));
-                    ext = __ldg(S.cptr + i) < __ldg(S.sf_split + i);
                 }
-                if (ext) t -= ldcg(w + i);
-                t *= rd;  // the row's result is t - rd * (sum of the internal products)
             }
         }
-        int j[M];
-        T u[M];
-        int cnt = 0;
+        cnt = 0;
 #pragma unroll
         for (int x = 0; x < M; ++x) {
             const int q = a + sl + x * G;
@@ -204,25 +212,58 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
                 cnt = x + 1;
             }
         }
-        const int most = __reduce_max_sync(0xffffffffu, cnt);
+        most = __reduce_max_sync(0xffffffffu, cnt);
+    };
+    // group g of R positions goes to warp g mod (warps): the groups of one level sit on
+    // consecutive warps, i.e. on different SM sub-partitions, whose FP64 units then
+    // work in parallel; each warp takes its groups in order, and a group depends only
+    // on lower groups, so the waits cannot cycle
+    const int nw = blockDim.x >> 5;
+    const int first = (threadIdx.x >> 5) * R;
+    if (first < len) load(first);
+    if (wait_t >= 0 && !wait_ready(wait_t, indeg, S.counter + 2, deadline, BW && S.trace ? S.trace + 4 * size_t(S.nftask) : S.trace, s_ok))
+        return false;
+    const int base = __ldg((BW ? S.lb_ptr : S.lf_ptr) + k);
+    const int s = __ldg(S.ranges + k);
+    if (!cont) {  // a continuation already holds the range's earlier results and count
+        for (int q = base + int(threadIdx.x); q < lo; q += blockDim.x) {
+            const int ii = __ldg(ord + q);
+            if (ii >= 0) sh[ii - s] = ldcg(out + ii);
+        }
+        if (threadIdx.x == 0) *done = lo > base ? __ldg(need_a + lo) : 0;
+        __syncthreads();
+    }
+    for (int t0 = first; t0 < len; t0 += nw * R) {
+        if (t0 != first) load(t0);
+        // the row's result is t - rd * (sum of the internal products); a row without
+        // external entries keeps w = 0 (never written), which leaves t unchanged
+        if (i >= 0 && sl == 0) t = (t - ldcg(w + i)) * rd;
         if (!await_count(done, need, S.counter + 2, deadline)) break;
         // the source values first: M independent shared-memory loads issued together
         // (an unused slot reads sh[0], which is never used), so their latency is paid
-        // once instead of once per entry; then the FMA chain, two accumulators
+        // once instead of once per entry; then the FMA chain over interleaved
+        // accumulators: two in FP64, whose FMAs issue about 64 cycles apart in a warp
+        // anyway (more would only add the additions that combine them), four in FP32
+        constexpr int NA = sizeof(T) == 4 ? 4 : 2;
         T sv[M];
 #pragma unroll
         for (int x = 0; x < M; ++x) sv[x] = sh[j[x]];
-        T acc0 = T(0), acc1 = T(0);
+        T acc[NA];
 #pragma unroll
-        for (int x = 0; x < M; x += 2) {
+        for (int yy = 0; yy < NA; ++yy) acc[yy] = T(0);
+#pragma unroll
+        for (int x = 0; x < M; x += NA) {
             if (x >= most) break;
-            if (x < cnt) acc0 = fma(u[x], sv[x], acc0);
-            if (x + 1 < cnt) acc1 = fma(u[x + 1], sv[x + 1], acc1);
+#pragma unroll
+            for (int yy = 0; yy < NA; ++yy)
+                if (x + yy < M && x + yy < cnt) acc[yy] = fma(u[x + yy], sv[x + yy], acc[yy]);
         }
-        for (int q = a + sl + M * G; q < c; q += G) acc0 = fma(__ldg(xv + q), sh[__ldg(xj + q)], acc0);
-        const T acc = sum_group<G>(acc0 + acc1);
+        for (int q = a + sl + M * G; q < c; q += G) acc[0] = fma(__ldg(xv + q), sh[__ldg(xj + q)], acc[0]);
+        T tot = acc[0] + acc[1];
+        if constexpr (NA == 4) tot = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        const T accs = sum_group<G>(tot);
         if (sl == 0 && i >= 0) {
-            const T v = fma(-rd, acc, t);
+            const T v = fma(-rd, accs, t);
             sh[i - s] = v;
             // the count is raised before the global stores, so its release waits only
             // for the shared-memory result; later tasks read the global copies after
@@ -232,6 +273,7 @@ __device__ void solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
             if (BW) z[dst] = double(v);
         }
     }
+    return true;
 }
 
 // ----------------------------------------------------------------- backward tasks
@@ -266,10 +308,9 @@ __device__ __forceinline__ unsigned smid() {
     return r;
 }
 
-// Claims the next task; thread 0 waits until its in-degree is zero.  Returns the task
-// index, or -1 when the list is exhausted or the solve was aborted.
-__device__ int claim_task(int* claim_ctr, int ntasks, const int* indeg, int* taken, int* abort_word,
-                          unsigned long long deadline, int* s_task, int* s_done,
+// Claims the next task (its in-degree is awaited by the task itself, with wait_ready).
+// Returns the task index, or -1 when the list is exhausted or the solve was aborted.
+__device__ int claim_task(int* claim_ctr, int ntasks, int* taken, int* abort_word, int* s_task,
                           unsigned long long* trace) {
     if (threadIdx.x == 0) {
         int t = -1;
@@ -279,18 +320,12 @@ __device__ int claim_task(int* claim_ctr, int ntasks, const int* indeg, int* tak
             } while (t < ntasks && atomicExch(taken + t, 1) != 0);
             if (t >= ntasks) {
                 t = -1;
-            } else {
-                const unsigned long long t0 = gclock();
-                if (!await_zero(indeg + t, abort_word, deadline)) t = -1;
-                if (trace && t >= 0) {
-                    trace[4 * t] = t0;
-                    trace[4 * t + 1] = gclock();
-                    trace[4 * t + 3] = (unsigned long long)t | ((unsigned long long)smid() << 32);
-                }
+            } else if (trace) {
+                trace[4 * t] = gclock();
+                trace[4 * t + 3] = (unsigned long long)t | ((unsigned long long)smid() << 32);
             }
         }
         *s_task = t;
-        *s_done = 0;
     }
     __syncthreads();
     return *s_task;
@@ -332,7 +367,7 @@ forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all
             T* y, T* w, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_task, s_done;
+    __shared__ int s_task, s_done, s_ok;
     const unsigned long long deadline = gclock() + timeout_ns;
     int* indeg = S.dag_indeg;
     int* taken = S.dag_taken;
@@ -340,17 +375,19 @@ forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all
     bool cont = false;
     for (;;) {
         if (t < 0) {
-            t = claim_task(S.counter + 0, S.nftask, indeg, taken, S.counter + 2, deadline, &s_task, &s_done,
-                           S.trace);
+            t = claim_task(S.counter + 0, S.nftask, taken, S.counter + 2, &s_task, S.trace);
             cont = false;
         }
         if (t < 0) break;
         const int4 tk = S.ftask[t];
-        if (tk.x == 0)
+        if (tk.x == 0) {
+            if (!wait_ready(t, indeg, S.counter + 2, deadline, S.trace, &s_ok)) break;
             fwd_external<G, T>(S, uvt, y, w, tk.z, tk.w);
-        else
-            solve_local<G, T, false>(S, static_cast<const T*>(S.xf_val), rd_all, r, nullptr, y, nullptr, w, tk.y,
-                                     tk.z, tk.w, sh, &s_done, cont, deadline);
+        } else if (!solve_local<G, T, false>(S, static_cast<const T*>(S.xf_val), rd_all, r, nullptr, y, nullptr, w,
+                                             tk.y, tk.z, tk.w, sh, &s_done, cont, cont ? -1 : t, indeg, deadline,
+                                             &s_ok)) {
+            break;
+        }
         t = release(t, tk.x == 1, S.f_succ_ptr, S.f_succ, S.f_next, indeg, taken, S.trace, &s_task);
         cont = t >= 0;
     }
@@ -362,7 +399,7 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
              double* __restrict__ z, T* w, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_task, s_done;
+    __shared__ int s_task, s_done, s_ok;
     const unsigned long long deadline = gclock() + timeout_ns;
     int* indeg = S.dag_indeg + S.nftask;
     int* taken = S.dag_taken + S.nftask;
@@ -371,16 +408,18 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
     bool cont = false;
     for (;;) {
         if (t < 0) {
-            t = claim_task(S.counter + 1, S.nbtask, indeg, taken, S.counter + 2, deadline, &s_task, &s_done, tr);
+            t = claim_task(S.counter + 1, S.nbtask, taken, S.counter + 2, &s_task, tr);
             cont = false;
         }
         if (t < 0) break;
         const int4 tk = S.btask[t];
-        if (tk.x == 0)
+        if (tk.x == 0) {
+            if (!wait_ready(t, indeg, S.counter + 2, deadline, tr, &s_ok)) break;
             bwd_external<G, T>(S, uv, zv, w, tk.z, tk.w);
-        else
-            solve_local<G, T, true>(S, static_cast<const T*>(S.xb_val), rd_all, nullptr, y, zv, z, w, tk.y, tk.z,
-                                    tk.w, sh, &s_done, cont, deadline);
+        } else if (!solve_local<G, T, true>(S, static_cast<const T*>(S.xb_val), rd_all, nullptr, y, zv, z, w, tk.y,
+                                            tk.z, tk.w, sh, &s_done, cont, cont ? -1 : t, indeg, deadline, &s_ok)) {
+            break;
+        }
         t = release(t, tk.x == 1, S.b_succ_ptr, S.b_succ, S.b_next, indeg, taken, tr, &s_task);
         cont = t >= 0;
     }
@@ -408,7 +447,7 @@ void launch_dag(const SolvePlan& S, const T* uv, const T* rd, const double* r, d
                 size_t smem, unsigned long long timeout_ns, cudaStream_t s, cudaEvent_t t1) {
     forward_dag<G, T><<<grid, kDagThreads, smem, s>>>(S, static_cast<const T*>(S.uvt), rd, r, y, w, timeout_ns);
     if (t1) cudaEventRecord(t1, s);
-    backward_dag<G, T><<<grid, kDagThreads, smem, s>>>(S, uv, rd, y, y + S.n, z, w, timeout_ns);
+    backward_dag<G, T><<<grid, kDagThreads, smem, s>>>(S, uv, rd, y, y + S.n, z, w + S.n, timeout_ns);
 }
 
 template <typename T>

@@ -205,7 +205,8 @@ struct SolvePlan {
     const int* f_next;     // per task: the same range's next L part, or -1
     const int* b_next;
     int* dag_taken;        // per task (forward then backward): 1 once a CTA has taken it
-    void* dag_w;           // external sums of the rows (n values of the solve type)
+    void* dag_w;           // external sums of the rows, n values of the solve type per
+                           // direction (forward, then backward); 0 where a row has none
     unsigned long long* trace;  // NULL, or 4 words per task: forward tasks, then backward
 };
 
