@@ -453,9 +453,19 @@ static int symbolic_impl(const ic_csr_pattern* A, int k, const int32_t* perm, co
             delete h;
             return fail(IC_ERR_ARG, "rows_per_item / timeout_s / solve_lanes / solve_mode out of range");
         }
+        // the solves' grid as upload_plan will size it (SMs of the current device, or
+        // kHostOnlyCtas for a host-only handle, times the CTAs per SM asked for)
+        int sms = kHostOnlyCtas;
+        if (!h->opts.host_only) {
+            int dev = 0, cnt = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&cnt, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && cnt > 0)
+                sms = cnt;
+        }
         std::string err;
         int st = build_plan(A, k, perm, ranges, nranges, h->opts.block_rows, h->opts.rows_per_item,
-                            h->opts.threads, h->opts.exact != 0, h->hp, err);
+                            h->opts.threads, h->opts.exact != 0, sms * std::max(1, h->opts.solve_ctas_per_sm),
+                            h->hp, err);
         if (st) {
             delete h;
             return fail(st, err);

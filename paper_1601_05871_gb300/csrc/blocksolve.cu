@@ -331,31 +331,36 @@ __device__ int claim_task(int* claim_ctr, int ntasks, int* taken, int* abort_wor
     return *s_task;
 }
 
-// After a task: its results are made visible, then its successors are released.  If
-// the task was an L part whose range's next part is now ready and not yet taken, the
-// CTA takes it (returned; -1 otherwise) and runs it with the shared-memory state it
-// already holds.
+// After a task: its results are made visible, then its successors are released, by
+// all threads of the CTA at once (a separator's part can have a hundred successors,
+// and released one after another they would wait a memory round trip each).  If the
+// task was an L part whose range's next part is now ready and not yet taken, the CTA
+// takes it (returned; -1 otherwise) and runs it with the shared-memory state it
+// already holds: the thread whose decrement made that part's in-degree zero takes it.
 __device__ __forceinline__ int release(int t, bool is_l, const int* succ_ptr, const int* succ, const int* next,
                                        int* indeg, int* taken, unsigned long long* trace, int* s_task) {
     __threadfence();
-    __syncthreads();
     if (threadIdx.x == 0) {
         if (trace) trace[4 * t + 2] = gclock();
-        const int a = __ldg(succ_ptr + t), b = __ldg(succ_ptr + t + 1);
-        for (int q = a; q < b; ++q) atomicSub(indeg + __ldg(succ + q), 1);
-        int nx = is_l ? __ldg(next + t) : -1;
-        if (nx >= 0 && !(*reinterpret_cast<volatile int*>(indeg + nx) == 0 && atomicExch(taken + nx, 1) == 0))
-            nx = -1;
-        if (nx >= 0) {
-            __threadfence();
+        *s_task = -1;
+    }
+    __syncthreads();
+    const int a = __ldg(succ_ptr + t), b = __ldg(succ_ptr + t + 1);
+    const int nx = is_l ? __ldg(next + t) : -1;
+    for (int q = a + int(threadIdx.x); q < b; q += blockDim.x) {
+        const int sx = __ldg(succ + q);
+        if (sx != nx) {
+            atomicSub(indeg + sx, 1);
+        } else if (atomicSub(indeg + sx, 1) == 1 && atomicExch(taken + sx, 1) == 0) {
+            __threadfence();  // acquire: the part's other inputs are visible to this CTA
             if (trace) {
                 const unsigned long long now = gclock();
-                trace[4 * nx] = now;
-                trace[4 * nx + 1] = now;
-                trace[4 * nx + 3] = (unsigned long long)nx | ((unsigned long long)smid() << 32);
+                trace[4 * sx] = now;
+                trace[4 * sx + 1] = now;
+                trace[4 * sx + 3] = (unsigned long long)sx | ((unsigned long long)smid() << 32);
             }
+            *s_task = sx;
         }
-        *s_task = nx;
     }
     __syncthreads();
     return *s_task;

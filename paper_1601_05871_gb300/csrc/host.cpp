@@ -395,7 +395,7 @@ void split_tail_tasks(HostPlan& P, const std::vector<std::vector<int4>>& ttgt,
 
 int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
                int64_t nranges, int block_rows, int rows_per_item, int threads, bool k_order,
-               HostPlan& P, std::string& err) {
+               int solve_ctas, HostPlan& P, std::string& err) {
     if (!A) { err = "NULL pattern"; return IC_ERR_ARG; }
     if (k < 0) { err = "k < 0"; return IC_ERR_ARG; }
     if (block_rows <= 0 || block_rows > kMaxBlockRows) { err = "block_rows out of range"; return IC_ERR_ARG; }
@@ -819,7 +819,7 @@ int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_
     // write L (values and column indices) and its row pointers
     const double nnz_low = double(P.nnz_a + n) / 2.0;
     P.bytes = nnz_low * (8 + 4) + double(P.nnz_u) * (8 + 4) + double(n + 1) * 8;
-    build_solve_dag(P, nthr);
+    build_solve_dag(P, nthr, solve_ctas);
     return IC_OK;
 }
 

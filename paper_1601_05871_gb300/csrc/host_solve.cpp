@@ -14,12 +14,14 @@
 // last ones.  The backward solve L^T z = y is the mirror image (external = entries of
 // row i in a later range).  Nested-dissection leaves have no external entries in the
 // forward solve: each is one L task and they start at once.  Tasks are claimed in a
-// fixed order: ascending start time of an as-soon-as-possible schedule under a simple
-// cost model, which is a topological order of the task DAG.
+// fixed order: the order in which a list schedule of the task DAG on the solve grid's
+// CTAs, under a simple cost model, starts them (a free CTA takes the ready task with
+// the longest remaining path), which is a topological order of the task DAG.
 #include <omp.h>
 
 #include <algorithm>
 #include <numeric>
+#include <queue>
 
 #include "ick_internal.h"
 
@@ -87,7 +89,7 @@ void internal_layout(const HostPlan& P, Count count_of_row, Src src_pos, SolveLa
 
 }  // namespace
 
-void build_solve_dag(HostPlan& P, int nthr) {
+void build_solve_dag(HostPlan& P, int nthr, int ctas) {
     const int64_t n = P.n;
     const int32_t nb = int32_t(P.ranges.size()) - 1;
     P.sf_split.assign(n, 0);
@@ -156,8 +158,8 @@ void build_solve_dag(HostPlan& P, int nthr) {
     // (one L task each, after the previous part); each part's external sums form E
     // tasks (chunks of at most kChunkEntries entries / kChunkRows order positions) that
     // depend on the L tasks holding their source rows.  A range without external
-    // entries is one L task.  Claim order: ascending start of an as-soon-as-possible
-    // schedule under the cost model (a topological order).
+    // entries is one L task.  Claim order: the start order of a list schedule on ctas
+    // CTAs under the cost model (a topological order).
     auto build = [&](bool fwd, SolveTasks& out) {
         struct Tk {
             double start, cost;
@@ -238,14 +240,65 @@ void build_solve_dag(HostPlan& P, int nthr) {
                 lo = hi;
             }
         }
-        // claim order: ascending start; at equal start, the longer task first
+        // claim order: a list schedule of the tasks on the grid's CTAs under the cost
+        // model.  A free CTA takes the ready task with the longest path to the end of
+        // the solve (bottom level); when an L part ends and the range's next part is
+        // ready, the same CTA goes on with it, as the kernel does.  The order in which
+        // tasks start is the claim order (topological: a task starts only when ready).
         const size_t nt = tk.size();
-        std::vector<int32_t> idx(nt), pos(nt);
-        std::iota(idx.begin(), idx.end(), 0);
-        std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
-            if (tk[x].start != tk[y].start) return tk[x].start < tk[y].start;
-            return tk[x].cost > tk[y].cost;
-        });
+        std::vector<std::vector<int32_t>> succs(nt);
+        std::vector<int32_t> deg(nt, 0), nextg(nt, -1);
+        for (size_t q = 0; q < nt; ++q) {
+            deg[q] = int32_t(tk[q].preds.size());
+            for (int32_t pr : tk[q].preds) {
+                succs[pr].push_back(int32_t(q));
+                if (tk[q].t.x == 1 && tk[pr].t.x == 1) nextg[pr] = int32_t(q);
+            }
+        }
+        std::vector<double> bottom(nt, 0.0);  // tasks are generated after their predecessors
+        for (size_t q = nt; q-- > 0;) {
+            double m = 0.0;
+            for (int32_t s2 : succs[q]) m = std::max(m, bottom[s2]);
+            bottom[q] = tk[q].cost + m;
+        }
+        using Entry = std::pair<double, int32_t>;
+        std::priority_queue<Entry> ready;  // (bottom level, task): largest first
+        std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> running;  // (finish, task)
+        std::vector<uint8_t> started(nt, 0);
+        std::vector<int32_t> idx, pos(nt);
+        idx.reserve(nt);
+        for (size_t q = 0; q < nt; ++q)
+            if (deg[q] == 0) ready.push({bottom[q], int32_t(q)});
+        int free_ctas = std::max(1, ctas);
+        double now = 0.0;
+        auto start = [&](int32_t q) {
+            started[q] = 1;
+            idx.push_back(q);
+            running.push({now + tk[q].cost, q});
+        };
+        while (idx.size() < nt) {
+            while (free_ctas > 0 && !ready.empty()) {
+                const int32_t q = ready.top().second;
+                ready.pop();
+                if (started[q]) continue;  // already taken as a continuation
+                start(q);
+                --free_ctas;
+            }
+            if (running.empty()) break;  // not reached: the task graph is acyclic
+            const Entry ev = running.top();
+            running.pop();
+            now = ev.first;
+            ++free_ctas;
+            for (int32_t s2 : succs[ev.second])
+                if (--deg[s2] == 0) ready.push({bottom[s2], s2});
+            const int32_t nx = nextg[ev.second];
+            if (nx >= 0 && deg[nx] == 0 && !started[nx]) {
+                start(nx);
+                --free_ctas;
+            }
+        }
+        for (size_t q = 0; q < nt; ++q)  // not reached either: every task has started
+            if (!started[q]) idx.push_back(int32_t(q));
         for (size_t q = 0; q < nt; ++q) pos[idx[q]] = int32_t(q);
         out.task.resize(nt);
         out.indeg0.assign(nt, 0);

@@ -298,10 +298,11 @@ cudaError_t measure_fma_peak(int dtype, double* gflops, cudaStream_t s);
 // Host symbolic phase (host.cpp).
 // k_order: updates into each block applied in ascending k (the task generator's order,
 // which exact mode needs); otherwise ordered by the estimated readiness of their inputs.
+// solve_ctas: the CTAs of the block-DAG solves' grid, for their claim order's schedule.
 int build_plan(const ic_csr_pattern* A, int k, const int32_t* perm, const int64_t* ranges,
                int64_t nranges, int block_rows, int rows_per_item, int threads, bool k_order,
-               HostPlan& P, std::string& err);
-void build_solve_dag(HostPlan& P, int threads);
+               int solve_ctas, HostPlan& P, std::string& err);
+void build_solve_dag(HostPlan& P, int threads, int ctas);
 void build_claim_order(HostPlan& P, int nctas);
 int block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, std::vector<int4>& task,
               std::vector<int64_t>& pred_ptr, std::vector<int32_t>& pred);
