@@ -7,11 +7,14 @@ Workload (default): 27-point constant-coefficient Laplacian on a 96^3 grid
 (884,736 rows, 23,393,656 nonzeros), geometric nested dissection, 2D blocks of at
 most 4096 rows, IC(2), FP64, b ~ N(0,1), PCG to relative residual 1e-10.
 
-A step is one numeric factorization plus one PCG solve.  value = algorithmic factor
-flops / factor time (GFLOP/s, the time of the two numeric kernels measured with CUDA
-events on the launching stream).  e2e repeats the step through the C ABI from pinned
-host buffers, with the host-to-device copies of A's values and b and the
-device-to-host copy of x inside the timed region.
+A step is one numeric factorization plus one PCG solve, which runs as one CUDA graph
+(the library's loop on the device).  value = algorithmic factor flops / factor time
+(GFLOP/s, the time of the factorization's kernels, CUDA events recorded on the
+launching stream before and after them).  The per-kernel times of the roofline
+objects come from a pass of three more steps with the library's own CUDA events
+around every kernel (PCG then loops on the host).  e2e repeats the step through the C
+ABI from pinned host buffers, with the host-to-device copies of A's values and b and
+the device-to-host copy of x inside the timed region.
 
 With one GPU the line also carries, outside the timed region, the other workloads of
 the method (each with a few fixed repetitions): c4_shift (Q1 elasticity, FP32 +
@@ -50,6 +53,35 @@ SOLVE_TRAFFIC_PER_ENTRY = {(2, "forward_dag"): 14.76, (2, "backward_dag"): 14.97
 # problems gave 50.4, 57.7 and 54.9 bytes per entry; the 80^3 figure is scaled to the
 # factor at hand
 NUMERIC_TRAFFIC_PER_ENTRY = {2: 54.9}
+
+
+def timed_solve(ick, torch, h, av, b, x, tol, stream=None):
+    """One factorization and PCG solve with the library's per-kernel timing off, so that
+    pcg_solve runs as one graph (its loop on the device).  Returns the CUDA events
+    recorded on the stream before and after the factorization and after the solve,
+    the iterations and the residual; the factorization's status is checked."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    ick.ic_numeric_async(h, av, stream)
+    ev[1].record(stream)
+    it, rel = ick.pcg_solve(h, av, b, x, tol, 5000, stream)
+    ev[2].record(stream)
+    ick.ic_numeric_status(h)
+    return ev, it, rel
+
+
+def factor_kernel_ms(ick, h, av, stream=None, reps=3):
+    """Mean time of the factorization's own kernels (value scatter + task-DAG kernel),
+    from the library's CUDA events around them: reps factorizations with the
+    library's per-kernel timing on (switched off again afterwards)."""
+    ick.ic_set_timing(h, True)
+    t = []
+    for _ in range(reps):
+        ick.ic_numeric(h, av, stream)
+        tm = ick.ic_get_timing(h)
+        t.append(tm["prepare_ms"] + tm["numeric_ms"])
+    ick.ic_set_timing(h, False)
+    return sum(t) / len(t)
 
 
 def parse():
@@ -370,24 +402,16 @@ def c5_workload(a, side, warmup, steps, densities=True):
         h = ick.ic_symbolic(p.rowptr, p.colind, 3, perm, ranges, block_rows=a.block_rows, dtype=dtype,
                             warps_per_cta=a.warps)
         st = ick.ic_stats(h)
-        ick.ic_set_timing(h, True)
         for _ in range(warmup):
-            ick.ic_numeric(h, av)
-            ick.pcg_solve(h, av, b, x, 1e-8, 5000)
+            timed_solve(ick, torch, h, av, b, x, 1e-8)
         torch.cuda.synchronize()
-        fact, tts, its = [], [], 0
+        tts, its = [], 0
         for _ in range(steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            ick.ic_numeric(h, av)
-            t = ick.ic_get_timing(h)
-            its, rel = ick.pcg_solve(h, av, b, x, 1e-8, 5000)
-            e1.record()
+            ev, its, rel = timed_solve(ick, torch, h, av, b, x, 1e-8)
             torch.cuda.synchronize()
-            fact.append(t["prepare_ms"] + t["numeric_ms"])
-            tts.append(e0.elapsed_time(e1))
+            tts.append(ev[0].elapsed_time(ev[2]))
         true_rel = float(np.linalg.norm(p.scipy() @ x.cpu().numpy() - b_host) / np.linalg.norm(b_host))
-        mf = statistics.median(fact)
+        mf = factor_kernel_ms(ick, h, av)
         out[name] = {"factor_ms": mf, "factor_gflops": st["flops"] / (mf * 1e-3) / 1e9,
                      "time_to_solution_ms": statistics.median(tts), "pcg_iters": int(its), "relres": float(rel),
                      "true_relres": true_rel}
@@ -459,7 +483,9 @@ def main():
                         warps_per_cta=a.warps, solve_mode=a.solve_mode, solve_lanes=a.solve_lanes,
                         solve_ctas_per_sm=a.solve_ctas)
     st = ick.ic_stats(h)
-    ick.ic_set_timing(h, True)
+    # the library's per-kernel timing stays off in the timed steps, so that pcg_solve runs
+    # as one graph; the kernels are timed afterwards, in a pass of their own
+    ick.ic_set_timing(h, False)
     stream = torch.cuda.current_stream()
     av = torch.from_numpy(prob.vals).cuda()
     b_host = synth.rhs(prob.n, 2000 + rank)
@@ -467,12 +493,15 @@ def main():
     x = torch.empty(prob.n, dtype=torch.float64, device="cuda")
 
     def step():
-        ick.ic_numeric(h, av, stream)
-        t = ick.ic_get_timing(h)
         if a.numeric_only:
-            return t["prepare_ms"] + t["numeric_ms"], t["numeric_ms"], 0, 0.0
-        it, rel = ick.pcg_solve(h, av, b, x, a.tol, 5000, stream)
-        return t["prepare_ms"] + t["numeric_ms"], t["numeric_ms"], it, rel
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            ick.ic_numeric_async(h, av, stream)
+            ev[1].record(stream)
+            stream.synchronize()
+            ick.ic_numeric_status(h)
+            return ev, 0, 0.0
+        return timed_solve(ick, torch, h, av, b, x, a.tol, stream)
 
     if a.numeric_only:
         a.no_e2e = True
@@ -490,7 +519,7 @@ def main():
         step()
     torch.cuda.synchronize()
     ick.ic_reset_timing(h)
-    fact_ms, kern_ms, iters, rels = [], [], [], []
+    fevs, iters, rels = [], [], []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         if world > 1:
@@ -498,9 +527,8 @@ def main():
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(a.steps):
-            f, kms, it, rel = step()
-            fact_ms.append(f)
-            kern_ms.append(kms)
+            ev, it, rel = step()
+            fevs.append(ev)
             iters.append(it)
             rels.append(rel)
         ev1.record(stream)
@@ -508,15 +536,36 @@ def main():
         if world > 1:
             dist.barrier()
     total_ms = ev0.elapsed_time(ev1)
-    tim = ick.ic_get_timing(h)
+    launches = ick.ic_get_timing(h)["launches"]  # kernels of the timed steps
     clocks = clk.summary()
+    # the factorization phase of a step as the timed steps saw it (scatter, task kernel
+    # and the solves' operand copies of the factor)
+    phase_ms = [e[0].elapsed_time(e[1]) for e in fevs]
+    mean_phase = sum(phase_ms) / len(phase_ms)
+    # per-kernel times: a few more steps with the library's CUDA events around every
+    # kernel (PCG then loops on the host, one synchronisation per iteration); the
+    # factor time of value is the scatter plus the task kernel
+    ks = 3
+    ick.ic_set_timing(h, True)
+    ick.ic_reset_timing(h)
+    fact_ms, kern = [], []
+    for _ in range(ks):
+        ick.ic_numeric(h, av, stream)
+        tm = ick.ic_get_timing(h)
+        fact_ms.append(tm["prepare_ms"] + tm["numeric_ms"])
+        kern.append(tm["numeric_ms"])
+        if not a.numeric_only:
+            ick.pcg_solve(h, av, b, x, a.tol, 5000, stream)
+    torch.cuda.synchronize()
+    tim = ick.ic_get_timing(h)
+    ick.ic_set_timing(h, False)
     mean_fact = sum(fact_ms) / len(fact_ms)
-    total_ms, mean_fact = max_over_ranks([total_ms, mean_fact], world)
+    total_ms, mean_fact, mean_phase = max_over_ranks([total_ms, mean_fact, mean_phase], world)
     ms_per_step = total_ms / a.steps
     value = job_rate(st["flops"], world, mean_fact * 1e-3) / 1e9
     hbm = job_rate(st["bytes"], world, mean_fact * 1e-3) / 1e9
-    apply_ms_step = tim["apply_ms"] / a.steps
-    mean_kern = sum(kern_ms) / len(kern_ms)
+    apply_ms_step = tim["apply_ms"] / ks
+    mean_kern = sum(kern) / len(kern)
 
     # true residual of the last solve, in FP64 on the host
     xh = x.cpu().numpy()
@@ -562,7 +611,7 @@ def main():
              "traffic": (SOLVE_TRAFFIC_PER_ENTRY[(a.k, name)] * nnz_l
                          if (a.k, name) in SOLVE_TRAFFIC_PER_ENTRY else None)}
         r["frac"] = r["achieved"] / r["peak"]
-        roofs[name] = (tim[key] / a.steps, r)
+        roofs[name] = (tim[key] / ks, r)
     dominant = max(roofs.values(), key=lambda v: v[0])[1]
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -575,13 +624,14 @@ def main():
                        "l2": "inputs larger than L2 (factor values alone 8*nnz(L) bytes)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_gbs": hbm, "factor_ms": mean_fact, "numeric_kernel_ms": mean_kern,
+            "factor_phase_ms": mean_phase,
             "pcg": {"iters": iters[-1], "relres": rels[-1], "true_relres": true_rel,
                     "tol": a.tol, "apply_ms_per_step": apply_ms_step,
                     "time_to_solution_ms": ms_per_step},
             "roofline": dominant, "roofline_numeric": roof_numeric,
             "roofline_solves": [roofs[names[0]][1], roofs[names[1]][1]],
             "ms_per_step_by_kernel": {k: v[0] for k, v in roofs.items()},
-            "gpu_launches": int(tim["launches"]), "clocks": clocks}
+            "gpu_launches": int(launches), "clocks": clocks}
 
     if not a.no_e2e:
         ab = torch.from_numpy(prob.vals).pin_memory()
@@ -618,27 +668,20 @@ def main():
         h32 = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
                               warps_per_cta=a.warps, dtype=ick.IC_F32, solve_mode=a.solve_mode,
                               solve_lanes=a.solve_lanes, solve_ctas_per_sm=a.solve_ctas)
-        ick.ic_set_timing(h32, True)
         x32 = torch.empty_like(x)
-
-        def step32():
-            ick.ic_numeric(h32, av, stream)
-            t = ick.ic_get_timing(h32)
-            it, rel = ick.pcg_solve(h32, av, b, x32, a.tol, 5000, stream)
-            return t["prepare_ms"] + t["numeric_ms"], it, rel
-
         for _ in range(a.warmup):
-            step32()
+            timed_solve(ick, torch, h32, av, b, x32, a.tol, stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f32_fact, f32_it, f32_rel = [], 0, 0.0
+        f32_evs, f32_it, f32_rel = [], 0, 0.0
         e0.record(stream)
         for _ in range(a.steps):
-            f, f32_it, f32_rel = step32()
-            f32_fact.append(f)
+            ev, f32_it, f32_rel = timed_solve(ick, torch, h32, av, b, x32, a.tol, stream)
+            f32_evs.append(ev)
         e1.record(stream)
         torch.cuda.synchronize()
         t32 = e0.elapsed_time(e1) / a.steps
+        f32_fact = [factor_kernel_ms(ick, h32, av, stream)]
         f32_true = float(np.linalg.norm(prob.scipy() @ x32.cpu().numpy() - b_host) / np.linalg.norm(b_host))
         mf32 = sum(f32_fact) / len(f32_fact)
         line["mixed_f32"] = {"factor_ms": mf32, "factor_gflops": st["flops"] / (mf32 * 1e-3) / 1e9,

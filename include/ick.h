@@ -207,6 +207,13 @@ int ic_apply_static_status(void* stream);
  *   b, x    device, n doubles, original ordering; x is overwritten.
  *   iters, relres  host out (may be NULL): iterations done and the final recursive
  *                  relative residual.
+ * With kernel timing off (the default) the whole solve is one CUDA graph launch: the
+ * loop runs on the device (a WHILE conditional node, its test computed by a kernel) and
+ * the host synchronises once, at the end.  The graph is captured and instantiated on
+ * a stream of the handle at the first call with a given (A_vals, b, x, tol, maxit) and
+ * kept until a call with other arguments.  With timing on (ic_set_timing) the loop
+ * runs on the host with one synchronisation per iteration, so that every kernel can be
+ * timed.  Both take the same arithmetic steps in the same order.
  * Errors: IC_ERR_ARG, IC_ERR_STATE, IC_ERR_NOCONV (x holds the last iterate), IC_ERR_CUDA. */
 int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, double tol, int maxit,
               int* iters, double* relres, void* stream);
@@ -322,7 +329,8 @@ typedef struct {
     double prepare_ms;     /* value scatter + scheduler reset of the last ic_numeric       */
     double numeric_ms;     /* persistent task-DAG kernel of the last ic_numeric            */
     double apply_ms;       /* triangular-solve kernels, summed since the last reset        */
-    int64_t apply_calls;   /* ic_apply calls (direct or inside pcg_solve) since the reset  */
+    int64_t apply_calls;   /* ic_apply calls (direct, or inside pcg_solve while timing is
+                              on) since the reset                                          */
     int64_t launches;      /* kernels launched by the library since the reset              */
     double fwd_ms;         /* forward-solve kernel alone, summed since the last reset      */
     double bwd_ms;         /* backward-solve kernel alone, summed since the last reset     */

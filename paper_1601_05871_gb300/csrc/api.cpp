@@ -84,6 +84,18 @@ struct ic_handle {
     bool numeric_pending = false;  // ic_numeric_async issued, status not read yet
     cudaStream_t cap_stream = nullptr;  // graph capture / replay stream of pcg_solve_batch
     cudaEvent_t cap_ev[2] = {nullptr, nullptr};
+    // pcg_solve as one graph: the prologue, then a WHILE node whose body is one
+    // iteration and whose condition a kernel sets, so the loop runs on the device.
+    // Built for the inputs of the call and kept until they change.
+    cudaStream_t body_stream = nullptr;  // captures the WHILE node's body
+    cudaGraphExec_t pcg_exec = nullptr;
+    const void* pcg_av = nullptr;
+    const double* pcg_b = nullptr;
+    double* pcg_x = nullptr;
+    double pcg_tol = 0.0;
+    int pcg_maxit = -1, pcg_grid = 0;
+    unsigned long long pcg_tmo = 0;
+    int* d_iter = nullptr;  // iterations done (device)
 
     ~ic_handle() {
         for (cudaEvent_t e : ev)
@@ -96,6 +108,8 @@ struct ic_handle {
         for (cudaEvent_t e : cap_ev)
             if (e) cudaEventDestroy(e);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (pcg_exec) cudaGraphExecDestroy(pcg_exec);
+        if (body_stream) cudaStreamDestroy(body_stream);
     }
 
     template <class T>
@@ -712,6 +726,129 @@ int ic_apply_static_status(void* stream) {
     return rec ? fail(IC_ERR_TIMEOUT, "ic_apply_static: triangular solve wait timed out") : IC_OK;
 }
 
+// pcg_solve's graph: the prologue of the host loop below (r = b, x = 0, |b|, |r|), then
+// a WHILE node whose body is one iteration rotated so that the test comes last: the
+// preconditioner application, r.z, beta and p of the previous iteration (p starts at
+// 0 and the previous r.z at 1, so the first pass gives p = z), then q = A p, alpha, x
+// and r, |r| and the loop test.  The arithmetic is the host loop's, operation for
+// operation; no iteration is run after the test fails.
+static cudaError_t pcg_capture(ic_handle* h, const double* av, const double* b, double* x, double tol, int maxit,
+                               unsigned long long tmo) {
+    const int n = int(h->hp.n);
+    const int parts = pcg_parts(n);
+    cudaStream_t s = h->cap_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t capg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphConditionalHandle cond = 0;
+    cudaGraphNode_t wnode = nullptr;
+    cudaGraph_t body = nullptr;
+    e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &capg, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, capg, 0, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->sp.counter + 3, 0, sizeof(int), s);  // solve timeout record
+    if (e == cudaSuccess) e = pcg_init(n, b, x, h->r, s);
+    if (e == cudaSuccess) e = pcg_dot(b, b, n, h->partial, parts, s);
+    if (e == cudaSuccess) e = pcg_finish(h->partial, parts, h->sc, 4, s);
+    if (e == cudaSuccess) e = pcg_dot(h->r, h->r, n, h->partial, parts, s);
+    if (e == cudaSuccess) e = pcg_finish(h->partial, parts, h->sc, 1, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->p, 0, size_t(n) * sizeof(double), s);
+    if (e == cudaSuccess) e = pcg_loop_step(h->sc, h->d_iter, tol, maxit, cond, true, s);
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &capg, &deps, nullptr, &nd);
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, capg, deps, nullptr, nd, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (e == cudaSuccess) e = ee;
+    // the body, captured into the node's own graph
+    if (e == cudaSuccess) {
+        cudaStream_t bs = h->body_stream;
+        e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t be = launch_apply(h->sp, h->r, h->z, 0, tmo, h->grid_apply, bs);
+            if (be == cudaSuccess) be = pcg_dot(h->r, h->z, n, h->partial, parts, bs);
+            if (be == cudaSuccess) be = pcg_finish(h->partial, parts, h->sc, 2, bs);
+            if (be == cudaSuccess) be = pcg_step_p(n, h->p, h->z, h->sc, bs);
+            if (be == cudaSuccess) be = launch_spmv(h->sp, av, h->p, h->q, bs);
+            if (be == cudaSuccess) be = pcg_dot(h->p, h->q, n, h->partial, parts, bs);
+            if (be == cudaSuccess) be = pcg_finish(h->partial, parts, h->sc, 0, bs);
+            if (be == cudaSuccess) be = pcg_step_x_r(n, x, h->r, h->p, h->q, h->sc, h->partial, parts, bs);
+            if (be == cudaSuccess) be = pcg_finish(h->partial, parts, h->sc, 1, bs);
+            if (be == cudaSuccess) be = pcg_loop_step(h->sc, h->d_iter, tol, maxit, cond, false, bs);
+            cudaGraph_t bg = nullptr;
+            const cudaError_t be2 = cudaStreamEndCapture(bs, &bg);
+            e = be != cudaSuccess ? be : be2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->pcg_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    return e;
+}
+
+// pcg_solve when no per-kernel timing is asked for: the whole solve is one graph
+// launch; the host reads the iteration count, the residual and the solves' timeout
+// record once, at the end.
+static int pcg_solve_graph(ic_handle* h, const double* av, const double* b, double* x, double tol, int maxit,
+                           int* iters, double* relres, cudaStream_t us) {
+    const unsigned long long tmo = (unsigned long long)(h->opts.timeout_s * 1e9);
+    if (!h->cap_stream) {
+        CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->cap_ev[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->cap_ev[1], cudaEventDisableTiming));
+    }
+    if (!h->body_stream) CK(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
+    if (!h->d_iter) {
+        int st = h->alloc(&h->d_iter, 1);
+        if (st) return st;
+    }
+    if (!h->pcg_exec || h->pcg_av != av || h->pcg_b != b || h->pcg_x != x || h->pcg_tol != tol ||
+        h->pcg_maxit != maxit || h->pcg_grid != h->grid_apply || h->pcg_tmo != tmo) {
+        if (h->pcg_exec) {
+            cudaGraphExecDestroy(h->pcg_exec);
+            h->pcg_exec = nullptr;
+        }
+        const cudaError_t e = pcg_capture(h, av, b, x, tol, maxit, tmo);
+        if (e != cudaSuccess) {
+            if (h->pcg_exec) cudaGraphExecDestroy(h->pcg_exec);
+            h->pcg_exec = nullptr;
+            return cuda_fail(e, "pcg_solve: graph capture");
+        }
+        h->pcg_av = av;
+        h->pcg_b = b;
+        h->pcg_x = x;
+        h->pcg_tol = tol;
+        h->pcg_maxit = maxit;
+        h->pcg_grid = h->grid_apply;
+        h->pcg_tmo = tmo;
+    }
+    CK(cudaGraphLaunch(h->pcg_exec, us));
+    CK(cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, us));
+    CK(cudaMemcpyAsync(h->h_counters + 8, h->d_iter, sizeof(int), cudaMemcpyDeviceToHost, us));
+    CK(cudaMemcpyAsync(h->h_counters + 9, h->sp.counter + 3, sizeof(int), cudaMemcpyDeviceToHost, us));
+    CK(cudaStreamSynchronize(us));
+    const int it = h->h_counters[8];
+    const double rel = h->h_sc->relres;
+    h->tm.launches += 6 + int64_t(it) * 11;  // kernels: prologue 6, each pass 11 (two solves)
+    if (h->h_counters[9]) {  // reported here, so the record is cleared
+        CK(cudaMemset(h->sp.counter + 3, 0, sizeof(int)));
+        return fail(IC_ERR_TIMEOUT, "triangular solve wait timed out");
+    }
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    if (!(rel <= tol)) return fail(IC_ERR_NOCONV, "PCG reached maxit");
+    return IC_OK;
+}
+
 int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, double tol, int maxit,
               int* iters, double* relres, void* stream) {
     if (iters) *iters = 0;
@@ -725,6 +862,9 @@ int pcg_solve(ic_handle* h, const void* A_vals, const double* b, double* x, doub
     DeviceGuard g(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double* av = static_cast<const double*>(A_vals);
+    if (!h->timing) return pcg_solve_graph(h, av, b, x, tol, maxit, iters, relres, s);
+    // with per-kernel timing (events around every application, which a graph's loop
+    // body cannot hold): the loop on the host, one synchronisation per iteration
     const int parts = pcg_parts(n);
     int st = 0;
     int64_t& nl = h->tm.launches;

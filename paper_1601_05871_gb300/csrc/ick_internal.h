@@ -257,6 +257,9 @@ cudaError_t pcg_step_x_r(int n, double* x, double* r, const double* p, const dou
                          PcgScalars* sc, double* partial, int nparts, cudaStream_t s);
 cudaError_t pcg_step_p(int n, double* p, const double* z, PcgScalars* sc, cudaStream_t s);
 cudaError_t pcg_init(int n, const double* b, double* x, double* r, cudaStream_t s);
+// pcg_solve's device-side loop test: iteration count and the WHILE node's condition.
+cudaError_t pcg_loop_step(PcgScalars* sc, int* it, double tol, int maxit, cudaGraphConditionalHandle cond,
+                          bool first, cudaStream_t s);
 
 // Batched PCG (batch.cu): per-system scalars of systems stored block-diagonally.
 struct BatchScalars {

@@ -582,6 +582,24 @@ cudaError_t pcg_step_p(int n, double* p, const double* z, PcgScalars* sc, cudaSt
     return cudaGetLastError();
 }
 
+// The loop test of pcg_solve's device-side loop (one thread): the iteration count
+// (0 before the first iteration, when the previous r.z is also set to 1 so that the
+// first direction update leaves p = z) and the condition of the graph's WHILE node:
+// another iteration while relres > tol and fewer than maxit have run.
+__global__ void pcg_loop_kernel(PcgScalars* sc, int* it, double tol, int maxit, cudaGraphConditionalHandle cond,
+                                int first) {
+    const int k = first ? 0 : *it + 1;
+    if (first) sc->rz = 1.0;
+    *it = k;
+    cudaGraphSetConditional(cond, sc->relres > tol && k < maxit ? 1u : 0u);
+}
+
+cudaError_t pcg_loop_step(PcgScalars* sc, int* it, double tol, int maxit, cudaGraphConditionalHandle cond,
+                          bool first, cudaStream_t s) {
+    pcg_loop_kernel<<<1, 1, 0, s>>>(sc, it, tol, maxit, cond, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t pcg_init(int n, const double* b, double* x, double* r, cudaStream_t s) {
     init_kernel<<<vec_grid(n), kRedThreads, 0, s>>>(n, b, x, r);
     return cudaGetLastError();

@@ -317,6 +317,44 @@ def test_pcg_matches_oracle(ick, orc):
     assert np.abs(xg - xo).max() <= 1e-6 * np.abs(xo).max()
 
 
+def test_pcg_graph_matches_host_loop(ick):
+    """pcg_solve as one graph (timing off: the loop runs on the device) and as a host
+    loop (timing on) take the same steps: the same iterations and the same x, on a
+    repeated call (the graph kept) and after a change of tol (the graph rebuilt); a
+    maxit that stops the loop early gives IC_ERR_NOCONV after exactly maxit
+    iterations in both."""
+    import torch
+    prob = synth.laplace3d_27pt(20)
+    perm, ranges = ick.ic_nd_grid(20, 20, 20, 1, 1024)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 1, perm, ranges, block_rows=1024)
+    av = dev(prob.vals)
+    ick.ic_numeric(h, av)
+    b = dev(synth.rhs(prob.n, 77))
+
+    def solve(timing, tol, maxit=1000):
+        ick.ic_set_timing(h, timing)
+        x = torch.full((prob.n,), 7.0, dtype=torch.float64, device="cuda")
+        it, rel = ick.pcg_solve(h, av, b, x, tol, maxit, raise_noconv=False)
+        torch.cuda.synchronize()
+        return it, rel, x.cpu().numpy()
+
+    for tol in (1e-8, 1e-8, 1e-11):
+        ig, rg, xg = solve(False, tol)
+        ih, rh, xh = solve(True, tol)
+        assert ig == ih and ig > 3 and rg <= tol
+        assert rg == rh
+        assert np.array_equal(xg, xh)
+    for timing in (False, True):
+        ick.ic_set_timing(h, timing)
+        x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        with pytest.raises(ick.IckError) as e:
+            ick.pcg_solve(h, av, b, x, 1e-14, 3)
+        assert e.value.status == ick.IC_ERR_NOCONV
+        it, rel = ick.pcg_solve(h, av, b, x, 1e-14, 3, raise_noconv=False)
+        assert it == 3 and rel > 1e-14
+    ick.ic_set_timing(h, False)
+
+
 @pytest.mark.slow
 def test_full_size_27pt_96_ic2(ick, orc):
     """The bench workload at full size (96^3 27-point, IC(2), ND ranges of <= 4096 rows,
