@@ -145,9 +145,10 @@ struct WarpBuf {
 template <typename T>
 __device__ __forceinline__ int find_col(const WarpBuf<T>& W, int c, int c_0, unsigned span) {
     const unsigned off = unsigned(c - c_0);
-    const uint2 e = W.cmap[min(off >> 5, unsigned(kMapWords - 1))];
+    if (off >= span) return -1;
+    const uint2 e = W.cmap[off >> 5];
     const unsigned b = off & 31u;
-    return (off < span && ((e.x >> b) & 1u)) ? int(e.y) + __popc(e.x & ((1u << b) - 1u)) : -1;
+    return ((e.x >> b) & 1u) ? int(e.y) + __popc(e.x & ((1u << b) - 1u)) : -1;
 }
 
 template <bool EXACT, typename T>
@@ -191,11 +192,12 @@ __device__ T await_value(const DevPlan& P, const T* src, unsigned long long dead
 // One pivot in registers: lane l holds element l of the pivot row's source segment
 // (value v and column c), a the multiplier U_pr when it lies outside the segment, st 0
 // (empty segment), 1 (loaded) or 2 (the pivot row is not complete yet: it is waited for
-// and loaded when it is applied).
+// and loaded when it is applied), len and z the segment's length and first position
+// (kept here so that the application does not read the batch entry again).
 template <typename T>
 struct PivReg {
     T v, a;
-    int c, st;
+    int c, st, len, z;
 };
 
 // Load pivot j of the batch (W.piv) into R.  Chol/Trsm on one CTA: the pivot row's
@@ -211,6 +213,8 @@ __device__ __forceinline__ void load_pivot(const DevPlan& P, const T* U, const T
     const int4 pi = W.piv[j];
     const int len = pi.w;
     R.st = 0;
+    R.len = len;
+    R.z = pi.z;
     if (len == 0) return;
     if (!SPLIT && MODE != M_UPDATE && !((seen >> j) & 1u)) {
         int dn = 1;
@@ -240,10 +244,10 @@ __device__ __forceinline__ bool apply_pivot(const DevPlan& P, const T* U, const 
                                             unsigned long long deadline) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    const int4 pi = W.piv[q];
-    const int len = pi.w;
+    const int len = R.len;
     if (len > 0) {
         if (R.st == 2) {  // the pivot row is waited for, then loaded
+            const int4 pi = W.piv[q];
             int ok = 1;
             if (lane == 0) ok = wait_row(P, done, pi.x - rbase, deadline);
             if (!__shfl_sync(full, ok, 0)) return false;
@@ -254,15 +258,15 @@ __device__ __forceinline__ bool apply_pivot(const DevPlan& P, const T* U, const 
             R.a = start_at_r ? T(0) : ld_cg(U + pi.y);
         }
         const T* V = SPLIT ? shadow + W.psoff[q] : U;
-        if (SPLIT && lane < len && is_sentinel(R.v)) R.v = await_value(P, V + pi.z + lane, deadline);
+        if (SPLIT && lane < len && is_sentinel(R.v)) R.v = await_value(P, V + R.z + lane, deadline);
         const T a = start_at_r ? __shfl_sync(full, R.v, 0) : R.a;
         if (lane < len) {
             const int idx = find_col(W, R.c, c_0, span);
             if (idx >= 0) W.tval[idx] = sub_product<EXACT>(W.tval[idx], a, R.v);
         }
         for (int o = 32 + lane; o < len; o += 32) {
-            const T v = SPLIT ? await_value(P, V + pi.z + o, deadline) : ld_cg(U + pi.z + o);
-            apply_one<EXACT>(W, __ldg(P.ucol + pi.z + o), c_0, span, a, v);
+            const T v = SPLIT ? await_value(P, V + R.z + o, deadline) : ld_cg(U + R.z + o);
+            apply_one<EXACT>(W, __ldg(P.ucol + R.z + o), c_0, span, a, v);
         }
         if (dchunk && lane == 0) W.dacc = fma(-double(a), double(a), W.dacc);
     }
