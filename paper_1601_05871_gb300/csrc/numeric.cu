@@ -338,11 +338,12 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
         }
         __syncwarp();
         for (int q0 = ca; q0 < cb; q0 += 32) {
-            const int nq = min(32, cb - q0);
-            int dn = 1;
-            if (lane < nq) {
+            const int nq0 = min(32, cb - q0);
+            int dn = 1, len = 0, so = 0;
+            int4 pv = make_int4(0, 0, 0, 0);
+            if (lane < nq0) {
                 const int2 pe = __ldg(P.csc + q0 + lane);
-                int sb, len;
+                int sb;
                 if (start_at_r) {
                     sb = pe.y;
                     len = __ldg(P.cseg_end + q0 + lane) - pe.y;
@@ -351,12 +352,22 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                     sb = s.x;
                     len = s.y - s.x;
                 }
-                W.piv[lane] = make_int4(pe.x, pe.y, sb, len);
-                if (SPLIT) W.psoff[lane] = len > 0 ? __ldg(soffs + pe.x - rbase) : 0;
+                pv = make_int4(pe.x, pe.y, sb, len);
+                if (SPLIT) so = len > 0 ? __ldg(soffs + pe.x - rbase) : 0;
                 // one CTA's Chol/Trsm: the completion flags of the whole batch, one per lane
                 else if (MODE != M_UPDATE && len > 0) dn = done[pe.x - rbase];
             }
-            unsigned seen = __ballot_sync(full, dn != 0);
+            // the batch without the pivots whose source segment is empty (a pivot row
+            // with no entry in the source block column contributes nothing; a third of
+            // the Trsm pivots, say), in the same ascending order
+            const unsigned keep = __ballot_sync(full, len > 0);
+            const int pos = __popc(keep & ((1u << lane) - 1u));
+            const int nq = __popc(keep);
+            if (len > 0) {
+                W.piv[pos] = pv;
+                if (SPLIT) W.psoff[pos] = so;
+            }
+            unsigned seen = __reduce_or_sync(full, len > 0 && dn != 0 ? 1u << pos : 0u);
             if (!SPLIT && MODE != M_UPDATE) __threadfence_block();
             __syncwarp();
             // each pivot is loaded when its turn comes (the other warps of the CTA cover
