@@ -136,6 +136,7 @@ struct WarpBuf {
     int psoff[32];         // split tasks: the pivot row's shadow offset
     double dacc;           // FP64 diagonal accumulator (T = float)
     double pad;
+    T abuf[32];            // T = float: the batch's multipliers U_pr, for the diagonal
     uint2 cmap[kMapWords]; // (bits, rank) per 32 column offsets
     T tval[kSegCap];       // target segment values (one chunk)
     int tcol[kSegCap];     // target segment columns
@@ -268,7 +269,7 @@ __device__ __forceinline__ bool apply_pivot(const DevPlan& P, const T* U, const 
             const T v = SPLIT ? await_value(P, V + R.z + o, deadline) : ld_cg(U + R.z + o);
             apply_one<EXACT>(W, __ldg(P.ucol + R.z + o), c_0, span, a, v);
         }
-        if (dchunk && lane == 0) W.dacc = fma(-double(a), double(a), W.dacc);
+        if (dchunk && lane == 0) W.abuf[q] = a;  // the diagonal takes the batch's squares at once
     }
     __syncwarp();
     return true;
@@ -382,6 +383,20 @@ __device__ void process_target(const DevPlan& P, T* U, int r, int ca, int cb, in
                     return;
             }
             __syncwarp();
+            if (dchunk) {
+                // FP64 diagonal (T = float): d -= sum of the batch's U_pr^2, each square exact
+                // in FP64, summed in a fixed tree; a handful of FP64 instructions per batch
+                // instead of a dependent multiply-add per pivot on the SM's scarce FP64 unit
+                double sq = 0.0;
+                if (lane < nq) {
+                    const double av = double(W.abuf[lane]);
+                    sq = av * av;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(full, sq, o);
+                if (lane == 0) W.dacc -= sq;
+                __syncwarp();
+            }
         }
         if (MODE == M_CHOL) {
             if (c0 == tb) {

@@ -331,9 +331,11 @@ def test_pcg_graph_matches_host_loop(ick):
     ick.ic_numeric(h, av)
     b = dev(synth.rhs(prob.n, 77))
 
+    x = torch.empty(prob.n, dtype=torch.float64, device="cuda")  # the same x every call
+
     def solve(timing, tol, maxit=1000):
         ick.ic_set_timing(h, timing)
-        x = torch.full((prob.n,), 7.0, dtype=torch.float64, device="cuda")
+        x.fill_(7.0)
         it, rel = ick.pcg_solve(h, av, b, x, tol, maxit, raise_noconv=False)
         torch.cuda.synchronize()
         return it, rel, x.cpu().numpy()
@@ -344,9 +346,15 @@ def test_pcg_graph_matches_host_loop(ick):
         assert ig == ih and ig > 3 and rg <= tol
         assert rg == rh
         assert np.array_equal(xg, xh)
+    # new values behind the same pointer (the kept graph reads them): 2A x = b
+    av.mul_(2.0)
+    ick.ic_numeric(h, av)
+    ig, rg, x2 = solve(False, 1e-11)
+    ih, rh, x2h = solve(True, 1e-11)
+    assert ig == ih and np.array_equal(x2, x2h)
+    assert np.abs(2.0 * x2 - xg).max() <= 1e-8 * np.abs(xg).max()
     for timing in (False, True):
         ick.ic_set_timing(h, timing)
-        x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
         with pytest.raises(ick.IckError) as e:
             ick.pcg_solve(h, av, b, x, 1e-14, 3)
         assert e.value.status == ick.IC_ERR_NOCONV
