@@ -235,8 +235,9 @@ __device__ bool solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
     }
     for (int t0 = first; t0 < len; t0 += nw * R) {
         if (t0 != first) load(t0);
-        // the row's result is t - rd * (sum of the internal products); a row without
-        // external entries keeps w = 0 (never written), which leaves t unchanged
+        // the row's result is rd * t plus the sum of the internal products, whose
+        // values hold -rd already (gather_scaled); a row without external entries keeps
+        // w = 0 (never written), which leaves t unchanged
         if (i >= 0 && sl == 0) t = (t - ldcg(w + i)) * rd;
         if (!await_count(done, need, S.counter + 2, deadline)) break;
         // the source values first: M independent shared-memory loads issued together
@@ -251,6 +252,7 @@ __device__ bool solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
         T acc[NA];
 #pragma unroll
         for (int yy = 0; yy < NA; ++yy) acc[yy] = T(0);
+        acc[0] = t;  // the scaled right-hand side (0 on the other lanes of the row)
 #pragma unroll
         for (int x = 0; x < M; x += NA) {
             if (x >= most) break;
@@ -263,7 +265,7 @@ __device__ bool solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
         if constexpr (NA == 4) tot = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         const T accs = sum_group<G>(tot);
         if (sl == 0 && i >= 0) {
-            const T v = fma(-rd, accs, t);
+            const T v = accs;
             sh[i - s] = v;
             // the count is raised before the global stores, so its release waits only
             // for the shared-memory result; later tasks read the global copies after
@@ -476,18 +478,26 @@ __global__ void transpose_values(int noff, const int2* __restrict__ csc, const T
         uvt[q] = uv[__ldg(&csc[q].y)];
 }
 
-// out[q] = uv[pos[q]].
 template <typename T>
-__global__ void gather_values(int cnt, const int* __restrict__ pos, const T* __restrict__ uv, T* __restrict__ out) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) out[q] = uv[__ldg(pos + q)];
+__global__ void gather_scaled(int n, const int* __restrict__ ptr, const int* __restrict__ pos,
+                              const T* __restrict__ uv, const T* __restrict__ rd, T* __restrict__ out) {
+    const int lane = threadIdx.x & 31, warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const T m = -__ldg(rd + i);
+        const int e = __ldg(ptr + i + 1);
+        for (int q = __ldg(ptr + i) + lane; q < e; q += 32) out[q] = __ldg(uv + __ldg(pos + q)) * m;
+    }
 }
 
 template <typename T>
-void launch_gathers(const SolvePlan& S, const T* uv, cudaStream_t s) {
+void launch_gathers(const SolvePlan& S, const T* uv, const T* rd, cudaStream_t s) {
     auto grid = [](int cnt) { return (cnt + 255) / 256 < 8192 ? (cnt + 255) / 256 : 8192; };
     if (S.noff > 0) transpose_values<T><<<grid(S.noff), 256, 0, s>>>(S.noff, S.csc, uv, static_cast<T*>(S.uvt));
-    if (S.nxf > 0) gather_values<T><<<grid(S.nxf), 256, 0, s>>>(S.nxf, S.xf_pos, uv, static_cast<T*>(S.xf_val));
-    if (S.nxb > 0) gather_values<T><<<grid(S.nxb), 256, 0, s>>>(S.nxb, S.xb_pos, uv, static_cast<T*>(S.xb_val));
+    const int rows = (S.n + 7) / 8 < 8192 ? (S.n + 7) / 8 : 8192;  // 8 warps of 256 threads per block
+    if (S.nxf > 0)
+        gather_scaled<T><<<rows, 256, 0, s>>>(S.n, S.xf_ptr, S.xf_pos, uv, rd, static_cast<T*>(S.xf_val));
+    if (S.nxb > 0)
+        gather_scaled<T><<<rows, 256, 0, s>>>(S.n, S.xb_ptr, S.xb_pos, uv, rd, static_cast<T*>(S.xb_val));
 }
 
 }  // namespace
@@ -499,8 +509,8 @@ int dag_prepare_launches(const SolvePlan& S) {
 
 cudaError_t launch_dag_prepare(const SolvePlan& S, cudaStream_t s) {
     if (S.solve_mode != 0) return cudaSuccess;
-    if (S.dtype == IC_F32) launch_gathers<float>(S, S.uval32, s);
-    else launch_gathers<double>(S, S.uval, s);
+    if (S.dtype == IC_F32) launch_gathers<float>(S, S.uval32, S.rdiag32, s);
+    else launch_gathers<double>(S, S.uval, S.rdiag, s);
     return cudaGetLastError();
 }
 
