@@ -312,7 +312,10 @@ __device__ __forceinline__ unsigned smid() {
 
 // Claims the next task (its in-degree is awaited by the task itself, with wait_ready).
 // Returns the task index, or -1 when the list is exhausted or the solve was aborted.
-__device__ int claim_task(int* claim_ctr, int ntasks, int* taken, int* abort_word, int* s_task,
+// s_claim is a shared word of its own, not release's s_task: the barrier at the start of
+// release orders every read of its last value before the next write, whereas a warp
+// delayed past a claim into s_task could read the new task as a continuation.
+__device__ int claim_task(int* claim_ctr, int ntasks, int* taken, int* abort_word, int* s_claim,
                           unsigned long long* trace) {
     if (threadIdx.x == 0) {
         int t = -1;
@@ -327,10 +330,10 @@ __device__ int claim_task(int* claim_ctr, int ntasks, int* taken, int* abort_wor
                 trace[4 * t + 3] = (unsigned long long)t | ((unsigned long long)smid() << 32);
             }
         }
-        *s_task = t;
+        *s_claim = t;
     }
     __syncthreads();
-    return *s_task;
+    return *s_claim;
 }
 
 // After a task: its results are made visible, then its successors are released, by
@@ -342,6 +345,7 @@ __device__ int claim_task(int* claim_ctr, int ntasks, int* taken, int* abort_wor
 __device__ __forceinline__ int release(int t, bool is_l, const int* succ_ptr, const int* succ, const int* next,
                                        int* indeg, int* taken, unsigned long long* trace, int* s_task) {
     __threadfence();
+    __syncthreads();  // the task is done in every thread, and s_task is no longer read
     if (threadIdx.x == 0) {
         if (trace) trace[4 * t + 2] = gclock();
         *s_task = -1;
@@ -374,7 +378,7 @@ forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all
             T* y, T* w, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_task, s_done, s_ok;
+    __shared__ int s_task, s_claim, s_done, s_ok;
     const unsigned long long deadline = gclock() + timeout_ns;
     int* indeg = S.dag_indeg;
     int* taken = S.dag_taken;
@@ -382,7 +386,7 @@ forward_dag(SolvePlan S, const T* __restrict__ uvt, const T* __restrict__ rd_all
     bool cont = false;
     for (;;) {
         if (t < 0) {
-            t = claim_task(S.counter + 0, S.nftask, taken, S.counter + 2, &s_task, S.trace);
+            t = claim_task(S.counter + 0, S.nftask, taken, S.counter + 2, &s_claim, S.trace);
             cont = false;
         }
         if (t < 0) break;
@@ -406,7 +410,7 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
              double* __restrict__ z, T* w, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sh = reinterpret_cast<T*>(smem);
-    __shared__ int s_task, s_done, s_ok;
+    __shared__ int s_task, s_claim, s_done, s_ok;
     const unsigned long long deadline = gclock() + timeout_ns;
     int* indeg = S.dag_indeg + S.nftask;
     int* taken = S.dag_taken + S.nftask;
@@ -415,7 +419,7 @@ backward_dag(SolvePlan S, const T* __restrict__ uv, const T* __restrict__ rd_all
     bool cont = false;
     for (;;) {
         if (t < 0) {
-            t = claim_task(S.counter + 1, S.nbtask, taken, S.counter + 2, &s_task, tr);
+            t = claim_task(S.counter + 1, S.nbtask, taken, S.counter + 2, &s_claim, tr);
             cont = false;
         }
         if (t < 0) break;

@@ -317,6 +317,28 @@ def test_pcg_matches_oracle(ick, orc):
     assert np.abs(xg - xo).max() <= 1e-6 * np.abs(xo).max()
 
 
+def test_repeated_applies_are_identical(ick):
+    """Two hundred preconditioner applications in a row give the same bits and no
+    timeout: the solves are deterministic, so a CTA whose warps disagreed on the task
+    at hand (a race on the shared task slot between a release and the next claim)
+    would show here as a changed result or a wait that gives up."""
+    import torch
+    prob = synth.laplace3d_27pt(24)
+    perm, ranges = ick.ic_nd_grid(24, 24, 24, 1, 1024)
+    h = ick.ic_symbolic(prob.rowptr, prob.colind, 2, perm, ranges, block_rows=1024)
+    ick.ic_numeric(h, dev(prob.vals))
+    r = dev(synth.rhs(prob.n, 5))
+    z = torch.empty_like(r)
+    ick.ic_apply(h, r, z)
+    torch.cuda.synchronize()
+    z0 = z.cpu().numpy()
+    outs = torch.empty((200, prob.n), dtype=torch.float64, device="cuda")
+    for k in range(200):
+        ick.ic_apply(h, r, outs[k])
+    ick.ic_apply_status(h)  # raises if a wait gave up
+    assert bool((outs == torch.from_numpy(z0).cuda()).all())
+
+
 def test_pcg_graph_matches_host_loop(ick):
     """pcg_solve as one graph (timing off: the loop runs on the device) and as a host
     loop (timing on) take the same steps: the same iterations and the same x, on a
