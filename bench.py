@@ -45,14 +45,14 @@ METRIC = "IC(k) factor GFLOP/s & HBM GB/s; PCG time-to-1e-8 vs plain FP64 on GB3
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300's nominal FP64 rate, used only if the probe cannot run
 # DRAM bytes (read + write) per launch of a solve kernel of the 27-point IC(2) problem,
 # per factor entry: ncu captures (dram__bytes_read.sum + dram__bytes_write.sum, one
-# launch each) of the 48^3 and 64^3 problems gave 14.87 / 14.77 (forward) and 14.98 /
+# launch each) of the 48^3 and 64^3 problems gave 14.89 / 14.76 (forward) and 14.98 /
 # 14.97 (backward) bytes per entry; the 64^3 figures are scaled to the factor at hand
-SOLVE_TRAFFIC_PER_ENTRY = {(2, "forward_dag"): 14.77, (2, "backward_dag"): 14.97}
+SOLVE_TRAFFIC_PER_ENTRY = {(2, "forward_dag"): 14.76, (2, "backward_dag"): 14.97}
 # DRAM bytes (read + write) per factor entry of one launch of the numeric task kernel
 # of the 27-point IC(k) problem, by k: ncu captures of the 48^3, 64^3 and 80^3
-# problems gave 50.6, 57.8 and 55.0 bytes per entry; the 80^3 figure is scaled to the
+# problems gave 50.4, 57.8 and 55.1 bytes per entry; the 80^3 figure is scaled to the
 # factor at hand
-NUMERIC_TRAFFIC_PER_ENTRY = {2: 55.0}
+NUMERIC_TRAFFIC_PER_ENTRY = {2: 55.1}
 
 
 def timed_solve(ick, torch, h, av, b, x, tol, stream=None):
