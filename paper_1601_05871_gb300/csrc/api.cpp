@@ -767,7 +767,8 @@ static cudaError_t pcg_capture(ic_handle* h, const double* av, const double* b, 
         e = cudaGraphAddNode(&wnode, capg, deps, nullptr, nd, &cp);
         if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
     }
-    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
     const cudaError_t ee = cudaStreamEndCapture(s, &graph);
     if (e == cudaSuccess) e = ee;
     // the body, captured into the node's own graph
@@ -1373,7 +1374,8 @@ int ic_autotune(int64_t count, const ic_csr_pattern* A, int k, const int32_t* co
             const double t = time_numeric(o, nullptr);
             if (t >= 0 && (best_num < 0 || t < best_num)) { best_num = t; pick = o; }
         }
-        if (best_num < 0) return fail(IC_ERR_ARG, "autotune: no candidate factored (" + std::string(ic_last_error()) + ")");
+        if (best_num < 0)
+            return fail(IC_ERR_ARG, "autotune: no candidate factored (" + std::string(ic_last_error()) + ")");
         cur = pick;
     }
     for (int w : {8, 16, 32}) {

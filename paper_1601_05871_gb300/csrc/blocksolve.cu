@@ -221,8 +221,8 @@ __device__ bool solve_local(const SolvePlan& S, const T* __restrict__ xv, const 
     const int nw = blockDim.x >> 5;
     const int first = (threadIdx.x >> 5) * R;
     if (first < len) load(first);
-    if (wait_t >= 0 && !wait_ready(wait_t, indeg, S.counter + 2, deadline, BW && S.trace ? S.trace + 4 * size_t(S.nftask) : S.trace, s_ok))
-        return false;
+    unsigned long long* trace = S.trace && BW ? S.trace + 4 * size_t(S.nftask) : S.trace;
+    if (wait_t >= 0 && !wait_ready(wait_t, indeg, S.counter + 2, deadline, trace, s_ok)) return false;
     const int base = __ldg((BW ? S.lb_ptr : S.lf_ptr) + k);
     const int s = __ldg(S.ranges + k);
     if (!cont) {  // a continuation already holds the range's earlier results and count
