@@ -116,6 +116,8 @@ def parse():
                     help="7-point diffusion workload instead: 160^3 (--side), sigma 2, z faces x100, IC(3)")
     ap.add_argument("--leaf-rows", type=int, default=0,
                     help="nested-dissection leaf size (the pruning of the ND tree); 0: --block-rows")
+    ap.add_argument("--sep-colours", type=int, default=0,
+                    help="number each ND separator plane in C x C colour classes (0: lexicographic)")
     ap.add_argument("--no-sub", action="store_true",
                     help="leave the C4 / C3 / C5 workloads out of the default line")
     a = ap.parse_args()
@@ -126,6 +128,8 @@ def parse():
 
 def workload_name(a):
     leaf = "" if a.leaf_rows == a.block_rows else f" (ND leaves <= {a.leaf_rows} rows)"
+    if a.sep_colours >= 2:
+        leaf += f", separators in {a.sep_colours}x{a.sep_colours} colour classes"
     solves = {0: "block-DAG", 1: "row-level"}[a.solve_mode]
     return (f"27-point Laplacian {a.side}^3 (n={a.side ** 3}), geometric ND{leaf}, 2D blocks <= "
             f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}, {solves} triangular solves")
@@ -198,13 +202,13 @@ class ClockSampler:
                 "samples": len(loaded), "reasons": sorted(reasons)}
 
 
-def oracle_problem(side, k, leaf_rows):
+def oracle_problem(side, k, leaf_rows, sep_colours):
     """The oracle's symbolic phase of the side^3 27-point problem, as the GPU arm orders
-    it (geometric ND with the same leaf size)."""
+    it (geometric ND with the same leaf size and separator order)."""
     import oracle
     import synth
     prob = synth.laplace3d_27pt(side)
-    perm, _ = oracle.nd_grid(side, side, side, 1, leaf_rows)
+    perm, _ = oracle.nd_grid(side, side, side, 1, leaf_rows, sep_colours=sep_colours)
     return prob, oracle.OracleIC.from_problem(prob, perm, k)
 
 
@@ -238,7 +242,7 @@ def reference_arm(a, rank, world):
     if rank != 0:
         return
     # each step: one oracle numeric factorization of the full workload (single thread)
-    prob, h = oracle_problem(a.side, a.k, a.leaf_rows)
+    prob, h = oracle_problem(a.side, a.k, a.leaf_rows, a.sep_colours)
     for _ in range(a.warmup):
         time_oracle_numeric(prob, h)
     ts = [time_oracle_numeric(prob, h) for _ in range(a.steps)]
@@ -481,7 +485,7 @@ def main():
     ick.load()
 
     prob = synth.laplace3d_27pt(a.side)
-    perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.leaf_rows)
+    perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.leaf_rows, sep_colours=a.sep_colours)
     h = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
                         warps_per_cta=a.warps, solve_mode=a.solve_mode, solve_lanes=a.solve_lanes,
                         solve_ctas_per_sm=a.solve_ctas)
@@ -694,7 +698,10 @@ def main():
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle
-        o = oracle.OracleIC.from_problem(prob, perm, a.k)
+        operm, _ = oracle.nd_grid(a.side, a.side, a.side, 1, a.leaf_rows, sep_colours=a.sep_colours)
+        if not np.array_equal(operm, perm):
+            raise RuntimeError("the library's nested-dissection order differs from the oracle's")
+        o = oracle.OracleIC.from_problem(prob, operm, a.k)
         t0 = time.perf_counter()
         assert o.numeric(prob.vals) == 0
         t = time.perf_counter() - t0

@@ -116,15 +116,23 @@ typedef struct ic_handle ic_handle;
  * the high half and the plane are numbered in that order, recursively.  A part
  * with <= leaf_rows kept rows, or whose longest extent is < 3, is a leaf (this is
  * the pruning of the ND tree, Algorithm 1 step 3).  Inside a part rows are
- * lexicographic with x fastest; dof > 1 keeps a node's dofs together.
+ * lexicographic with x fastest; dof > 1 keeps a node's dofs together.  The paper
+ * takes the order inside a separator from Scotch and does not fix it; with
+ * sep_colours = C >= 2 a separator plane cut across axis a is numbered colour class
+ * by colour class instead: a node's class is (u mod C) + C (v mod C), u and v its
+ * coordinates along the two other axes (u the lower-numbered axis), classes in
+ * ascending order, lexicographic inside a class.  Same fill pattern and flops for
+ * IC(k) of a 27-point grid; shorter dependence chains in the triangular solves.
+ *   sep_colours 0 or 1: lexicographic separators; 2..16: C.
  *   keep      host, nx*ny*nz*dof bytes or NULL: 0 drops that dof (eliminated
  *             boundary conditions); the returned order covers the kept dofs only,
  *             indexed in grid order among the kept ones.
  *   perm_out  host, >= n entries: perm[new] = old.
  *   ranges_out host, >= n+1 entries or NULL: 0 then the end of each part, in order.
  *   nranges_out, n_out: number of parts and of kept rows.
- * Errors: IC_ERR_ARG for non-positive sizes or NULL perm_out. */
-int ic_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep,
+ * Errors: IC_ERR_ARG for non-positive sizes, sep_colours outside 0..16 or NULL
+ * perm_out. */
+int ic_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int sep_colours, const uint8_t* keep,
                int32_t* perm_out, int64_t* ranges_out, int64_t* nranges_out, int64_t* n_out);
 
 /* Symbolic factorization (Algorithm 1, steps 2, 4, 5; Sections 3.1-3.3) on the host:

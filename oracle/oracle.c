@@ -8,7 +8,11 @@
  *   orc_nd_grid   geometric nested dissection (Algorithm 1, step 1; Section 3.1):
  *                 the longest box axis is cut by a one-node plane at lo+(hi-lo)/2,
  *                 low half, high half, then the plane; stop at <= leaf_rows rows or
- *                 an extent below 3; lexicographic (x fastest) inside a part.
+ *                 an extent below 3; lexicographic (x fastest) inside a part.  With
+ *                 colours C >= 2 a plane cut across axis a is reordered by a stable
+ *                 sort on the key (u mod C) + C (v mod C), u < v the other two axes'
+ *                 coordinates (the paper leaves the order inside a separator to
+ *                 Scotch).
  *   orc_ic_create symmetric reordering B = P^T A P (Algorithm 1, step 2) and the
  *                 level-k fill pattern (Algorithm 1, step 4).  Levels follow the
  *                 definition in the Section 1 footnote: original entries have level
@@ -43,7 +47,10 @@
 
 typedef struct {
     int nx, ny, nz, dof, leaf_rows;
+    int colours; /* separator planes sorted by C x C colour key when >= 2 */
     const uint8_t* keep;
+    const int64_t* full_of; /* kept index -> grid dof index (colours >= 2 only) */
+    int failed;             /* an allocation failed */
     int32_t* perm;
     int64_t next;    /* next new index */
     int64_t* ranges; /* boundaries of the ordered parts, may be NULL */
@@ -79,6 +86,37 @@ static void emit_box(nd_state* s, const int lo[3], const int hi[3], int64_t* old
     if (s->next > start && s->ranges) s->ranges[++s->nranges] = s->next;
 }
 
+/* Stable counting sort of the separator rows perm[first..next) by the colour key of
+ * their grid node; the plane is cut across axis ax. */
+static void colour_sort(nd_state* s, int64_t first, int ax) {
+    const int C = s->colours;
+    const int u_ax = ax == 0 ? 1 : 0, v_ax = ax == 2 ? 1 : 2;
+    const int64_t m = s->next - first;
+    if (m <= 1) return;
+    int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * m);
+    int* key = (int*)malloc(sizeof(int) * m);
+    int64_t* count = (int64_t*)calloc((size_t)C * C + 1, sizeof(int64_t));
+    if (!tmp || !key || !count) {
+        s->failed = 1;
+    } else {
+        for (int64_t r = 0; r < m; ++r) {
+            int64_t node = s->full_of[s->perm[first + r]] / s->dof;
+            int q[3];
+            q[0] = (int)(node % s->nx);
+            q[1] = (int)((node / s->nx) % s->ny);
+            q[2] = (int)(node / ((int64_t)s->nx * s->ny));
+            key[r] = q[u_ax] % C + C * (q[v_ax] % C);
+            count[key[r] + 1]++;
+        }
+        for (int k = 0; k < C * C; ++k) count[k + 1] += count[k];
+        for (int64_t r = 0; r < m; ++r) tmp[count[key[r]]++] = s->perm[first + r];
+        memcpy(s->perm + first, tmp, sizeof(int32_t) * m);
+    }
+    free(count);
+    free(key);
+    free(tmp);
+}
+
 static void nd_rec(nd_state* s, const int lo[3], const int hi[3], int64_t* old2new) {
     int ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
     if (ext[0] <= 0 || ext[1] <= 0 || ext[2] <= 0) return;
@@ -99,24 +137,39 @@ static void nd_rec(nd_state* s, const int lo[3], const int hi[3], int64_t* old2n
     his[ax] = m + 1;
     nd_rec(s, lo1, hi1, old2new);
     nd_rec(s, lo2, hi2, old2new);
+    int64_t first = s->next;
     emit_box(s, los, his, old2new);
+    if (s->colours >= 2) colour_sort(s, first, ax);
 }
 
 /* perm[new] = old (index into the kept dofs, in grid order).  ranges (optional, size
  * >= n+1) receives 0 followed by the end of every ordered part.  Returns n. */
-int64_t orc_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep,
+int64_t orc_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int colours, const uint8_t* keep,
                     int32_t* perm, int64_t* ranges, int64_t* nranges) {
-    if (nx <= 0 || ny <= 0 || nz <= 0 || dof <= 0 || leaf_rows <= 0) return -1;
+    if (nx <= 0 || ny <= 0 || nz <= 0 || dof <= 0 || leaf_rows <= 0 || colours < 0) return -1;
     int64_t nfull = (int64_t)nx * ny * nz * dof;
     int64_t* old2new = (int64_t*)malloc(sizeof(int64_t) * nfull);
     if (!old2new) return -1;
+    int64_t* full_of = colours >= 2 ? (int64_t*)malloc(sizeof(int64_t) * nfull) : NULL;
+    if (colours >= 2 && !full_of) {
+        free(old2new);
+        return -1;
+    }
     int64_t c = 0;
-    for (int64_t i = 0; i < nfull; ++i) old2new[i] = (!keep || keep[i]) ? c++ : -1;
-    nd_state s = {nx, ny, nz, dof, leaf_rows, keep, perm, 0, ranges, 0};
+    for (int64_t i = 0; i < nfull; ++i) {
+        old2new[i] = (!keep || keep[i]) ? c : -1;
+        if (!keep || keep[i]) {
+            if (full_of) full_of[c] = i;
+            ++c;
+        }
+    }
+    nd_state s = {nx, ny, nz, dof, leaf_rows, colours, keep, full_of, 0, perm, 0, ranges, 0};
     if (ranges) ranges[0] = 0;
     int lo[3] = {0, 0, 0}, hi[3] = {nx, ny, nz};
     nd_rec(&s, lo, hi, old2new);
+    free(full_of);
     free(old2new);
+    if (s.failed) return -1;
     if (nranges) *nranges = s.nranges;
     return s.next;
 }

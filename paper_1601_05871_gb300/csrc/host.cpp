@@ -20,6 +20,7 @@ namespace {
 
 struct NdCtx {
     int nx, ny, nz, dof, leaf_rows;
+    int colours;                // separator colouring: c x c classes when >= 2
     const uint8_t* keep;
     const int64_t* kept_index;  // grid dof -> index among kept dofs, -1 if dropped
     int32_t* perm;
@@ -41,17 +42,29 @@ int64_t count_rows(const NdCtx& c, const int lo[3], const int hi[3]) {
     return cnt;
 }
 
-void number_part(NdCtx& c, const int lo[3], const int hi[3]) {
+// Numbers one part.  A separator plane cut across axis cut (cut < 0: a box) with
+// c.colours >= 2 is numbered colour class by colour class: the class of a node is
+// (u mod C) + C (v mod C), u and v its coordinates along the two other axes (u the
+// lower-numbered one), classes ascending; inside a class, and in every other part,
+// the order is lexicographic with x fastest.
+void number_part(NdCtx& c, const int lo[3], const int hi[3], int cut) {
     const int64_t first = c.next;
-    for (int z = lo[2]; z < hi[2]; ++z)
-        for (int y = lo[1]; y < hi[1]; ++y)
-            for (int x = lo[0]; x < hi[0]; ++x) {
-                int64_t base = (x + int64_t(c.nx) * (y + int64_t(c.ny) * z)) * c.dof;
-                for (int d = 0; d < c.dof; ++d) {
-                    int64_t idx = c.kept_index[base + d];
-                    if (idx >= 0) c.perm[c.next++] = int32_t(idx);
-                }
-            }
+    const int nc = (cut >= 0 && c.colours > 1) ? c.colours : 1;
+    const int a0 = cut == 0 ? 1 : 0;
+    const int a1 = cut == 2 ? 1 : 2;
+    for (int p1 = 0; p1 < nc; ++p1)
+        for (int p0 = 0; p0 < nc; ++p0)
+            for (int z = lo[2]; z < hi[2]; ++z)
+                for (int y = lo[1]; y < hi[1]; ++y)
+                    for (int x = lo[0]; x < hi[0]; ++x) {
+                        const int q[3] = {x, y, z};
+                        if (q[a0] % nc != p0 || q[a1] % nc != p1) continue;
+                        int64_t base = (x + int64_t(c.nx) * (y + int64_t(c.ny) * z)) * c.dof;
+                        for (int d = 0; d < c.dof; ++d) {
+                            int64_t idx = c.kept_index[base + d];
+                            if (idx >= 0) c.perm[c.next++] = int32_t(idx);
+                        }
+                    }
     if (c.next > first) {
         ++c.nranges;
         if (c.ranges) c.ranges[c.nranges] = c.next;
@@ -61,20 +74,20 @@ void number_part(NdCtx& c, const int lo[3], const int hi[3]) {
 // Iterative ND over boxes: each stack frame is a box, or a plane to be numbered
 // after its two halves (post-order: low, high, separator).
 void dissect(NdCtx& c) {
-    struct Frame { int lo[3], hi[3]; bool plane; };
+    struct Frame { int lo[3], hi[3]; int cut; };  // cut: the plane's axis, -1 for a box
     std::vector<Frame> st;
-    st.push_back({{0, 0, 0}, {c.nx, c.ny, c.nz}, false});
+    st.push_back({{0, 0, 0}, {c.nx, c.ny, c.nz}, -1});
     while (!st.empty()) {
         Frame f = st.back();
         st.pop_back();
         if (f.hi[0] <= f.lo[0] || f.hi[1] <= f.lo[1] || f.hi[2] <= f.lo[2]) continue;
-        if (f.plane) { number_part(c, f.lo, f.hi); continue; }
+        if (f.cut >= 0) { number_part(c, f.lo, f.hi, f.cut); continue; }
         int ext[3] = {f.hi[0] - f.lo[0], f.hi[1] - f.lo[1], f.hi[2] - f.lo[2]};
         int ax = 0;
         if (ext[1] > ext[ax]) ax = 1;
         if (ext[2] > ext[ax]) ax = 2;
         if (ext[ax] < 3 || count_rows(c, f.lo, f.hi) <= c.leaf_rows) {
-            number_part(c, f.lo, f.hi);
+            number_part(c, f.lo, f.hi, -1);
             continue;
         }
         int m = f.lo[ax] + (f.hi[ax] - f.lo[ax]) / 2;
@@ -83,7 +96,7 @@ void dissect(NdCtx& c) {
         high.lo[ax] = m + 1;
         sep.lo[ax] = m;
         sep.hi[ax] = m + 1;
-        sep.plane = true;
+        sep.cut = ax;
         st.push_back(sep);   // popped last
         st.push_back(high);
         st.push_back(low);   // popped first
@@ -92,15 +105,16 @@ void dissect(NdCtx& c) {
 
 }  // namespace
 
-int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, const uint8_t* keep, int32_t* perm,
-            int64_t* ranges, int64_t* nranges, int64_t* n_out) {
+int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int sep_colours, const uint8_t* keep,
+            int32_t* perm, int64_t* ranges, int64_t* nranges, int64_t* n_out) {
     if (nx <= 0 || ny <= 0 || nz <= 0 || dof <= 0 || leaf_rows <= 0 || !perm) return IC_ERR_ARG;
+    if (sep_colours < 0 || sep_colours > 16) return IC_ERR_ARG;
     const int64_t nfull = int64_t(nx) * ny * nz * dof;
     if (nfull > INT32_MAX) return IC_ERR_ARG;
     std::vector<int64_t> kept(nfull);
     int64_t cnt = 0;
     for (int64_t i = 0; i < nfull; ++i) kept[i] = (!keep || keep[i]) ? cnt++ : -1;
-    NdCtx c{nx, ny, nz, dof, leaf_rows, keep, kept.data(), perm, 0, ranges, 0};
+    NdCtx c{nx, ny, nz, dof, leaf_rows, sep_colours, keep, kept.data(), perm, 0, ranges, 0};
     if (ranges) ranges[0] = 0;
     dissect(c);
     if (nranges) *nranges = c.nranges;

@@ -317,6 +317,23 @@ def test_pcg_matches_oracle(ick, orc):
     assert np.abs(xg - xo).max() <= 1e-6 * np.abs(xo).max()
 
 
+def test_coloured_separators_parity(ick, orc):
+    """Separator planes numbered in 2x2 colour classes (the oracle's own ordering):
+    the factor is bit-exact in exact mode and within TOL with FMAs, and the
+    block-DAG solves match the oracle's substitutions."""
+    import torch
+    prob = synth.laplace3d_27pt(20)
+    perm, ranges = orc.nd_grid(20, 20, 20, 1, 1024, sep_colours=2)
+    check_parity(ick, orc, prob, perm, ranges, 2, exact=1, block_rows=1024)
+    h, o, _ = check_parity(ick, orc, prob, perm, ranges, 2, exact=0, block_rows=1024)
+    r = synth.rhs(prob.n, 9)
+    z = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    ick.ic_apply(h, dev(r), z)
+    ick.ic_apply_status(h)
+    zr = o.apply(r)
+    assert np.abs(z.cpu().numpy() - zr).max() <= 1e-11 * np.abs(zr).max()
+
+
 def test_repeated_applies_are_identical(ick):
     """Two hundred preconditioner applications in a row give the same bits and no
     timeout: the solves are deterministic, so a CTA whose warps disagreed on the task

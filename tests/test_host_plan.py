@@ -112,20 +112,42 @@ def test_block_dag_rejects_bad_patterns():
 
 # ------------------------------------------------------------------ ND and symbolic vs oracle
 
+@pytest.mark.parametrize("colours", [0, 2, 3])
 @pytest.mark.parametrize("grid", [(64, 64, 1, 1, 256), (17, 9, 5, 1, 40), (6, 6, 6, 3, 50),
-                                  (12, 12, 12, 1, 1), (1, 1, 1, 1, 1)])
-def test_nd_matches_oracle(orc, grid):
+                                  (12, 12, 12, 1, 1), (1, 1, 1, 1, 1), (31, 30, 29, 1, 700)])
+def test_nd_matches_oracle(orc, grid, colours):
     nx, ny, nz, dof, leaf = grid
-    p1, r1 = ick.ic_nd_grid(nx, ny, nz, dof, leaf)
-    p2, r2 = orc.nd_grid(nx, ny, nz, dof, leaf)
+    p1, r1 = ick.ic_nd_grid(nx, ny, nz, dof, leaf, sep_colours=colours)
+    p2, r2 = orc.nd_grid(nx, ny, nz, dof, leaf, sep_colours=colours)
     assert np.array_equal(p1, p2) and np.array_equal(r1, r2)
 
 
-def test_nd_keep_matches_oracle(orc):
+@pytest.mark.parametrize("colours", [0, 2])
+def test_nd_keep_matches_oracle(orc, colours):
     p = synth.elasticity3d_q1(4, seed=4002)
-    p1, r1 = ick.ic_nd_grid(5, 5, 5, 3, 30, keep=p.keep)
-    p2, r2 = orc.nd_grid(5, 5, 5, 3, 30, keep=p.keep)
+    p1, r1 = ick.ic_nd_grid(5, 5, 5, 3, 30, keep=p.keep, sep_colours=colours)
+    p2, r2 = orc.nd_grid(5, 5, 5, 3, 30, keep=p.keep, sep_colours=colours)
     assert np.array_equal(p1, p2) and np.array_equal(r1, r2) and len(p1) == p.n
+
+
+def test_nd_rejects_bad_colours():
+    for c in (-1, 17):
+        with pytest.raises(ick.IckError):
+            ick.ic_nd_grid(8, 8, 8, 1, 40, sep_colours=c)
+
+
+def test_coloured_separators_shorten_the_solve_dag():
+    """Colour classes of a separator plane hold no 27-point neighbours, so the
+    triangular solves' dependence DAG gets shallower (both directions) while the
+    level-k pattern keeps its size."""
+    p = synth.laplace3d_27pt(24)
+    st = []
+    for c in (0, 2):
+        perm, ranges = ick.ic_nd_grid(24, 24, 24, 1, 1024, sep_colours=c)
+        h = ick.ic_symbolic(p.rowptr, p.colind, 2, perm, ranges, block_rows=1024, host_only=1)
+        st.append(ick.ic_stats(h))
+    assert st[1]["nnz_l"] == st[0]["nnz_l"] and st[1]["flops"] == st[0]["flops"]
+    assert all(d1 < d0 for d0, d1 in zip(st[0]["solve_depth"], st[1]["solve_depth"]))
 
 
 def _cases(orc):

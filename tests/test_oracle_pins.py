@@ -287,6 +287,60 @@ def test_nd_keep_mask(orc):
     assert perm_kept.tolist() == want
 
 
+def _consecutive_independent_segments(rows, adjacent):
+    """Fewest consecutive segments of `rows` with no two rows of a segment adjacent
+    (greedy is optimal: a sub-run of an independent run is independent)."""
+    segs, cur = 0, []
+    for r in rows:
+        if not cur or any(adjacent(r, q) for q in cur):
+            segs += 1
+            cur = []
+        cur.append(r)
+    return segs
+
+
+@pytest.mark.parametrize("colours,reach", [(2, 1), (3, 2)])
+def test_nd_coloured_separators(orc, colours, reach):
+    """With C x C colour classes a separator plane is numbered as C*C runs, each an
+    independent set of the plane's nodes at Chebyshev distance <= reach (reach 1: the
+    27-point stencil; C = 3 keeps nodes up to distance 2 apart), each run in grid
+    order; boxes keep their lexicographic order, and the parts keep their rows."""
+    nx, ny, nz = 11, 9, 7
+    plain, r0 = orc.nd_grid(nx, ny, nz, 1, 20)
+    perm, r1 = orc.nd_grid(nx, ny, nz, 1, 20, sep_colours=colours)
+    assert np.array_equal(r0, r1)
+    assert np.array_equal(orc.nd_grid(nx, ny, nz, 1, 20, sep_colours=1)[0], plain)
+
+    def xyz(v):
+        return v % nx, (v // nx) % ny, v // (nx * ny)
+
+    def adjacent(u, v):
+        return max(abs(a - b) for a, b in zip(xyz(u), xyz(v))) <= reach
+
+    changed = 0
+    for a, b in zip(r0[:-1], r0[1:]):
+        got, lex = perm[a:b].tolist(), plain[a:b].tolist()
+        assert sorted(got) == sorted(lex)
+        if got == lex:
+            continue
+        changed += 1
+        const = [ax for ax in range(3) if len({xyz(v)[ax] for v in got}) == 1]
+        assert const, "only separator planes are recoloured"
+        assert _consecutive_independent_segments(got, adjacent) <= colours * colours
+        # inside each colour class rows ascend in grid order
+        cls = [tuple(c % colours for i, c in enumerate(xyz(v)) if i != const[0]) for v in got]
+        for k in set(cls):
+            run = [v for v, c in zip(got, cls) if c == k]
+            assert run == sorted(run)
+        # classes in ascending (u mod C) + C (v mod C), u the lower-numbered free axis
+        keys = [c[0] + colours * c[1] for c in cls]
+        assert keys == sorted(keys)
+    assert changed >= 3
+    # the lexicographic separators are not independent runs of that count
+    seps = [plain[a:b].tolist() for a, b in zip(r0[:-1], r0[1:]) if perm[a:b].tolist() != plain[a:b].tolist()]
+    assert max(_consecutive_independent_segments(s_, adjacent) for s_ in seps) > colours * colours
+
+
 # --------------------------------------------------------------- apply / PCG pins
 
 def test_apply_with_complete_factor_inverts(orc):
