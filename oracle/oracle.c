@@ -9,10 +9,11 @@
  *                 the longest box axis is cut by a one-node plane at lo+(hi-lo)/2,
  *                 low half, high half, then the plane; stop at <= leaf_rows rows or
  *                 an extent below 3; lexicographic (x fastest) inside a part.  With
- *                 colours C >= 2 a plane cut across axis a is reordered by a stable
- *                 sort on the key (u mod C) + C (v mod C), u < v the other two axes'
- *                 coordinates (the paper leaves the order inside a separator to
- *                 Scotch).
+ *                 colours C >= 2 a plane of R rows cut across axis a becomes m =
+ *                 ceil(R / leaf_rows) even strips of its lexicographic order, each a
+ *                 part, each reordered by a stable sort on the key (u mod C) +
+ *                 C (v mod C), u < v the other two axes' coordinates (the paper
+ *                 leaves the order inside a separator to Scotch).
  *   orc_ic_create symmetric reordering B = P^T A P (Algorithm 1, step 2) and the
  *                 level-k fill pattern (Algorithm 1, step 4).  Levels follow the
  *                 definition in the Section 1 footnote: original entries have level
@@ -86,12 +87,12 @@ static void emit_box(nd_state* s, const int lo[3], const int hi[3], int64_t* old
     if (s->next > start && s->ranges) s->ranges[++s->nranges] = s->next;
 }
 
-/* Stable counting sort of the separator rows perm[first..next) by the colour key of
+/* Stable counting sort of the separator rows perm[first..last) by the colour key of
  * their grid node; the plane is cut across axis ax. */
-static void colour_sort(nd_state* s, int64_t first, int ax) {
+static void colour_sort(nd_state* s, int64_t first, int64_t last, int ax) {
     const int C = s->colours;
     const int u_ax = ax == 0 ? 1 : 0, v_ax = ax == 2 ? 1 : 2;
-    const int64_t m = s->next - first;
+    const int64_t m = last - first;
     if (m <= 1) return;
     int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * m);
     int* key = (int*)malloc(sizeof(int) * m);
@@ -139,7 +140,17 @@ static void nd_rec(nd_state* s, const int lo[3], const int hi[3], int64_t* old2n
     nd_rec(s, lo2, hi2, old2new);
     int64_t first = s->next;
     emit_box(s, los, his, old2new);
-    if (s->colours >= 2) colour_sort(s, first, ax);
+    if (s->colours >= 2 && s->next > first) {
+        /* the plane's one range becomes m even strips, each sorted by colour key */
+        int64_t rows = s->next - first;
+        int64_t m = (rows + s->leaf_rows - 1) / s->leaf_rows;
+        s->nranges--;
+        for (int64_t q = 0; q < m; ++q) {
+            int64_t lo_q = first + rows * q / m, hi_q = first + rows * (q + 1) / m;
+            colour_sort(s, lo_q, hi_q, ax);
+            if (s->ranges) s->ranges[++s->nranges] = hi_q;
+        }
+    }
 }
 
 /* perm[new] = old (index into the kept dofs, in grid order).  ranges (optional, size

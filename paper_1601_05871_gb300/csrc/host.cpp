@@ -42,32 +42,53 @@ int64_t count_rows(const NdCtx& c, const int lo[3], const int hi[3]) {
     return cnt;
 }
 
-// Numbers one part.  A separator plane cut across axis cut (cut < 0: a box) with
-// c.colours >= 2 is numbered colour class by colour class: the class of a node is
+void close_range(NdCtx& c) {
+    ++c.nranges;
+    if (c.ranges) c.ranges[c.nranges] = c.next;
+}
+
+// Numbers one part (cut < 0: a box; else a separator plane cut across axis cut) in
+// lexicographic order, x fastest, and closes its range.  With c.colours = C >= 2 a
+// plane of R kept rows is instead cut into m = ceil(R / leaf_rows) strips, strip q
+// holding rows [q R / m, (q+1) R / m) of the lexicographic order, each a range of its
+// own, and a strip is numbered colour class by colour class: the class of a node is
 // (u mod C) + C (v mod C), u and v its coordinates along the two other axes (u the
-// lower-numbered one), classes ascending; inside a class, and in every other part,
-// the order is lexicographic with x fastest.
+// lower-numbered one), classes ascending, lexicographic inside a class.  The strips
+// are the even pieces the block partition would cut the plane into, so the 2D block
+// pattern is that of the lexicographic order.
 void number_part(NdCtx& c, const int lo[3], const int hi[3], int cut) {
     const int64_t first = c.next;
     const int nc = (cut >= 0 && c.colours > 1) ? c.colours : 1;
     const int a0 = cut == 0 ? 1 : 0;
     const int a1 = cut == 2 ? 1 : 2;
-    for (int p1 = 0; p1 < nc; ++p1)
-        for (int p0 = 0; p0 < nc; ++p0)
-            for (int z = lo[2]; z < hi[2]; ++z)
-                for (int y = lo[1]; y < hi[1]; ++y)
-                    for (int x = lo[0]; x < hi[0]; ++x) {
-                        const int q[3] = {x, y, z};
-                        if (q[a0] % nc != p0 || q[a1] % nc != p1) continue;
-                        int64_t base = (x + int64_t(c.nx) * (y + int64_t(c.ny) * z)) * c.dof;
-                        for (int d = 0; d < c.dof; ++d) {
-                            int64_t idx = c.kept_index[base + d];
-                            if (idx >= 0) c.perm[c.next++] = int32_t(idx);
-                        }
-                    }
-    if (c.next > first) {
-        ++c.nranges;
-        if (c.ranges) c.ranges[c.nranges] = c.next;
+    std::vector<int> key;  // colour class of each row in lexicographic order (nc > 1)
+    for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y)
+            for (int x = lo[0]; x < hi[0]; ++x) {
+                const int q[3] = {x, y, z};
+                int64_t base = (x + int64_t(c.nx) * (y + int64_t(c.ny) * z)) * c.dof;
+                for (int d = 0; d < c.dof; ++d) {
+                    int64_t idx = c.kept_index[base + d];
+                    if (idx < 0) continue;
+                    c.perm[c.next++] = int32_t(idx);
+                    if (nc > 1) key.push_back(q[a0] % nc + nc * (q[a1] % nc));
+                }
+            }
+    const int64_t rows = c.next - first;
+    if (rows == 0) return;
+    if (nc == 1) {
+        close_range(c);
+        return;
+    }
+    const int64_t m = (rows + c.leaf_rows - 1) / c.leaf_rows;
+    std::vector<int32_t> lex(c.perm + first, c.perm + c.next);
+    c.next = first;
+    for (int64_t s = 0; s < m; ++s) {
+        const int64_t b = rows * s / m, e = rows * (s + 1) / m;
+        for (int cls = 0; cls < nc * nc; ++cls)
+            for (int64_t r = b; r < e; ++r)
+                if (key[r] == cls) c.perm[c.next++] = lex[r];
+        close_range(c);
     }
 }
 

@@ -318,14 +318,14 @@ def test_pcg_matches_oracle(ick, orc):
 
 
 def test_coloured_separators_parity(ick, orc):
-    """Separator planes numbered in 2x2 colour classes (the oracle's own ordering):
+    """Separator strips numbered in 2x2 colour classes (the oracle's own ordering):
     the factor is bit-exact in exact mode and within TOL with FMAs, and the
     block-DAG solves match the oracle's substitutions."""
     import torch
     prob = synth.laplace3d_27pt(20)
-    perm, ranges = orc.nd_grid(20, 20, 20, 1, 1024, sep_colours=2)
-    check_parity(ick, orc, prob, perm, ranges, 2, exact=1, block_rows=1024)
-    h, o, _ = check_parity(ick, orc, prob, perm, ranges, 2, exact=0, block_rows=1024)
+    perm, ranges = orc.nd_grid(20, 20, 20, 1, 256, sep_colours=2)
+    check_parity(ick, orc, prob, perm, ranges, 2, exact=1, block_rows=256)
+    h, o, _ = check_parity(ick, orc, prob, perm, ranges, 2, exact=0, block_rows=256)
     r = synth.rhs(prob.n, 9)
     z = torch.empty(prob.n, dtype=torch.float64, device="cuda")
     ick.ic_apply(h, dev(r), z)

@@ -137,16 +137,20 @@ def test_nd_rejects_bad_colours():
 
 
 def test_coloured_separators_shorten_the_solve_dag():
-    """Colour classes of a separator plane hold no 27-point neighbours, so the
-    triangular solves' dependence DAG gets shallower (both directions) while the
-    level-k pattern keeps its size."""
+    """Colour classes of a separator strip hold no 27-point neighbours, so the
+    triangular solves' dependence DAG gets shallower (both directions); the strips are
+    the blocks the lexicographic plane is cut into, so the level-k pattern, the block
+    pattern and the task DAG keep their size."""
     p = synth.laplace3d_27pt(24)
-    st = []
+    st, parts = [], []
     for c in (0, 2):
-        perm, ranges = ick.ic_nd_grid(24, 24, 24, 1, 1024, sep_colours=c)
-        h = ick.ic_symbolic(p.rowptr, p.colind, 2, perm, ranges, block_rows=1024, host_only=1)
+        perm, ranges = ick.ic_nd_grid(24, 24, 24, 1, 256, sep_colours=c)
+        parts.append(len(ranges) - 1)
+        h = ick.ic_symbolic(p.rowptr, p.colind, 2, perm, ranges, block_rows=256, host_only=1)
         st.append(ick.ic_stats(h))
-    assert st[1]["nnz_l"] == st[0]["nnz_l"] and st[1]["flops"] == st[0]["flops"]
+    for key in ("nnz_l", "flops", "nranges", "nblocks", "ntasks", "critical_path"):
+        assert st[1][key] == st[0][key], key
+    assert parts[1] > parts[0]  # planes of more than 256 rows come as strips
     assert all(d1 < d0 for d0, d1 in zip(st[0]["solve_depth"], st[1]["solve_depth"]))
 
 

@@ -301,15 +301,17 @@ def _consecutive_independent_segments(rows, adjacent):
 
 @pytest.mark.parametrize("colours,reach", [(2, 1), (3, 2)])
 def test_nd_coloured_separators(orc, colours, reach):
-    """With C x C colour classes a separator plane is numbered as C*C runs, each an
-    independent set of the plane's nodes at Chebyshev distance <= reach (reach 1: the
-    27-point stencil; C = 3 keeps nodes up to distance 2 apart), each run in grid
-    order; boxes keep their lexicographic order, and the parts keep their rows."""
-    nx, ny, nz = 11, 9, 7
-    plain, r0 = orc.nd_grid(nx, ny, nz, 1, 20)
-    perm, r1 = orc.nd_grid(nx, ny, nz, 1, 20, sep_colours=colours)
-    assert np.array_equal(r0, r1)
-    assert np.array_equal(orc.nd_grid(nx, ny, nz, 1, 20, sep_colours=1)[0], plain)
+    """With C x C colour classes a separator plane of R rows becomes ceil(R/leaf_rows)
+    even strips of its lexicographic order, each a part of its own, numbered as at
+    most C*C runs, each an independent set of the plane's nodes at Chebyshev
+    distance <= reach (reach 1: the 27-point stencil; C = 3 keeps nodes up to
+    distance 2 apart), classes in ascending key order, rows ascending inside each;
+    boxes keep their order and their part."""
+    nx, ny, nz, leaf = 11, 9, 7, 20
+    plain, r0 = orc.nd_grid(nx, ny, nz, 1, leaf)
+    perm, r1 = orc.nd_grid(nx, ny, nz, 1, leaf, sep_colours=colours)
+    assert set(r0.tolist()) <= set(r1.tolist())
+    assert np.array_equal(orc.nd_grid(nx, ny, nz, 1, leaf, sep_colours=1)[0], plain)
 
     def xyz(v):
         return v % nx, (v // nx) % ny, v // (nx * ny)
@@ -317,28 +319,35 @@ def test_nd_coloured_separators(orc, colours, reach):
     def adjacent(u, v):
         return max(abs(a - b) for a, b in zip(xyz(u), xyz(v))) <= reach
 
-    changed = 0
+    planes = strips_total = 0
+    lex_runs = []
     for a, b in zip(r0[:-1], r0[1:]):
-        got, lex = perm[a:b].tolist(), plain[a:b].tolist()
-        assert sorted(got) == sorted(lex)
-        if got == lex:
-            continue
-        changed += 1
-        const = [ax for ax in range(3) if len({xyz(v)[ax] for v in got}) == 1]
+        subs = r1[(r1 >= a) & (r1 <= b)].tolist()
+        if len(subs) == 2 and perm[a:b].tolist() == plain[a:b].tolist():
+            continue  # a box, or a plane that colouring leaves as it was
+        planes += 1
+        got_all = perm[a:b].tolist()
+        const = [ax for ax in range(3) if len({xyz(v)[ax] for v in got_all}) == 1]
         assert const, "only separator planes are recoloured"
-        assert _consecutive_independent_segments(got, adjacent) <= colours * colours
-        # inside each colour class rows ascend in grid order
-        cls = [tuple(c % colours for i, c in enumerate(xyz(v)) if i != const[0]) for v in got]
-        for k in set(cls):
-            run = [v for v, c in zip(got, cls) if c == k]
-            assert run == sorted(run)
-        # classes in ascending (u mod C) + C (v mod C), u the lower-numbered free axis
-        keys = [c[0] + colours * c[1] for c in cls]
-        assert keys == sorted(keys)
-    assert changed >= 3
-    # the lexicographic separators are not independent runs of that count
-    seps = [plain[a:b].tolist() for a, b in zip(r0[:-1], r0[1:]) if perm[a:b].tolist() != plain[a:b].tolist()]
-    assert max(_consecutive_independent_segments(s_, adjacent) for s_ in seps) > colours * colours
+        rows = b - a
+        m = -(-rows // leaf)
+        assert subs == [a + rows * q // m for q in range(m + 1)]
+        strips_total += m
+        for lo, hi in zip(subs[:-1], subs[1:]):
+            got, lex = perm[lo:hi].tolist(), plain[lo:hi].tolist()
+            assert sorted(got) == sorted(lex)
+            assert _consecutive_independent_segments(got, adjacent) <= colours * colours
+            lex_runs.append(_consecutive_independent_segments(lex, adjacent))
+            cls = [tuple(c % colours for i, c in enumerate(xyz(v)) if i != const[0]) for v in got]
+            for k in set(cls):
+                run = [v for v, c in zip(got, cls) if c == k]
+                assert run == sorted(run)
+            # classes in ascending (u mod C) + C (v mod C), u the lower-numbered free axis
+            keys = [c[0] + colours * c[1] for c in cls]
+            assert keys == sorted(keys)
+    assert planes >= 3 and strips_total > planes
+    # the lexicographic strips are not independent runs of that count
+    assert max(lex_runs) > colours * colours
 
 
 # --------------------------------------------------------------- apply / PCG pins
