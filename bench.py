@@ -4,7 +4,8 @@ persistent Chol/Trsm/Herk/Gemm task-DAG kernel) followed by a PCG solve with the
 factor as preconditioner.
 
 Workload (default): 27-point constant-coefficient Laplacian on a 96^3 grid
-(884,736 rows, 23,393,656 nonzeros), geometric nested dissection, 2D blocks of at
+(884,736 rows, 23,393,656 nonzeros), geometric nested dissection (separator planes cut
+into strips of at most 4096 rows, each numbered in 2x2 colour classes), 2D blocks of at
 most 4096 rows, IC(2), FP64, b ~ N(0,1), PCG to relative residual 1e-10.
 
 A step is one numeric factorization plus one PCG solve, which runs as one CUDA graph
@@ -48,6 +49,9 @@ FP64_NOMINAL_GFLOPS = 1250.0  # GB300's nominal FP64 rate, used only if the prob
 # launch each) of the 48^3 and 64^3 problems gave 14.89 / 14.76 (forward) and 14.98 /
 # 14.97 (backward) bytes per entry; the 64^3 figures are scaled to the factor at hand
 SOLVE_TRAFFIC_PER_ENTRY = {(2, "forward_dag"): 14.76, (2, "backward_dag"): 14.97}
+# The captures above and below ordered the separators lexicographically (sep_colours
+# 0); under another separator order the traffic fields are left null, not reused
+CAPTURED_SEP_COLOURS = 0
 # DRAM bytes (read + write) per factor entry of one launch of the numeric task kernel
 # of the 27-point IC(k) problem, by k: ncu captures of the 48^3, 64^3 and 80^3
 # problems gave 50.4, 57.8 and 55.1 bytes per entry; the 80^3 figure is scaled to the
@@ -116,8 +120,9 @@ def parse():
                     help="7-point diffusion workload instead: 160^3 (--side), sigma 2, z faces x100, IC(3)")
     ap.add_argument("--leaf-rows", type=int, default=0,
                     help="nested-dissection leaf size (the pruning of the ND tree); 0: --block-rows")
-    ap.add_argument("--sep-colours", type=int, default=0,
-                    help="number each ND separator plane in C x C colour classes (0: lexicographic)")
+    ap.add_argument("--sep-colours", type=int, default=2,
+                    help="ND separator planes cut into block-sized strips numbered in C x C colour "
+                         "classes (0: lexicographic)")
     ap.add_argument("--no-sub", action="store_true",
                     help="leave the C4 / C3 / C5 workloads out of the default line")
     a = ap.parse_args()
@@ -129,7 +134,7 @@ def parse():
 def workload_name(a):
     leaf = "" if a.leaf_rows == a.block_rows else f" (ND leaves <= {a.leaf_rows} rows)"
     if a.sep_colours >= 2:
-        leaf += f", separators in {a.sep_colours}x{a.sep_colours} colour classes"
+        leaf += f", separator strips in {a.sep_colours}x{a.sep_colours} colour classes"
     solves = {0: "block-DAG", 1: "row-level"}[a.solve_mode]
     return (f"27-point Laplacian {a.side}^3 (n={a.side ** 3}), geometric ND{leaf}, 2D blocks <= "
             f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}, {solves} triangular solves")
@@ -595,7 +600,8 @@ def main():
     # (compulsory bytes / bandwidth), so the FP64 FMA rate is its roof; the FP32 factor
     # takes the same time, so what limits the kernel is instruction issue while every
     # CTA is busy and the dependence chain of the top separators at the end
-    traffic_entry = NUMERIC_TRAFFIC_PER_ENTRY.get(a.k) if a.leaf_rows == a.block_rows else None
+    captured = a.leaf_rows == a.block_rows and a.sep_colours == CAPTURED_SEP_COLOURS
+    traffic_entry = NUMERIC_TRAFFIC_PER_ENTRY.get(a.k) if captured else None
     roof_numeric = {"kernel": "numeric_persistent (+ numeric_prepare scatter)",
                     "bound": "alu", "achieved": st["flops"] / (mean_fact * 1e-3) / 1e9,
                     "peak": fp64_peak, "unit": "GFLOP/s", "peak_source": fp64_src,
@@ -616,7 +622,7 @@ def main():
              "peak": peak_hbm, "unit": "GB/s", "peak_source": peak_src,
              "launch_ms": per, "algorithmic_bytes": solve_bytes,
              "traffic": (SOLVE_TRAFFIC_PER_ENTRY[(a.k, name)] * nnz_l
-                         if (a.k, name) in SOLVE_TRAFFIC_PER_ENTRY else None)}
+                         if captured and (a.k, name) in SOLVE_TRAFFIC_PER_ENTRY else None)}
         r["frac"] = r["achieved"] / r["peak"]
         roofs[name] = (tim[key] / ks, r)
     dominant = max(roofs.values(), key=lambda v: v[0])[1]
