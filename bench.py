@@ -123,6 +123,8 @@ def parse():
     ap.add_argument("--sep-colours", type=int, default=2,
                     help="ND separator planes cut into block-sized strips numbered in C x C colour "
                          "classes (0: lexicographic)")
+    ap.add_argument("--leaf-colours", type=int, default=0,
+                    help="number each ND leaf box in C x C x C colour classes (0: lexicographic)")
     ap.add_argument("--no-sub", action="store_true",
                     help="leave the C4 / C3 / C5 workloads out of the default line")
     a = ap.parse_args()
@@ -135,6 +137,9 @@ def workload_name(a):
     leaf = "" if a.leaf_rows == a.block_rows else f" (ND leaves <= {a.leaf_rows} rows)"
     if a.sep_colours >= 2:
         leaf += f", separator strips in {a.sep_colours}x{a.sep_colours} colour classes"
+    if a.leaf_colours >= 2:
+        c = a.leaf_colours
+        leaf += f", leaves in {c}x{c}x{c} colour classes"
     solves = {0: "block-DAG", 1: "row-level"}[a.solve_mode]
     return (f"27-point Laplacian {a.side}^3 (n={a.side ** 3}), geometric ND{leaf}, 2D blocks <= "
             f"{a.block_rows} rows, IC({a.k}) FP64 factor + FP64 PCG to {a.tol:g}, {solves} triangular solves")
@@ -207,13 +212,13 @@ class ClockSampler:
                 "samples": len(loaded), "reasons": sorted(reasons)}
 
 
-def oracle_problem(side, k, leaf_rows, sep_colours):
+def oracle_problem(side, k, leaf_rows, sep_colours, leaf_colours):
     """The oracle's symbolic phase of the side^3 27-point problem, as the GPU arm orders
-    it (geometric ND with the same leaf size and separator order)."""
+    it (geometric ND with the same leaf size, separator and leaf orders)."""
     import oracle
     import synth
     prob = synth.laplace3d_27pt(side)
-    perm, _ = oracle.nd_grid(side, side, side, 1, leaf_rows, sep_colours=sep_colours)
+    perm, _ = oracle.nd_grid(side, side, side, 1, leaf_rows, sep_colours=sep_colours, leaf_colours=leaf_colours)
     return prob, oracle.OracleIC.from_problem(prob, perm, k)
 
 
@@ -247,7 +252,7 @@ def reference_arm(a, rank, world):
     if rank != 0:
         return
     # each step: one oracle numeric factorization of the full workload (single thread)
-    prob, h = oracle_problem(a.side, a.k, a.leaf_rows, a.sep_colours)
+    prob, h = oracle_problem(a.side, a.k, a.leaf_rows, a.sep_colours, a.leaf_colours)
     for _ in range(a.warmup):
         time_oracle_numeric(prob, h)
     ts = [time_oracle_numeric(prob, h) for _ in range(a.steps)]
@@ -490,7 +495,8 @@ def main():
     ick.load()
 
     prob = synth.laplace3d_27pt(a.side)
-    perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.leaf_rows, sep_colours=a.sep_colours)
+    perm, ranges = ick.ic_nd_grid(a.side, a.side, a.side, 1, a.leaf_rows, sep_colours=a.sep_colours,
+                                  leaf_colours=a.leaf_colours)
     h = ick.ic_symbolic(prob.rowptr, prob.colind, a.k, perm, ranges, block_rows=a.block_rows,
                         warps_per_cta=a.warps, solve_mode=a.solve_mode, solve_lanes=a.solve_lanes,
                         solve_ctas_per_sm=a.solve_ctas)
@@ -600,7 +606,7 @@ def main():
     # (compulsory bytes / bandwidth), so the FP64 FMA rate is its roof; the FP32 factor
     # takes the same time, so what limits the kernel is instruction issue while every
     # CTA is busy and the dependence chain of the top separators at the end
-    captured = a.leaf_rows == a.block_rows and a.sep_colours == CAPTURED_SEP_COLOURS
+    captured = a.leaf_rows == a.block_rows and a.sep_colours == CAPTURED_SEP_COLOURS and a.leaf_colours < 2
     traffic_entry = NUMERIC_TRAFFIC_PER_ENTRY.get(a.k) if captured else None
     roof_numeric = {"kernel": "numeric_persistent (+ numeric_prepare scatter)",
                     "bound": "alu", "achieved": st["flops"] / (mean_fact * 1e-3) / 1e9,
@@ -704,7 +710,8 @@ def main():
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle
-        operm, _ = oracle.nd_grid(a.side, a.side, a.side, 1, a.leaf_rows, sep_colours=a.sep_colours)
+        operm, _ = oracle.nd_grid(a.side, a.side, a.side, 1, a.leaf_rows, sep_colours=a.sep_colours,
+                                  leaf_colours=a.leaf_colours)
         if not np.array_equal(operm, perm):
             raise RuntimeError("the library's nested-dissection order differs from the oracle's")
         o = oracle.OracleIC.from_problem(prob, operm, a.k)

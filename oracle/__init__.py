@@ -26,7 +26,7 @@ def _load():
         L = C.CDLL(path)
         P = C.c_void_p
         L.orc_nd_grid.restype = C.c_int64
-        L.orc_nd_grid.argtypes = [C.c_int] * 6 + [P, P, P, P]
+        L.orc_nd_grid.argtypes = [C.c_int] * 7 + [P, P, P, P]
         L.orc_ic_create.restype = P
         L.orc_ic_create.argtypes = [C.c_int64, P, P, P, C.c_int, P]
         L.orc_ic_free.argtypes = [P]
@@ -53,16 +53,18 @@ def _p(a):
 OK, ERR_ARG, ERR_BREAKDOWN, ERR_NOMEM, ERR_NOCONV = 0, 1, 3, 6, 7
 
 
-def nd_grid(nx, ny, nz, dof=1, leaf_rows=64, keep=None, sep_colours=0):
+def nd_grid(nx, ny, nz, dof=1, leaf_rows=64, keep=None, sep_colours=0, leaf_colours=0):
     """Geometric nested dissection: returns (perm, ranges); perm[new] = old.
-    sep_colours >= 2 sorts each separator plane by its nodes' colour key."""
+    sep_colours >= 2 cuts each separator plane into strips sorted by their nodes' colour
+    key; leaf_colours >= 2 sorts each leaf box by its nodes' 3D colour key."""
     L = _load()
     nfull = nx * ny * nz * dof
     perm = np.empty(nfull, dtype=np.int32)
     ranges = np.empty(nfull + 1, dtype=np.int64)
     nr = np.zeros(1, dtype=np.int64)
     keep_a = None if keep is None else np.ascontiguousarray(keep, dtype=np.uint8)
-    n = L.orc_nd_grid(nx, ny, nz, dof, leaf_rows, sep_colours, _p(keep_a), _p(perm), _p(ranges), _p(nr))
+    n = L.orc_nd_grid(nx, ny, nz, dof, leaf_rows, sep_colours, leaf_colours, _p(keep_a), _p(perm), _p(ranges),
+                      _p(nr))
     if n < 0:
         raise ValueError("orc_nd_grid: bad arguments")
     return perm[:n].copy(), ranges[: nr[0] + 1].copy()

@@ -13,7 +13,9 @@
  *                 ceil(R / leaf_rows) even strips of its lexicographic order, each a
  *                 part, each reordered by a stable sort on the key (u mod C) +
  *                 C (v mod C), u < v the other two axes' coordinates (the paper
- *                 leaves the order inside a separator to Scotch).
+ *                 leaves the order inside a separator to Scotch).  With
+ *                 leaf_colours C >= 2 a leaf box is sorted the same way by the key
+ *                 (x mod C) + C (y mod C) + C^2 (z mod C).
  *   orc_ic_create symmetric reordering B = P^T A P (Algorithm 1, step 2) and the
  *                 level-k fill pattern (Algorithm 1, step 4).  Levels follow the
  *                 definition in the Section 1 footnote: original entries have level
@@ -48,7 +50,8 @@
 
 typedef struct {
     int nx, ny, nz, dof, leaf_rows;
-    int colours; /* separator planes sorted by C x C colour key when >= 2 */
+    int colours;      /* separator planes sorted by C x C colour key when >= 2 */
+    int leaf_colours; /* leaf boxes sorted by C x C x C colour key when >= 2 */
     const uint8_t* keep;
     const int64_t* full_of; /* kept index -> grid dof index (colours >= 2 only) */
     int failed;             /* an allocation failed */
@@ -87,16 +90,19 @@ static void emit_box(nd_state* s, const int lo[3], const int hi[3], int64_t* old
     if (s->next > start && s->ranges) s->ranges[++s->nranges] = s->next;
 }
 
-/* Stable counting sort of the separator rows perm[first..last) by the colour key of
- * their grid node; the plane is cut across axis ax. */
+/* Stable counting sort of the rows perm[first..last) by the colour key of their grid
+ * node: for a separator plane cut across axis ax, (u mod C) + C (v mod C) with u < v the
+ * other two axes and C = colours; for a leaf box (ax < 0), (x mod C) + C (y mod C) +
+ * C^2 (z mod C) with C = leaf_colours. */
 static void colour_sort(nd_state* s, int64_t first, int64_t last, int ax) {
-    const int C = s->colours;
+    const int C = ax >= 0 ? s->colours : s->leaf_colours;
+    const int nkeys = ax >= 0 ? C * C : C * C * C;
     const int u_ax = ax == 0 ? 1 : 0, v_ax = ax == 2 ? 1 : 2;
     const int64_t m = last - first;
     if (m <= 1) return;
     int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * m);
     int* key = (int*)malloc(sizeof(int) * m);
-    int64_t* count = (int64_t*)calloc((size_t)C * C + 1, sizeof(int64_t));
+    int64_t* count = (int64_t*)calloc((size_t)nkeys + 1, sizeof(int64_t));
     if (!tmp || !key || !count) {
         s->failed = 1;
     } else {
@@ -106,10 +112,13 @@ static void colour_sort(nd_state* s, int64_t first, int64_t last, int ax) {
             q[0] = (int)(node % s->nx);
             q[1] = (int)((node / s->nx) % s->ny);
             q[2] = (int)(node / ((int64_t)s->nx * s->ny));
-            key[r] = q[u_ax] % C + C * (q[v_ax] % C);
+            if (ax >= 0)
+                key[r] = q[u_ax] % C + C * (q[v_ax] % C);
+            else
+                key[r] = q[0] % C + C * (q[1] % C) + C * C * (q[2] % C);
             count[key[r] + 1]++;
         }
-        for (int k = 0; k < C * C; ++k) count[k + 1] += count[k];
+        for (int k = 0; k < nkeys; ++k) count[k + 1] += count[k];
         for (int64_t r = 0; r < m; ++r) tmp[count[key[r]]++] = s->perm[first + r];
         memcpy(s->perm + first, tmp, sizeof(int32_t) * m);
     }
@@ -125,7 +134,9 @@ static void nd_rec(nd_state* s, const int lo[3], const int hi[3], int64_t* old2n
     if (ext[1] > ext[ax]) ax = 1;
     if (ext[2] > ext[ax]) ax = 2;
     if (box_rows(s, lo, hi) <= s->leaf_rows || ext[ax] < 3) {
+        int64_t first = s->next;
         emit_box(s, lo, hi, old2new);
+        if (s->leaf_colours >= 2) colour_sort(s, first, s->next, -1);
         return;
     }
     int m = lo[ax] + (hi[ax] - lo[ax]) / 2;
@@ -155,14 +166,16 @@ static void nd_rec(nd_state* s, const int lo[3], const int hi[3], int64_t* old2n
 
 /* perm[new] = old (index into the kept dofs, in grid order).  ranges (optional, size
  * >= n+1) receives 0 followed by the end of every ordered part.  Returns n. */
-int64_t orc_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int colours, const uint8_t* keep,
-                    int32_t* perm, int64_t* ranges, int64_t* nranges) {
-    if (nx <= 0 || ny <= 0 || nz <= 0 || dof <= 0 || leaf_rows <= 0 || colours < 0) return -1;
+int64_t orc_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int colours, int leaf_colours,
+                    const uint8_t* keep, int32_t* perm, int64_t* ranges, int64_t* nranges) {
+    if (nx <= 0 || ny <= 0 || nz <= 0 || dof <= 0 || leaf_rows <= 0 || colours < 0 || leaf_colours < 0)
+        return -1;
     int64_t nfull = (int64_t)nx * ny * nz * dof;
     int64_t* old2new = (int64_t*)malloc(sizeof(int64_t) * nfull);
     if (!old2new) return -1;
-    int64_t* full_of = colours >= 2 ? (int64_t*)malloc(sizeof(int64_t) * nfull) : NULL;
-    if (colours >= 2 && !full_of) {
+    const int any_colours = colours >= 2 || leaf_colours >= 2;
+    int64_t* full_of = any_colours ? (int64_t*)malloc(sizeof(int64_t) * nfull) : NULL;
+    if (any_colours && !full_of) {
         free(old2new);
         return -1;
     }
@@ -174,7 +187,7 @@ int64_t orc_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int colours,
             ++c;
         }
     }
-    nd_state s = {nx, ny, nz, dof, leaf_rows, colours, keep, full_of, 0, perm, 0, ranges, 0};
+    nd_state s = {nx, ny, nz, dof, leaf_rows, colours, leaf_colours, keep, full_of, 0, perm, 0, ranges, 0};
     if (ranges) ranges[0] = 0;
     int lo[3] = {0, 0, 0}, hi[3] = {nx, ny, nz};
     nd_rec(&s, lo, hi, old2new);

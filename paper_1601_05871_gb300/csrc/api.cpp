@@ -431,11 +431,12 @@ const char* ic_strerror(int s) {
 
 const char* ic_last_error(void) { return g_last_error.c_str(); }
 
-int ic_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int sep_colours, const uint8_t* keep,
-               int32_t* perm_out, int64_t* ranges_out, int64_t* nranges_out, int64_t* n_out) {
+int ic_nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int sep_colours, int leaf_colours,
+               const uint8_t* keep, int32_t* perm_out, int64_t* ranges_out, int64_t* nranges_out,
+               int64_t* n_out) {
     try {
-        return nd_grid(nx, ny, nz, dof, leaf_rows, sep_colours, keep, perm_out, ranges_out, nranges_out,
-                       n_out);
+        return nd_grid(nx, ny, nz, dof, leaf_rows, sep_colours, leaf_colours, keep, perm_out, ranges_out,
+                       nranges_out, n_out);
     } catch (const std::bad_alloc&) {
         return fail(IC_ERR_NOMEM, "host allocation failed");
     }

@@ -20,7 +20,8 @@ namespace {
 
 struct NdCtx {
     int nx, ny, nz, dof, leaf_rows;
-    int colours;                // separator colouring: c x c classes when >= 2
+    int colours;                // separator planes: C x C classes in strips when >= 2
+    int leaf_colours;           // boxes: C x C x C classes when >= 2
     const uint8_t* keep;
     const int64_t* kept_index;  // grid dof -> index among kept dofs, -1 if dropped
     int32_t* perm;
@@ -55,10 +56,13 @@ void close_range(NdCtx& c) {
 // (u mod C) + C (v mod C), u and v its coordinates along the two other axes (u the
 // lower-numbered one), classes ascending, lexicographic inside a class.  The strips
 // are the even pieces the block partition would cut the plane into, so the 2D block
-// pattern is that of the lexicographic order.
+// pattern is that of the lexicographic order.  With c.leaf_colours = C >= 2 a box is
+// numbered by the classes (x mod C) + C (y mod C) + C^2 (z mod C) the same way, as
+// one part.
 void number_part(NdCtx& c, const int lo[3], const int hi[3], int cut) {
     const int64_t first = c.next;
-    const int nc = (cut >= 0 && c.colours > 1) ? c.colours : 1;
+    const int want = cut >= 0 ? c.colours : c.leaf_colours;
+    const int nc = want > 1 ? want : 1;
     const int a0 = cut == 0 ? 1 : 0;
     const int a1 = cut == 2 ? 1 : 2;
     std::vector<int> key;  // colour class of each row in lexicographic order (nc > 1)
@@ -71,7 +75,9 @@ void number_part(NdCtx& c, const int lo[3], const int hi[3], int cut) {
                     int64_t idx = c.kept_index[base + d];
                     if (idx < 0) continue;
                     c.perm[c.next++] = int32_t(idx);
-                    if (nc > 1) key.push_back(q[a0] % nc + nc * (q[a1] % nc));
+                    if (nc == 1) continue;
+                    key.push_back(cut >= 0 ? q[a0] % nc + nc * (q[a1] % nc)
+                                           : x % nc + nc * (y % nc) + nc * nc * (z % nc));
                 }
             }
     const int64_t rows = c.next - first;
@@ -80,14 +86,16 @@ void number_part(NdCtx& c, const int lo[3], const int hi[3], int cut) {
         close_range(c);
         return;
     }
-    const int64_t m = (rows + c.leaf_rows - 1) / c.leaf_rows;
+    const int64_t m = cut >= 0 ? (rows + c.leaf_rows - 1) / c.leaf_rows : 1;
     std::vector<int32_t> lex(c.perm + first, c.perm + c.next);
+    std::vector<int64_t> ord(rows);
     c.next = first;
     for (int64_t s = 0; s < m; ++s) {
         const int64_t b = rows * s / m, e = rows * (s + 1) / m;
-        for (int cls = 0; cls < nc * nc; ++cls)
-            for (int64_t r = b; r < e; ++r)
-                if (key[r] == cls) c.perm[c.next++] = lex[r];
+        std::iota(ord.begin() + b, ord.begin() + e, b);
+        std::stable_sort(ord.begin() + b, ord.begin() + e,
+                         [&](int64_t u, int64_t v) { return key[u] < key[v]; });
+        for (int64_t r = b; r < e; ++r) c.perm[c.next++] = lex[ord[r]];
         close_range(c);
     }
 }
@@ -126,16 +134,16 @@ void dissect(NdCtx& c) {
 
 }  // namespace
 
-int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int sep_colours, const uint8_t* keep,
-            int32_t* perm, int64_t* ranges, int64_t* nranges, int64_t* n_out) {
+int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int sep_colours, int leaf_colours,
+            const uint8_t* keep, int32_t* perm, int64_t* ranges, int64_t* nranges, int64_t* n_out) {
     if (nx <= 0 || ny <= 0 || nz <= 0 || dof <= 0 || leaf_rows <= 0 || !perm) return IC_ERR_ARG;
-    if (sep_colours < 0 || sep_colours > 16) return IC_ERR_ARG;
+    if (sep_colours < 0 || sep_colours > 16 || leaf_colours < 0 || leaf_colours > 4) return IC_ERR_ARG;
     const int64_t nfull = int64_t(nx) * ny * nz * dof;
     if (nfull > INT32_MAX) return IC_ERR_ARG;
     std::vector<int64_t> kept(nfull);
     int64_t cnt = 0;
     for (int64_t i = 0; i < nfull; ++i) kept[i] = (!keep || keep[i]) ? cnt++ : -1;
-    NdCtx c{nx, ny, nz, dof, leaf_rows, sep_colours, keep, kept.data(), perm, 0, ranges, 0};
+    NdCtx c{nx, ny, nz, dof, leaf_rows, sep_colours, leaf_colours, keep, kept.data(), perm, 0, ranges, 0};
     if (ranges) ranges[0] = 0;
     dissect(c);
     if (nranges) *nranges = c.nranges;

@@ -309,7 +309,7 @@ void build_solve_dag(HostPlan& P, int threads, int ctas);
 void build_claim_order(HostPlan& P, int nctas);
 int block_dag(int64_t nb, const int64_t* bptr, const int32_t* bcol, std::vector<int4>& task,
               std::vector<int64_t>& pred_ptr, std::vector<int32_t>& pred);
-int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int sep_colours, const uint8_t* keep,
-            int32_t* perm, int64_t* ranges, int64_t* nranges, int64_t* n_out);
+int nd_grid(int nx, int ny, int nz, int dof, int leaf_rows, int sep_colours, int leaf_colours,
+            const uint8_t* keep, int32_t* perm, int64_t* ranges, int64_t* nranges, int64_t* n_out);
 
 }  // namespace ick

@@ -59,7 +59,7 @@ def load():
     L = C.CDLL(path)
     P, I, I64, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
     sig = {
-        "ic_nd_grid": (I, [I, I, I, I, I, I, P, P, P, P, P]),
+        "ic_nd_grid": (I, [I, I, I, I, I, I, I, P, P, P, P, P]),
         "ic_symbolic": (I, [P, I, P, P, I64, P, P]),
         "ic_numeric": (I, [P, P, P, P]),
         "ic_apply": (I, [P, P, P, P]),
@@ -150,9 +150,10 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
-def ic_nd_grid(nx, ny, nz, dof=1, leaf_rows=4096, keep=None, sep_colours=0):
+def ic_nd_grid(nx, ny, nz, dof=1, leaf_rows=4096, keep=None, sep_colours=0, leaf_colours=0):
     """Geometric nested dissection; returns (perm, ranges) with perm[new] = old.
-    sep_colours >= 2 numbers each separator plane colour class by colour class."""
+    sep_colours >= 2 numbers separator planes in block-sized strips, each colour class
+    by colour class; leaf_colours >= 2 numbers each leaf box colour class by class."""
     L = load()
     nfull = nx * ny * nz * dof
     perm = np.empty(nfull, dtype=np.int32)
@@ -160,8 +161,8 @@ def ic_nd_grid(nx, ny, nz, dof=1, leaf_rows=4096, keep=None, sep_colours=0):
     nr = np.zeros(1, dtype=np.int64)
     n = np.zeros(1, dtype=np.int64)
     keep_a = None if keep is None else np.ascontiguousarray(keep, dtype=np.uint8)
-    _check(L.ic_nd_grid(nx, ny, nz, dof, leaf_rows, sep_colours, _p(keep_a), _p(perm), _p(ranges), _p(nr),
-                        _p(n)))
+    _check(L.ic_nd_grid(nx, ny, nz, dof, leaf_rows, sep_colours, leaf_colours, _p(keep_a), _p(perm),
+                        _p(ranges), _p(nr), _p(n)))
     return perm[: n[0]].copy(), ranges[: nr[0] + 1].copy()
 
 

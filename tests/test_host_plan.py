@@ -112,21 +112,23 @@ def test_block_dag_rejects_bad_patterns():
 
 # ------------------------------------------------------------------ ND and symbolic vs oracle
 
-@pytest.mark.parametrize("colours", [0, 2, 3])
+@pytest.mark.parametrize("colours", [(0, 0), (2, 0), (3, 0), (0, 2), (2, 2), (3, 4)])
 @pytest.mark.parametrize("grid", [(64, 64, 1, 1, 256), (17, 9, 5, 1, 40), (6, 6, 6, 3, 50),
                                   (12, 12, 12, 1, 1), (1, 1, 1, 1, 1), (31, 30, 29, 1, 700)])
 def test_nd_matches_oracle(orc, grid, colours):
     nx, ny, nz, dof, leaf = grid
-    p1, r1 = ick.ic_nd_grid(nx, ny, nz, dof, leaf, sep_colours=colours)
-    p2, r2 = orc.nd_grid(nx, ny, nz, dof, leaf, sep_colours=colours)
+    sep, lc = colours
+    p1, r1 = ick.ic_nd_grid(nx, ny, nz, dof, leaf, sep_colours=sep, leaf_colours=lc)
+    p2, r2 = orc.nd_grid(nx, ny, nz, dof, leaf, sep_colours=sep, leaf_colours=lc)
     assert np.array_equal(p1, p2) and np.array_equal(r1, r2)
 
 
-@pytest.mark.parametrize("colours", [0, 2])
+@pytest.mark.parametrize("colours", [(0, 0), (2, 0), (2, 2)])
 def test_nd_keep_matches_oracle(orc, colours):
     p = synth.elasticity3d_q1(4, seed=4002)
-    p1, r1 = ick.ic_nd_grid(5, 5, 5, 3, 30, keep=p.keep, sep_colours=colours)
-    p2, r2 = orc.nd_grid(5, 5, 5, 3, 30, keep=p.keep, sep_colours=colours)
+    sep, lc = colours
+    p1, r1 = ick.ic_nd_grid(5, 5, 5, 3, 30, keep=p.keep, sep_colours=sep, leaf_colours=lc)
+    p2, r2 = orc.nd_grid(5, 5, 5, 3, 30, keep=p.keep, sep_colours=sep, leaf_colours=lc)
     assert np.array_equal(p1, p2) and np.array_equal(r1, r2) and len(p1) == p.n
 
 
@@ -134,6 +136,9 @@ def test_nd_rejects_bad_colours():
     for c in (-1, 17):
         with pytest.raises(ick.IckError):
             ick.ic_nd_grid(8, 8, 8, 1, 40, sep_colours=c)
+    for c in (-1, 5):
+        with pytest.raises(ick.IckError):
+            ick.ic_nd_grid(8, 8, 8, 1, 40, leaf_colours=c)
 
 
 def test_coloured_separators_shorten_the_solve_dag():

@@ -350,6 +350,45 @@ def test_nd_coloured_separators(orc, colours, reach):
     assert max(lex_runs) > colours * colours
 
 
+@pytest.mark.parametrize("colours,reach", [(2, 1), (3, 2)])
+def test_nd_coloured_leaves(orc, colours, reach):
+    """With C x C x C colour classes every leaf box is numbered as at most C^3 runs,
+    each an independent set of nodes at Chebyshev distance <= reach (reach 1: the
+    27-point stencil), classes in ascending (x mod C) + C (y mod C) + C^2 (z mod C),
+    rows ascending inside each; the parts, and the separators' order, do not change."""
+    nx, ny, nz, leaf = 12, 10, 8, 120
+    plain, r0 = orc.nd_grid(nx, ny, nz, 1, leaf)
+    perm, r1 = orc.nd_grid(nx, ny, nz, 1, leaf, leaf_colours=colours)
+    assert np.array_equal(r0, r1)
+    assert np.array_equal(orc.nd_grid(nx, ny, nz, 1, leaf, leaf_colours=1)[0], plain)
+
+    def xyz(v):
+        return v % nx, (v // nx) % ny, v // (nx * ny)
+
+    def adjacent(u, v):
+        return max(abs(a - b) for a, b in zip(xyz(u), xyz(v))) <= reach
+
+    boxes = 0
+    lex_runs = []
+    for a, b in zip(r0[:-1], r0[1:]):
+        got, lex = perm[a:b].tolist(), plain[a:b].tolist()
+        assert sorted(got) == sorted(lex)
+        if any(len({xyz(v)[ax] for v in lex}) == 1 for ax in range(3)) and b - a > 1:
+            assert got == lex  # a separator plane keeps its lexicographic order
+            continue
+        boxes += 1
+        assert _consecutive_independent_segments(got, adjacent) <= colours ** 3
+        lex_runs.append(_consecutive_independent_segments(lex, adjacent))
+        keys = [x % colours + colours * (y % colours) + colours * colours * (z % colours)
+                for x, y, z in map(xyz, got)]
+        assert keys == sorted(keys)
+        for k in set(keys):
+            run = [v for v, kk in zip(got, keys) if kk == k]
+            assert run == sorted(run)
+    assert boxes >= 4
+    assert max(lex_runs) > colours ** 3
+
+
 # --------------------------------------------------------------- apply / PCG pins
 
 def test_apply_with_complete_factor_inverts(orc):

@@ -33,6 +33,8 @@ def _cases(orc):
     yield "27pt-14-nd", p, perm, ranges, 2, 128
     perm, ranges = orc.nd_grid(14, 14, 14, 1, 256, sep_colours=2)
     yield "27pt-14-nd-coloured-separators", p, perm, ranges, 2, 128
+    perm, ranges = orc.nd_grid(14, 14, 14, 1, 256, sep_colours=2, leaf_colours=2)
+    yield "27pt-14-nd-coloured-leaves", p, perm, ranges, 2, 128
     p = synth.poisson2d_5pt(40, 40)
     yield "5pt-40-natural", p, None, None, 1, 100
     p = synth.elasticity3d_q1(5, nu=0.3)
