@@ -131,7 +131,7 @@ typedef struct ic_handle ic_handle;
  * With leaf_colours = C >= 2 every leaf box is numbered the same way by the classes
  * (x mod C) + C (y mod C) + C^2 (z mod C), as one part: the solves' chains through
  * the leaves get shorter, at the cost of more fill (on the 27-point grids measured
- * with C = 2, about 12 % more entries of L and a third more factor flops).
+ * with C = 2 and IC(2), 9-12 % more entries of L and 27-34 % more factor flops).
  *   leaf_colours 0 or 1: lexicographic leaves; 2..4: C.
  *   keep      host, nx*ny*nz*dof bytes or NULL: 0 drops that dof (eliminated
  *             boundary conditions); the returned order covers the kept dofs only,
